@@ -1,0 +1,208 @@
+/*
+ * plam.h -- C ABI of the GB300 (sm_103a) PLAM / PCAL hot path.
+ *
+ * Method: Gao, Liu, Yuan, "Parallelizable algorithms for optimization problems
+ * with orthogonality constraints" (arXiv:1810.03930).  The problem is
+ *
+ *     min f(X)  subject to  X^T X = I_p,   X in R^{n x p},  2p <= n      (Section 1, eq. prob)
+ *
+ * and one iteration at X = X^k, with G = grad f(X), B = X^T X, is
+ *
+ *     Lambda0 = Psi(G^T X),  Psi(A) = (A + A^T)/2                        (eq. Lambda1)
+ *     Lambda  = Lambda0 [+ Phi(X^T grad_X L_beta(X, Lambda0)) for PCAL]  (eq. lambda2)
+ *     R       = G - X Lambda + beta X (B - I)  = grad_X L_beta(X, Lambda) (eq. S1)
+ *     PLAM:  X <- X - R / eta                                            (eq. PLAM-main)
+ *     PCAL:  X_i <- (X_i - R_i/eta) / ||X_i - R_i/eta||_2 for every column (Algorithm 3)
+ *
+ * with eta from the rules of Section 5.1 (alternating Barzilai-Borwein by
+ * default), the stopping test ||G - X Psi(G^T X)||_F / (same at X^0) < tol
+ * (Section 5.1 with the Section 3.3 shortcut) and one final orthonormalisation
+ * (Section 5.3, Table "orth step").
+ *
+ * Conventions for every entry point
+ *   - Matrices are column-major.  X is n x p with leading dimension ldx >= n;
+ *     column i starts at X + i*ldx.  Device pointers must be 16-byte aligned and
+ *     ldx * sizeof(element) a multiple of 16 bytes.
+ *   - "storage type" is double for PLAM_PREC_FP64 and float for every other
+ *     precision mode.  X, G and dense operators are passed in the storage type.
+ *   - The caller owns every pointer it passes and keeps it alive until the call
+ *     (and, for device work, the stream) completes.  A handle owns its own
+ *     device workspace (allocated in plam_create, freed in plam_destroy) and
+ *     never frees caller memory.
+ *   - All device work is ordered on the handle's stream (a cudaStream_t passed
+ *     as void*; NULL selects the legacy default stream).  Calls that return
+ *     host-side results (info, f) synchronise that stream before returning.
+ *   - Every call returns a plam_status_t and never aborts the process.  On
+ *     PLAM_ERR_INVALID nothing was launched.  On PLAM_ERR_CUDA the CUDA error
+ *     string is available from plam_last_error().
+ */
+#ifndef PLAM_H_
+#define PLAM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PLAM_OK = 0,
+  PLAM_ERR_INVALID = 1,        /* null pointer, 2p > n, ld < n, bad enum, misalignment */
+  PLAM_ERR_NOT_CONVERGED = 2,  /* maxit iterations performed without meeting tol */
+  PLAM_ERR_DIVERGED = 3,       /* non-finite KKT value, step size or column norm */
+  PLAM_ERR_CHOLESKY = 4,       /* X^T X not numerically positive definite */
+  PLAM_ERR_TIMEOUT = 5,        /* a bounded device-side wait expired */
+  PLAM_ERR_CUDA = 6,           /* a CUDA runtime call failed */
+  PLAM_ERR_NOMEM = 7,          /* device or pinned host allocation failed */
+  PLAM_ERR_UNSUPPORTED = 8     /* valid request that this build does not implement */
+} plam_status_t;
+
+enum { PLAM_VARIANT_PLAM = 0, PLAM_VARIANT_PCAL = 1 };
+/* Multiplier rule: eq. (Lambda1), or eq. (lambda2) (PCAL only). */
+enum { PLAM_LAMBDA1 = 0, PLAM_LAMBDA2 = 1 };
+/* Proximal parameter rules of Section 5.1: alternating BB (default), BB1, BB2,
+ * constant gamma, differential ||Y||_F/||S||_F. */
+enum { PLAM_ETA_ABB = 0, PLAM_ETA_BB1 = 1, PLAM_ETA_BB2 = 2, PLAM_ETA_CONST = 3, PLAM_ETA_DIFF = 4 };
+/* Arithmetic of the iteration.  FP64: everything in double.  FP32: float
+ * storage and products, partial sums flushed into double, p x p work in double. */
+enum { PLAM_PREC_FP64 = 0, PLAM_PREC_FP32 = 1 };
+/* Built-in objectives (Section 5.2):
+ *   DENSE      f = 1/2 tr(X^T A X), A symmetric n x n              (Problem 3)
+ *   HARTREE1D  f = q tr(X^T L X) + (alpha/4) rho^T L^{-1} rho,     (Problem 1, KS form eq. KS-energy)
+ *              rho = diag(X X^T), L = tridiag(-1,2,-1) Dirichlet
+ *   STENCIL3D  f = 1/2 tr(X^T (L3 + Diag(V)) X), L3 the 7-point Dirichlet
+ *              Laplacian on nx*ny*nz points, index i = x + nx*(y + ny*z). */
+enum { PLAM_OBJ_DENSE = 0, PLAM_OBJ_HARTREE1D = 1, PLAM_OBJ_STENCIL3D = 2 };
+
+typedef struct {
+  int variant;          /* PLAM_VARIANT_* used by plam_solve (plam_step/pcal_step choose their own) */
+  int lambda_rule;      /* PLAM_LAMBDA1 / PLAM_LAMBDA2; PCAL default LAMBDA2, PLAM always LAMBDA1 */
+  double beta;          /* penalty parameter beta > = 0 */
+  int eta_rule;         /* PLAM_ETA_* */
+  double eta0;          /* eta at k = 0; <= 0 selects ||G^0||_F/||X^0||_F + beta */
+  double eta_gamma;     /* constant for PLAM_ETA_CONST (<= 0: use eta0) */
+  double tol;           /* relative KKT tolerance, Section 5.1 (1e-8 in the paper) */
+  int maxit;            /* iteration limit (3000 in the paper) */
+  int precision;        /* PLAM_PREC_* */
+  int final_orth;       /* 0: none, 1: one Cholesky-QR pass, 2: two passes (CholQR2) */
+  int graph_iters;      /* iterations per captured CUDA graph in plam_solve (even, >= 2); 0 = no graph */
+} plam_params_t;
+
+typedef struct {
+  int kind;             /* PLAM_OBJ_* */
+  const void* A;        /* DENSE: device, n x n symmetric, storage type, column-major */
+  int64_t lda;          /* DENSE: leading dimension >= n */
+  double alpha;         /* HARTREE1D: Hartree coupling alpha */
+  double quad_scale;    /* HARTREE1D: q, the coefficient of tr(X^T L X) (1/4 Kohn-Sham, 1/2 Problem 1) */
+  int nx, ny, nz;       /* STENCIL3D: grid, nx*ny*nz == n */
+  const void* V;        /* STENCIL3D: device n-vector potential, storage type (may be NULL: V = 0) */
+} plam_objective_t;
+
+typedef struct {
+  int iters;            /* updates performed so far (k) */
+  int status;           /* plam_status_t of the run / step */
+  int converged;        /* 1 when the relative KKT value fell below tol */
+  int pad_;
+  double f;             /* f(X^k) at the last evaluated iterate */
+  double kkt_rel;       /* ||G - X Psi(G^T X)||_F / K0 at that iterate */
+  double feas;          /* ||X^T X - I||_F at that iterate */
+  double eta;           /* last eta used for an update */
+  double K0;            /* ||G^0 - X^0 Psi(G^0^T X^0)||_F */
+  double eta0;          /* eta at k = 0 */
+  double f_orth;        /* after the final orthonormalisation (NaN if not run) */
+  double kkt_orth;      /* relative KKT after the final orthonormalisation */
+  double feas_orth;     /* ||Q^T Q - I||_F of the orthonormalised output */
+} plam_info_t;
+
+typedef struct plam_handle_s* plam_handle_t;
+
+/* Fills *prm with the paper's defaults: PCAL, eq. (lambda2), beta = 1, ABB,
+ * eta0 automatic, tol = 1e-8, maxit = 3000 (Section 5.1), FP64, one final
+ * orthonormalisation, 16 iterations per graph. */
+plam_status_t plam_default_params(plam_params_t* prm);
+
+/* Creates a solver for problem size n x p (2p <= n, p >= 1) with the given
+ * objective and parameters.  Allocates all device workspace (gradient,
+ * residual history, split-K partials, p x p buffers, state) on the current
+ * device.  The objective's device arrays are referenced, not copied: keep them
+ * alive until plam_destroy.  `stream` is a cudaStream_t (NULL: default stream).
+ * Errors: PLAM_ERR_INVALID, PLAM_ERR_NOMEM, PLAM_ERR_CUDA; *h is NULL then. */
+plam_status_t plam_create(plam_handle_t* h, int64_t n, int64_t p, const plam_objective_t* obj,
+                          const plam_params_t* prm, void* stream);
+
+/* Releases every resource of the handle (synchronises its stream first). */
+plam_status_t plam_destroy(plam_handle_t h);
+
+/* Forgets the iteration history (k = 0, no Barzilai-Borwein pair, K0 and eta0
+ * recomputed by the next step). */
+plam_status_t plam_reset(plam_handle_t h);
+
+/* One PLAM iteration (Algorithm 2): evaluates G, B, C = X^T G, the KKT value
+ * and feasibility at X = X^k; if the KKT test passes (or k = maxit) X is left
+ * unchanged and info->converged says why, else X is overwritten by X^{k+1}
+ * (eq. PLAM-main) with Lambda from eq. (Lambda1).  X: device, storage type,
+ * n x p, leading dimension ldx.  info may be NULL.  Returns PLAM_OK,
+ * PLAM_ERR_DIVERGED (X keeps the last finite iterate) or an error. */
+plam_status_t plam_step(plam_handle_t h, void* X, int64_t ldx, plam_info_t* info);
+
+/* One PCAL iteration (Algorithm 3 with its column-wise closed form): as
+ * plam_step, but Lambda from the handle's lambda_rule and every column of
+ * X - R/eta scaled to unit 2-norm. */
+plam_status_t pcal_step(plam_handle_t h, void* X, int64_t ldx, plam_info_t* info);
+
+/* Runs the handle's variant from X (in place, storage type) until the relative
+ * KKT value is below tol or maxit updates were made (Section 5.1), then, if
+ * final_orth > 0 and Xout != NULL, writes the orthonormalised FP64 result
+ * Q = X R^{-1}, X^T X = R^T R, to Xout (device, n x p, leading dimension ldo)
+ * (Section 5.3).  X keeps the last iterate.  The loop runs without host
+ * synchronisation inside a captured graph of graph_iters iterations; the
+ * host reads the device stop flag once per graph launch.
+ * Returns PLAM_OK, PLAM_ERR_NOT_CONVERGED (Xout still written), PLAM_ERR_DIVERGED,
+ * PLAM_ERR_CHOLESKY or an error. */
+plam_status_t plam_solve(plam_handle_t h, void* X, int64_t ldx, double* Xout, int64_t ldo,
+                         plam_info_t* info);
+
+/* Final orthonormalisation (Section 5.3; Eigen LLT in Section 5.4): B = X^T X
+ * in FP64, Cholesky B = R^T R with diag(R) > 0, Xout = X R^{-1} in FP64;
+ * `passes` = 2 repeats it on Xout (CholQR2).  X: device, storage type, n x p;
+ * Xout: device FP64 n x p (may alias X only in FP64 mode).  If feas is not NULL
+ * the host receives ||Xout^T Xout - I||_F.  Returns PLAM_ERR_CHOLESKY when a
+ * pivot is not positive and finite (Xout is then undefined). */
+plam_status_t plam_orthonormalize(plam_handle_t h, const void* X, int64_t ldx, double* Xout,
+                                  int64_t ldo, int passes, double* feas);
+
+/* Objective evaluation: G = grad f(X) (device, storage type, leading
+ * dimension ldg) and, if f is not NULL, the host value f(X) (Section 5.2, Table
+ * "cost" rows "evaluate function").  Used by the autograd wrapper and tests. */
+plam_status_t plam_energy_grad(plam_handle_t h, const void* X, int64_t ldx, void* G, int64_t ldg,
+                               double* f);
+
+/* The split-K tall-skinny Grams of one iteration (Table "cost": X^T X and
+ * grad f^T X): B = X^T X and C = X^T G as FP64 p x p column-major device
+ * matrices with leading dimension p.  Partial sums over row chunks go through
+ * the handle's workspace and are reduced in a fixed order (bitwise
+ * reproducible).  G may be NULL, then only B is formed. */
+plam_status_t plam_grams(plam_handle_t h, const void* X, int64_t ldx, const void* G, int64_t ldg,
+                         double* B, double* C);
+
+/* Copies up to `cap` per-iteration records (k, f, kkt_rel, feas, eta as 5
+ * doubles each, in that order) of the current run to host memory `out`;
+ * *count receives the number written. */
+plam_status_t plam_history(plam_handle_t h, double* out, int cap, int* count);
+
+/* Number of kernels this handle launched since creation (each graph replay
+ * counts its kernel nodes). */
+int64_t plam_kernel_launches(plam_handle_t h);
+
+/* Message of the last PLAM_ERR_CUDA on this thread (static storage). */
+const char* plam_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int plam_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PLAM_H_ */

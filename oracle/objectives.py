@@ -1,0 +1,169 @@
+"""Objectives f(X) and gradients of the paper's test problems, FP64 (oracle).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+  TraceObjective     Problem 3 (Section 5.2, eq. RR): f = 1/2 tr(X^T A X), grad = A X.
+  HartreeObjective   Problem 1 / Kohn-Sham form (Section 1.1 eq. KS-energy,
+                     Section 5.2 eq. nonlinear):
+                         f = q tr(X^T L X) + (alpha/4) rho^T L^{-1} rho,
+                         rho = diag(X X^T),
+                     L = tridiag(-1, 2, -1) with Dirichlet ends.  q = 1/4 follows
+                     the Kohn-Sham energy (q = 1/2 is Problem 1's scaling).
+                     Gradient: 2 q L X + alpha Diag(L^{-1} rho) X, since
+                     d rho_i / d X_ij = 2 X_ij and d(rho^T L^{-1} rho)/d rho = 2 L^{-1} rho.
+                     L^{-1} rho is a banded LAPACK solve (scipy.linalg.solve_banded).
+  Stencil3DObjective f = 1/2 tr(X^T (L3 + Diag(V)) X), L3 the 7-point Dirichlet
+                     Laplacian on an m^3 grid (6 on the diagonal, -1 per
+                     neighbour), built as a Kronecker sum of 1D tridiagonals;
+                     lexicographic index i = x + m y + m^2 z.
+  QuadLinearObjective Problem 2 (eq. OCQP): f = 1/2 tr(X^T A X) + tr(G^T X).
+  DenseHartreeObjective Problem 1 exactly (eq. nonlinear): dense symmetric L and
+                     its pseudo-inverse L^+ (numpy.linalg.pinv), coefficient q.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+
+class TraceObjective:
+    """f = 1/2 tr(X^T A X) (Problem 3)."""
+
+    def __init__(self, A: np.ndarray):
+        self.A = np.asarray(A, dtype=np.float64)
+        self.n = self.A.shape[0]
+
+    def value(self, X):
+        return 0.5 * float(np.sum(X * (self.A @ X)))
+
+    def grad(self, X):
+        return self.A @ X
+
+    def hess_norm_bound(self):
+        """s = ||grad^2 f(0)||_2 = ||A||_2 (Section 5.1)."""
+        return float(np.max(np.abs(np.linalg.eigvalsh(self.A))))
+
+
+class QuadLinearObjective:
+    """f = 1/2 tr(X^T A X) + tr(G^T X) (Problem 2)."""
+
+    def __init__(self, A: np.ndarray, Glin: np.ndarray):
+        self.A = np.asarray(A, dtype=np.float64)
+        self.Glin = np.asarray(Glin, dtype=np.float64)
+        self.n = self.A.shape[0]
+
+    def value(self, X):
+        return 0.5 * float(np.sum(X * (self.A @ X))) + float(np.sum(self.Glin * X))
+
+    def grad(self, X):
+        return self.A @ X + self.Glin
+
+
+def laplacian_1d_banded(n: int) -> np.ndarray:
+    """The 3 x n band storage of tridiag(-1, 2, -1) for scipy.linalg.solve_banded."""
+    ab = np.empty((3, n))
+    ab[0, :] = -1.0
+    ab[1, :] = 2.0
+    ab[2, :] = -1.0
+    return ab
+
+
+def laplacian_1d_apply(X: np.ndarray) -> np.ndarray:
+    """L X for L = tridiag(-1, 2, -1) with zero (Dirichlet) values outside."""
+    Y = 2.0 * X
+    Y[1:] -= X[:-1]
+    Y[:-1] -= X[1:]
+    return Y
+
+
+class HartreeObjective:
+    """f = q tr(X^T L X) + (alpha/4) rho^T L^{-1} rho with rho = diag(X X^T)."""
+
+    def __init__(self, n: int, alpha: float = 1.0, quad_scale: float = 0.25):
+        self.n = int(n)
+        self.alpha = float(alpha)
+        self.q = float(quad_scale)
+        self._ab = laplacian_1d_banded(self.n)
+
+    def density(self, X):
+        return np.sum(X * X, axis=1)
+
+    def hartree_potential(self, rho):
+        """L^{-1} rho by a banded LU solve (LAPACK gbsv)."""
+        return sla.solve_banded((1, 1), self._ab, rho, check_finite=False)
+
+    def value(self, X):
+        rho = self.density(X)
+        y = self.hartree_potential(rho)
+        return self.q * float(np.sum(X * laplacian_1d_apply(X))) + 0.25 * self.alpha * float(rho @ y)
+
+    def grad(self, X):
+        rho = self.density(X)
+        y = self.hartree_potential(rho)
+        return 2.0 * self.q * laplacian_1d_apply(X) + self.alpha * (y[:, None] * X)
+
+    def hess_norm_bound(self):
+        """Upper bound of ||grad^2 f(0)||_2 = 2 q ||L||_2 <= 8 q (the Hartree part vanishes at 0)."""
+        return 8.0 * self.q
+
+
+class DenseHartreeObjective:
+    """f = q tr(X^T L X) + (alpha/4) rho^T L^+ rho with a dense symmetric L (Problem 1)."""
+
+    def __init__(self, L: np.ndarray, alpha: float = 1.0, quad_scale: float = 0.5):
+        self.L = np.asarray(L, dtype=np.float64)
+        self.n = self.L.shape[0]
+        self.alpha = float(alpha)
+        self.q = float(quad_scale)
+        self.Lp = np.linalg.pinv(self.L, hermitian=True)
+
+    def value(self, X):
+        rho = np.sum(X * X, axis=1)
+        return self.q * float(np.sum(X * (self.L @ X))) + 0.25 * self.alpha * float(rho @ (self.Lp @ rho))
+
+    def grad(self, X):
+        rho = np.sum(X * X, axis=1)
+        return 2.0 * self.q * (self.L @ X) + self.alpha * ((self.Lp @ rho)[:, None] * X)
+
+    def hess_norm_bound(self):
+        """s = ||grad^2 f(0)||_2 = 2 q ||L||_2 (Problem 1 states s = ||L||_2 for q = 1/2)."""
+        return 2.0 * self.q * float(np.max(np.abs(np.linalg.eigvalsh(self.L))))
+
+
+def laplacian_3d(m: int) -> sp.csr_matrix:
+    """7-point Dirichlet Laplacian on an m^3 grid as I(x)I(x)T + I(x)T(x)I + T(x)I(x)I."""
+    T = sp.diags([-np.ones(m - 1), 2.0 * np.ones(m), -np.ones(m - 1)], [-1, 0, 1], format="csr")
+    Im = sp.identity(m, format="csr")
+    return (sp.kron(Im, sp.kron(Im, T)) + sp.kron(Im, sp.kron(T, Im)) + sp.kron(T, sp.kron(Im, Im))).tocsr()
+
+
+class Stencil3DObjective:
+    """f = 1/2 tr(X^T (L3 + Diag(V)) X) on an m^3 grid."""
+
+    def __init__(self, m: int, V: np.ndarray):
+        self.m = int(m)
+        self.n = self.m ** 3
+        self.V = np.asarray(V, dtype=np.float64)
+        self.H = (laplacian_3d(self.m) + sp.diags(self.V)).tocsr()
+
+    def value(self, X):
+        return 0.5 * float(np.sum(X * (self.H @ X)))
+
+    def grad(self, X):
+        return self.H @ X
+
+    def hess_norm_bound(self):
+        """||L3 + V||_2 <= 12 + max V (Gershgorin)."""
+        return 12.0 + float(np.max(self.V))
+
+
+def objective_for(w) -> object:
+    """Build the oracle objective described by a workloads.Workload."""
+    if w.kind == "dense":
+        return TraceObjective(w.A)
+    if w.kind == "hartree1d":
+        return HartreeObjective(w.n, w.alpha, w.quad_scale)
+    if w.kind == "stencil3d":
+        return Stencil3DObjective(w.m, w.V)
+    raise ValueError(w.kind)

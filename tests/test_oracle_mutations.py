@@ -1,0 +1,122 @@
+"""Plant plausible mistakes in the oracle (on the CPU) and check that a pin catches each one.
+
+Each mutation replaces one oracle function with a subtly wrong version (a
+dropped term, a flipped sign, a wrong factor, a missing neighbour, a wrong
+norm) and runs the pin that should detect it; the pin must fail.
+"""
+import numpy as np
+import pytest
+
+import oracle.objectives as oo
+import oracle.plam as op
+from tests import test_oracle_pins as pins
+from workloads import workload_dense_trace
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+def _c1_small():
+    w = workload_dense_trace(120, 6)
+    obj = oo.TraceObjective(w.A)
+    ev, U = np.linalg.eigh(w.A)
+    return w, obj, ev, U
+
+
+def _trace_pin():
+    w, obj, ev, _ = _c1_small()
+    r = op.solve(obj, w.X0, variant="pcal", beta=1.0, tol=1e-8, maxit=600)
+    assert r.converged
+    fstar = 0.5 * ev[: w.p].sum()
+    assert abs(r.f_orth - fstar) <= 1e-10 * abs(fstar)
+
+
+def test_unmutated_small_trace_pin_passes():
+    _trace_pin()
+
+
+def test_dropped_penalty_term_is_caught(monkeypatch):
+    def bad(G, X, B, Lam, beta):
+        return G - X @ Lam
+    monkeypatch.setattr(op, "lagrangian_grad", bad)
+    with pytest.raises(AssertionError):
+        pins.test_lemma2_feasibility_bound(0)
+
+
+def test_flipped_multiplier_sign_is_caught(monkeypatch):
+    def bad(G, X, B, Lam, beta):
+        p = X.shape[1]
+        return G + X @ Lam + beta * (X @ (B - np.eye(p)))
+    monkeypatch.setattr(op, "lagrangian_grad", bad)
+    with pytest.raises(AssertionError):
+        _trace_pin()
+
+
+def test_wrong_penalty_factor_is_caught(monkeypatch):
+    def bad(G, X, B, Lam, beta):
+        p = X.shape[1]
+        return G - X @ Lam + beta * (X @ (B - np.eye(p))) @ B   # X (B - I) B instead of X (B - I)
+    monkeypatch.setattr(op, "lagrangian_grad", bad)
+    with pytest.raises(AssertionError):
+        pins.test_single_step_matches_definitions()
+
+
+def test_lambda2_sign_error_is_caught(monkeypatch):
+    def bad(G, X, B, beta):
+        L0 = op.psi(G.T @ X)
+        R0 = op.lagrangian_grad(G, X, B, L0, beta)
+        return L0 - op.phi(X.T @ R0)
+    monkeypatch.setattr(op, "multiplier_lambda2", bad)
+    with pytest.raises(AssertionError):
+        pins.test_single_step_matches_definitions()
+
+
+def test_hartree_missing_factor_two_is_caught(monkeypatch):
+    def bad(self, X):
+        rho = self.density(X)
+        y = self.hartree_potential(rho)
+        return self.q * oo.laplacian_1d_apply(X) + self.alpha * (y[:, None] * X)
+    monkeypatch.setattr(oo.HartreeObjective, "grad", bad)
+    with pytest.raises(AssertionError):
+        pins.test_gradient_finite_difference("hartree")
+
+
+def test_hartree_wrong_operator_is_caught(monkeypatch):
+    def bad(self, rho):      # L rho instead of L^{-1} rho
+        return oo.laplacian_1d_apply(rho[:, None])[:, 0]
+    monkeypatch.setattr(oo.HartreeObjective, "hartree_potential", bad)
+    with pytest.raises(AssertionError):
+        pins.test_hartree_inverse_laplacian()
+
+
+def test_stencil_missing_neighbours_is_caught(monkeypatch):
+    import scipy.sparse as sp
+
+    def bad(m):
+        T = sp.diags([-np.ones(m - 1), 2.0 * np.ones(m), -np.ones(m - 1)], [-1, 0, 1], format="csr")
+        Im = sp.identity(m, format="csr")
+        # z-direction coupling dropped (diagonal kept at 6)
+        return (sp.kron(Im, sp.kron(Im, T)) + sp.kron(Im, sp.kron(T, Im))
+                + 2.0 * sp.identity(m ** 3)).tocsr()
+    monkeypatch.setattr(oo, "laplacian_3d", bad)
+    with pytest.raises(AssertionError):
+        pins.test_stencil3d_operator_brute_force()
+
+
+@pytest.mark.parametrize("wrong", ["row_norms", "max_norm"])
+def test_pcal_wrong_normalisation_is_caught(monkeypatch, wrong):
+    def bad(V):
+        if wrong == "row_norms":     # index mistake: normalise rows instead of columns
+            return V / np.linalg.norm(V, axis=1)[:, None]
+        return V / np.max(np.abs(V), axis=0)[None, :]
+    monkeypatch.setattr(op, "normalize_columns", bad)
+    w, obj, _, _ = _c1_small()
+    with pytest.raises(AssertionError):
+        pins.test_pcal_iterates_have_unit_columns((w, obj, None, None, None))
+
+
+def test_noop_orthonormalisation_is_caught(monkeypatch):
+    monkeypatch.setattr(op, "orthonormalize", lambda X: np.asfortranarray(X.copy()))
+    w, obj, ev, U = _c1_small()
+    sol = {v: op.solve(obj, w.X0, variant=v, beta=1.0, tol=1e-8, maxit=3000) for v in ("plam", "pcal")}
+    with pytest.raises(AssertionError):
+        pins.test_final_orthonormalisation((w, obj, ev, U, sol), "plam")
