@@ -21,8 +21,8 @@
  *
  * Conventions for every entry point
  *   - Matrices are column-major.  X is n x p with leading dimension ldx >= n;
- *     column i starts at X + i*ldx.  Device pointers must be 16-byte aligned and
- *     ldx * sizeof(element) a multiple of 16 bytes.
+ *     column i starts at X + i*ldx.  Device pointers must be aligned to their
+ *     element size (misaligned pointers are rejected with PLAM_ERR_INVALID).
  *   - "storage type" is double for PLAM_PREC_FP64 and float for every other
  *     precision mode.  X, G and dense operators are passed in the storage type.
  *   - The caller owns every pointer it passes and keeps it alive until the call
@@ -65,7 +65,10 @@ enum { PLAM_LAMBDA1 = 0, PLAM_LAMBDA2 = 1 };
  * constant gamma, differential ||Y||_F/||S||_F. */
 enum { PLAM_ETA_ABB = 0, PLAM_ETA_BB1 = 1, PLAM_ETA_BB2 = 2, PLAM_ETA_CONST = 3, PLAM_ETA_DIFF = 4 };
 /* Arithmetic of the iteration.  FP64: everything in double.  FP32: float
- * storage and products, partial sums flushed into double, p x p work in double. */
+ * storage, products and partial sums (Kahan-compensated across row chunks),
+ * the O(p^2) multiplier algebra and the scalars in double; the final
+ * orthonormalisation forms its Gram in double (exact products of floats) and
+ * writes a double result. */
 enum { PLAM_PREC_FP64 = 0, PLAM_PREC_FP32 = 1 };
 /* Built-in objectives (Section 5.2):
  *   DENSE      f = 1/2 tr(X^T A X), A symmetric n x n              (Problem 3)
@@ -86,7 +89,7 @@ typedef struct {
   int maxit;            /* iteration limit (3000 in the paper) */
   int precision;        /* PLAM_PREC_* */
   int final_orth;       /* 0: none, 1: one Cholesky-QR pass, 2: two passes (CholQR2) */
-  int graph_iters;      /* iterations per captured CUDA graph in plam_solve (even, >= 2); 0 = no graph */
+  int graph_iters;      /* iterations per captured CUDA graph in plam_solve; 0 = plain launches */
 } plam_params_t;
 
 typedef struct {
@@ -185,6 +188,17 @@ plam_status_t plam_energy_grad(plam_handle_t h, const void* X, int64_t ldx, void
  * reproducible).  G may be NULL, then only B is formed. */
 plam_status_t plam_grams(plam_handle_t h, const void* X, int64_t ldx, const void* G, int64_t ldg,
                          double* B, double* C);
+
+/* Kernel attribution: runs up to `iters` iterations of the handle's variant on
+ * X (in place, continuing the current run; call plam_reset for a fresh start)
+ * without a graph, recording CUDA events on the handle's stream between the
+ * kernel groups of each iteration.  ms[0..5] receive the average duration in
+ * milliseconds of: the objective gradient, gram_partial, gram_finalize
+ * (reduction and p x p multiplier step), update (R = G - XM with the column
+ * dots), step_size, primal_update.  *done receives the iterations run (fewer
+ * when the run stops).  The solver semantics are those of plam_solve. */
+plam_status_t plam_time_kernels(plam_handle_t h, void* X, int64_t ldx, int iters, double* ms,
+                                int* done);
 
 /* Copies up to `cap` per-iteration records (k, f, kkt_rel, feas, eta as 5
  * doubles each, in that order) of the current run to host memory `out`;

@@ -1,1 +1,166 @@
-"""GB300 (sm_103a) PLAM / PCAL hot path: Python binding of the C ABI in include/plam.h."""
+"""GB300 (sm_103a) PLAM / PCAL hot path (arXiv:1810.03930).
+
+The computation lives in lib/libplam.so (C ABI: include/plam.h).  `_lib`
+forwards the C entry points under the same names; `Solver` marshals torch
+device tensors (column-major n x p matrices stored as (p, ld) row-major
+tensors) into those calls.  PyTorch provides device memory and streams only.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _lib
+from ._lib import (PLAM_ETA_ABB, PLAM_ETA_BB1, PLAM_ETA_BB2, PLAM_ETA_CONST, PLAM_ETA_DIFF,  # noqa: F401
+                   PLAM_LAMBDA1, PLAM_LAMBDA2, PLAM_OBJ_DENSE, PLAM_OBJ_HARTREE1D,
+                   PLAM_OBJ_STENCIL3D, PLAM_PREC_FP32, PLAM_PREC_FP64, PLAM_VARIANT_PCAL,
+                   PLAM_VARIANT_PLAM, PlamError, check, pcal_step, plam_create,
+                   plam_default_params, plam_destroy, plam_energy_grad, plam_grams, plam_history,
+                   plam_kernel_launches, plam_orthonormalize, plam_reset, plam_solve, plam_step,
+                   plam_time_kernels)
+
+_RULES = {"abb": PLAM_ETA_ABB, "bb1": PLAM_ETA_BB1, "bb2": PLAM_ETA_BB2, "const": PLAM_ETA_CONST,
+          "diff": PLAM_ETA_DIFF}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def storage_dtype(precision: str):
+    torch = _torch()
+    return torch.float64 if precision == "fp64" else torch.float32
+
+
+def colmajor_to_device(M: np.ndarray, dtype, device="cuda", ld: int | None = None):
+    """An n x p (or n-vector) host array as a device tensor of shape (p, ld) holding it column-major."""
+    torch = _torch()
+    M = np.asarray(M)
+    if M.ndim == 1:
+        return torch.as_tensor(np.ascontiguousarray(M), device=device).to(dtype)
+    n, p = M.shape
+    ld = ld or n
+    t = torch.zeros((p, ld), dtype=dtype, device=device)
+    t[:, :n] = torch.as_tensor(np.ascontiguousarray(M.T), device=device).to(dtype)
+    return t
+
+
+def device_to_colmajor(t, n: int) -> np.ndarray:
+    """Inverse of colmajor_to_device: an n x p float64 host array (Fortran order)."""
+    return np.asfortranarray(t[:, :n].double().cpu().numpy().T)
+
+
+class Solver:
+    """One plam_handle_t with its objective; inputs and outputs are torch device tensors.
+
+    Matrices are torch tensors of shape (p, ld) whose memory is the column-major
+    n x p matrix (ld = leading dimension >= n).
+    """
+
+    def __init__(self, n, p, kind, *, A=None, alpha=1.0, quad_scale=0.25, grid=None, V=None,
+                 variant="pcal", lambda_rule="lambda2", beta=1.0, eta_rule="abb", eta0=0.0,
+                 eta_gamma=0.0, tol=1e-8, maxit=3000, precision="fp64", final_orth=1,
+                 graph_iters=16, stream=None):
+        torch = _torch()
+        self.n, self.p = int(n), int(p)
+        self.precision = precision
+        self.dtype = storage_dtype(precision)
+        prm = plam_default_params()
+        prm.variant = PLAM_VARIANT_PCAL if variant == "pcal" else PLAM_VARIANT_PLAM
+        prm.lambda_rule = PLAM_LAMBDA2 if lambda_rule == "lambda2" else PLAM_LAMBDA1
+        prm.beta = float(beta)
+        prm.eta_rule = _RULES[eta_rule]
+        prm.eta0 = float(eta0)
+        prm.eta_gamma = float(eta_gamma)
+        prm.tol = float(tol)
+        prm.maxit = int(maxit)
+        prm.precision = PLAM_PREC_FP64 if precision == "fp64" else PLAM_PREC_FP32
+        prm.final_orth = int(final_orth)
+        prm.graph_iters = int(graph_iters)
+        self.params = prm
+        obj = _lib.plam_objective_t()
+        self._keep = []
+        if kind == "dense":
+            At = A if isinstance(A, torch.Tensor) else colmajor_to_device(A, self.dtype)
+            self._keep.append(At)
+            obj.kind, obj.A, obj.lda = PLAM_OBJ_DENSE, At.data_ptr(), At.stride(0)
+        elif kind == "hartree1d":
+            obj.kind, obj.alpha, obj.quad_scale = PLAM_OBJ_HARTREE1D, float(alpha), float(quad_scale)
+        elif kind == "stencil3d":
+            nx, ny, nz = grid
+            obj.kind, obj.nx, obj.ny, obj.nz = PLAM_OBJ_STENCIL3D, nx, ny, nz
+            if V is not None:
+                Vt = V if isinstance(V, torch.Tensor) else colmajor_to_device(V, self.dtype)
+                self._keep.append(Vt)
+                obj.V = Vt.data_ptr()
+        else:
+            raise ValueError(kind)
+        self.objective = obj
+        self.stream = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        self.h = plam_create(self.n, self.p, obj, prm, self.stream)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            plam_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def new_matrix(self, dtype=None, ld=None):
+        torch = _torch()
+        return torch.zeros((self.p, ld or self.n), dtype=dtype or self.dtype, device="cuda")
+
+    def step(self, X, variant=None):
+        variant = variant or ("pcal" if self.params.variant == PLAM_VARIANT_PCAL else "plam")
+        fn = pcal_step if variant == "pcal" else plam_step
+        st, info = fn(self.h, X.data_ptr(), X.stride(0))
+        check(st, f"{variant}_step", ok=(0, 3))
+        return st, info
+
+    def solve(self, X, Xout=None):
+        st, info = plam_solve(self.h, X.data_ptr(), X.stride(0),
+                              Xout.data_ptr() if Xout is not None else None,
+                              Xout.stride(0) if Xout is not None else 0)
+        check(st, "plam_solve", ok=(0, 2, 3))
+        return st, info
+
+    def orthonormalize(self, X, Xout, passes=1):
+        st, feas = plam_orthonormalize(self.h, X.data_ptr(), X.stride(0), Xout.data_ptr(),
+                                       Xout.stride(0), passes)
+        check(st, "plam_orthonormalize")
+        return feas
+
+    def energy_grad(self, X, G):
+        st, f = plam_energy_grad(self.h, X.data_ptr(), X.stride(0), G.data_ptr(), G.stride(0))
+        check(st, "plam_energy_grad")
+        return f
+
+    def grams(self, X, G=None):
+        torch = _torch()
+        B = torch.empty((self.p, self.p), dtype=torch.float64, device="cuda")
+        Cm = torch.empty((self.p, self.p), dtype=torch.float64, device="cuda") if G is not None else None
+        st = plam_grams(self.h, X.data_ptr(), X.stride(0), G.data_ptr() if G is not None else None,
+                        G.stride(0) if G is not None else 0, B.data_ptr(),
+                        Cm.data_ptr() if Cm is not None else None)
+        check(st, "plam_grams")
+        # (p, p) row-major tensors holding column-major matrices: transpose back
+        return B.t().contiguous(), (Cm.t().contiguous() if Cm is not None else None)
+
+    def time_kernels(self, X, iters):
+        """Average per-launch milliseconds of each kernel group over up to `iters` iterations."""
+        st, ms, done = plam_time_kernels(self.h, X.data_ptr(), X.stride(0), iters)
+        check(st, "plam_time_kernels")
+        return ms, done
+
+    def history(self):
+        return plam_history(self.h, self.params.maxit + 2)
+
+    def reset(self):
+        plam_reset(self.h)
+
+    def kernel_launches(self):
+        return plam_kernel_launches(self.h)

@@ -1,0 +1,202 @@
+"""ctypes binding of the C ABI in include/plam.h (argument marshalling only).
+
+Every function here forwards to the identically named C entry point of
+lib/libplam.so; all computation happens in the CUDA kernels behind it.  The
+library is loaded on first use and a missing or unloadable library raises
+immediately: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libplam.so")
+
+PLAM_OK = 0
+PLAM_ERR_INVALID = 1
+PLAM_ERR_NOT_CONVERGED = 2
+PLAM_ERR_DIVERGED = 3
+PLAM_ERR_CHOLESKY = 4
+PLAM_ERR_TIMEOUT = 5
+PLAM_ERR_CUDA = 6
+PLAM_ERR_NOMEM = 7
+PLAM_ERR_UNSUPPORTED = 8
+STATUS_NAMES = {0: "PLAM_OK", 1: "PLAM_ERR_INVALID", 2: "PLAM_ERR_NOT_CONVERGED",
+                3: "PLAM_ERR_DIVERGED", 4: "PLAM_ERR_CHOLESKY", 5: "PLAM_ERR_TIMEOUT",
+                6: "PLAM_ERR_CUDA", 7: "PLAM_ERR_NOMEM", 8: "PLAM_ERR_UNSUPPORTED"}
+
+PLAM_VARIANT_PLAM, PLAM_VARIANT_PCAL = 0, 1
+PLAM_LAMBDA1, PLAM_LAMBDA2 = 0, 1
+PLAM_ETA_ABB, PLAM_ETA_BB1, PLAM_ETA_BB2, PLAM_ETA_CONST, PLAM_ETA_DIFF = 0, 1, 2, 3, 4
+PLAM_PREC_FP64, PLAM_PREC_FP32 = 0, 1
+PLAM_OBJ_DENSE, PLAM_OBJ_HARTREE1D, PLAM_OBJ_STENCIL3D = 0, 1, 2
+
+
+class plam_params_t(C.Structure):
+    _fields_ = [("variant", C.c_int), ("lambda_rule", C.c_int), ("beta", C.c_double),
+                ("eta_rule", C.c_int), ("eta0", C.c_double), ("eta_gamma", C.c_double),
+                ("tol", C.c_double), ("maxit", C.c_int), ("precision", C.c_int),
+                ("final_orth", C.c_int), ("graph_iters", C.c_int)]
+
+
+class plam_objective_t(C.Structure):
+    _fields_ = [("kind", C.c_int), ("A", C.c_void_p), ("lda", C.c_int64), ("alpha", C.c_double),
+                ("quad_scale", C.c_double), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("V", C.c_void_p)]
+
+
+class plam_info_t(C.Structure):
+    _fields_ = [("iters", C.c_int), ("status", C.c_int), ("converged", C.c_int), ("pad_", C.c_int),
+                ("f", C.c_double), ("kkt_rel", C.c_double), ("feas", C.c_double),
+                ("eta", C.c_double), ("K0", C.c_double), ("eta0", C.c_double),
+                ("f_orth", C.c_double), ("kkt_orth", C.c_double), ("feas_orth", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+SIGNATURES = {
+    "plam_default_params": (C.c_int, [C.POINTER(plam_params_t)]),
+    "plam_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int64, C.c_int64,
+                              C.POINTER(plam_objective_t), C.POINTER(plam_params_t), C.c_void_p]),
+    "plam_destroy": (C.c_int, [C.c_void_p]),
+    "plam_reset": (C.c_int, [C.c_void_p]),
+    "plam_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(plam_info_t)]),
+    "pcal_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(plam_info_t)]),
+    "plam_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                             C.POINTER(plam_info_t)]),
+    "plam_orthonormalize": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                      C.c_int, C.POINTER(C.c_double)]),
+    "plam_energy_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                   C.POINTER(C.c_double)]),
+    "plam_grams": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                             C.c_void_p, C.c_void_p]),
+    "plam_time_kernels": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int,
+                                    C.POINTER(C.c_double), C.POINTER(C.c_int)]),
+    "plam_history": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]),
+    "plam_kernel_launches": (C.c_int64, [C.c_void_p]),
+    "plam_last_error": (C.c_char_p, []),
+    "plam_version": (C.c_int, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libplam.so (once) and declare every signature.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+    try:
+        import torch  # noqa: F401  (share torch's CUDA runtime when it is present)
+    except Exception:
+        pass
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class PlamError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = load().plam_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)} {msg}".strip())
+        self.status = status
+
+
+def check(status: int, where: str, ok=(PLAM_OK,)) -> int:
+    if status not in ok:
+        raise PlamError(status, where)
+    return status
+
+
+# ---------------------------------------------------------------- same-name wrappers
+
+def plam_default_params() -> plam_params_t:
+    prm = plam_params_t()
+    check(load().plam_default_params(C.byref(prm)), "plam_default_params")
+    return prm
+
+
+def plam_create(n: int, p: int, obj: plam_objective_t, prm: plam_params_t, stream: int = 0) -> C.c_void_p:
+    h = C.c_void_p()
+    check(load().plam_create(C.byref(h), n, p, C.byref(obj), C.byref(prm), C.c_void_p(stream)),
+          "plam_create")
+    return h
+
+
+def plam_destroy(h) -> int:
+    return load().plam_destroy(h)
+
+
+def plam_reset(h) -> int:
+    return check(load().plam_reset(h), "plam_reset")
+
+
+def plam_step(h, X: int, ldx: int):
+    info = plam_info_t()
+    st = load().plam_step(h, C.c_void_p(X), ldx, C.byref(info))
+    return st, info
+
+
+def pcal_step(h, X: int, ldx: int):
+    info = plam_info_t()
+    st = load().pcal_step(h, C.c_void_p(X), ldx, C.byref(info))
+    return st, info
+
+
+def plam_solve(h, X: int, ldx: int, Xout: int | None, ldo: int):
+    info = plam_info_t()
+    st = load().plam_solve(h, C.c_void_p(X), ldx, C.c_void_p(Xout or 0), ldo, C.byref(info))
+    return st, info
+
+
+def plam_orthonormalize(h, X: int, ldx: int, Xout: int, ldo: int, passes: int = 1, want_feas=True):
+    feas = C.c_double(float("nan"))
+    st = load().plam_orthonormalize(h, C.c_void_p(X), ldx, C.c_void_p(Xout), ldo, passes,
+                                    C.byref(feas) if want_feas else None)
+    return st, feas.value
+
+
+def plam_energy_grad(h, X: int, ldx: int, G: int, ldg: int, want_f=True):
+    f = C.c_double(float("nan"))
+    st = load().plam_energy_grad(h, C.c_void_p(X), ldx, C.c_void_p(G), ldg,
+                                 C.byref(f) if want_f else None)
+    return st, f.value
+
+
+def plam_grams(h, X: int, ldx: int, G: int | None, ldg: int, B: int, Cm: int | None):
+    return load().plam_grams(h, C.c_void_p(X), ldx, C.c_void_p(G or 0), ldg, C.c_void_p(B),
+                             C.c_void_p(Cm or 0))
+
+
+KERNEL_GROUPS = ("objective", "gram_partial", "gram_finalize", "update", "step_size", "primal_update")
+
+
+def plam_time_kernels(h, X: int, ldx: int, iters: int):
+    ms = (C.c_double * 6)()
+    done = C.c_int(0)
+    st = load().plam_time_kernels(h, C.c_void_p(X), ldx, iters, ms, C.byref(done))
+    return st, dict(zip(KERNEL_GROUPS, list(ms))), done.value
+
+
+def plam_history(h, cap: int):
+    import numpy as np
+    buf = (C.c_double * (5 * max(cap, 1)))()
+    cnt = C.c_int(0)
+    check(load().plam_history(h, buf, cap, C.byref(cnt)), "plam_history")
+    return np.frombuffer(buf, dtype=np.float64, count=5 * cnt.value).reshape(cnt.value, 5).copy()
+
+
+def plam_kernel_launches(h) -> int:
+    return int(load().plam_kernel_launches(h))
+
+
+def plam_version() -> int:
+    return int(load().plam_version())

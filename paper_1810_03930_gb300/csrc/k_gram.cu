@@ -1,0 +1,299 @@
+// Tall-skinny Grams B = X^T X and C = X^T G (Table "cost" rows X^T X and
+// grad f^T X), split over row chunks, then reduced in a fixed order.
+//
+// gram_partial_kernel: one CTA per (64 x 64 output tile, row chunk).  Tiles of
+// B are computed only on and above the diagonal (B is symmetric); all tiles of
+// C are computed.  Rows are staged 32 at a time in shared memory exactly as
+// they lie in memory (contiguous along the row index), so global loads are
+// coalesced and the Gram inner product runs over shared memory.  In FP32 mode
+// the products and running sums are float; every kFlushRows rows the running
+// sums are added into an outer float sum with Kahan compensation, so the
+// rounding error grows with sqrt(kFlushRows) rather than with the chunk
+// length.  (GB300 executes FP64 at 1/64 of the FP32 rate, so FP32 mode keeps
+// double arithmetic out of every O(n p^2) and O(chunks p^2) loop.)  FP64 mode
+// is double throughout.  The chunk's partial tile is written in the storage
+// type to part[chunk][col][row] with col in [0, p) for B and [p, 2p) for C.
+//
+// gram_reduce_kernel: B and C (double) from the partials, summed over chunks
+// in chunk order (bitwise reproducible; FP32 partials with Kahan compensation).
+//
+// gram_finalize_kernel: the same reduction (one warp per entry, lanes striding
+// over the chunks, fixed butterfly) fused with the p x p part of one
+// iteration (one CTA per row i of the symmetric matrices):
+//   Lambda0 = Psi(C)                                  eq. (Lambda1)
+//   d_i = diag(X^T grad_X L_beta(X, Lambda0))_i        eq. (lambda2)
+//       = C_ii - sum_k B_ik Lambda0_ik + beta (sum_k B_ik^2 - B_ii)
+//     (since X^T (G - X Lambda0 + beta X (B - I)) = C - B Lambda0 + beta B (B - I)
+//      and B, Lambda0 are symmetric)
+//   M = Lambda0 + Diag(d) - beta (B - I)               eq. (S1): grad_X L_beta = G - X M
+//   feas_row_i = sum_j (B_ij - delta_ij)^2
+// M is symmetric, so column i of M is row i.
+#include "plam_device.cuh"
+
+namespace plam {
+
+__device__ inline void decode_tile(int bx, int nt, int& ti, int& tj, int& isg) {
+  const int upper = nt * (nt + 1) / 2;
+  if (bx < upper) {
+    int r = 0, rem = bx;
+    while (rem >= nt - r) { rem -= nt - r; ++r; }
+    ti = r; tj = r + rem; isg = 0;
+  } else {
+    const int idx = bx - upper;
+    ti = idx % nt; tj = idx / nt; isg = 1;
+  }
+}
+
+// Fixed-order sum of the partials of one entry over the chunks.
+template <typename T>
+__device__ inline double sum_chunks(const T* __restrict__ src, int nchunks, size_t cstride) {
+  if (sizeof(T) == 8) {
+    double s = 0.0;
+    for (int c = 0; c < nchunks; ++c) s += (double)src[(size_t)c * cstride];
+    return s;
+  } else {
+    float s = 0.0f, comp = 0.0f;
+    for (int c = 0; c < nchunks; ++c) {
+      const float y = (float)src[(size_t)c * cstride] - comp;
+      const float t = s + y;
+      comp = (t - s) - y;
+      s = t;
+    }
+    return (double)s - (double)comp;
+  }
+}
+
+// Tin: element type of X and G.  T: arithmetic / partial type (float, or
+// double; double with float inputs forms exact products, used by the final
+// orthonormalisation).
+template <typename Tin, typename T>
+__global__ void __launch_bounds__(kThreads)
+gram_partial_kernel(int64_t n, int p, const Tin* __restrict__ X, int64_t ldx, const Tin* __restrict__ G,
+                    int64_t ldg, int64_t rows_per_chunk, T* __restrict__ part,
+                    const DevState* __restrict__ st) {
+  if (st != nullptr && st->stop != kRunning) return;
+  const int nt = (p + kTile - 1) / kTile;
+  int ti, tj, isg;
+  decode_tile(blockIdx.x, nt, ti, tj, isg);
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk;
+  const int64_t r1 = min(n, r0 + rows_per_chunk);
+  const Tin* __restrict__ Y = isg ? G : X;
+  const int64_t ldy = isg ? ldg : ldx;
+  const int i0 = ti * kTile, j0 = tj * kTile;
+
+  __shared__ T As[kTile][kKStep + 1];
+  __shared__ T Bs[kTile][kKStep + 1];
+
+  const int t = threadIdx.x;
+  const int tx = t & 15, ty = t >> 4;
+  const int kk = t & (kKStep - 1);
+  const int cb = t / kKStep;
+  T acc[4][4], oacc[4][4], ocmp[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) { acc[u][v] = T(0); oacc[u][v] = T(0); ocmp[u][v] = T(0); }
+  int since = 0;
+
+  for (int64_t k0 = r0; k0 < r1; k0 += kKStep) {
+    const int64_t row = k0 + kk;
+    const bool rok = row < r1;
+#pragma unroll
+    for (int s = 0; s < kTile / 8; ++s) {
+      const int c = cb + 8 * s;
+      const int ci = i0 + c, cj = j0 + c;
+      As[c][kk] = (rok && ci < p) ? (T)X[row + (int64_t)ci * ldx] : T(0);
+      Bs[c][kk] = (rok && cj < p) ? (T)Y[row + (int64_t)cj * ldy] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int q = 0; q < kKStep; ++q) {
+      T a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { a[u] = As[tx + 16 * u][q]; b[u] = Bs[ty + 16 * u][q]; }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+    if (sizeof(T) == 4) {
+      since += kKStep;
+      if (since >= kFlushRows) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const T y = acc[u][v] - ocmp[u][v];
+            const T tt = oacc[u][v] + y;
+            ocmp[u][v] = (tt - oacc[u][v]) - y;
+            oacc[u][v] = tt;
+            acc[u][v] = T(0);
+          }
+        since = 0;
+      }
+    }
+  }
+  const size_t cstride = (size_t)2 * p * p;
+  T* out = part + (size_t)blockIdx.y * cstride;
+  const int cofs = isg ? p : 0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + tx + 16 * u;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int j = j0 + ty + 16 * v;
+      if (i < p && j < p) out[(size_t)(cofs + j) * p + i] = (oacc[u][v] - ocmp[u][v]) + acc[u][v];
+    }
+  }
+}
+
+template <typename T>
+__global__ void gram_reduce_kernel(int p, int nchunks, int with_g, const T* __restrict__ part,
+                                   double* __restrict__ B, double* __restrict__ C) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int col = blockIdx.y * 8 + threadIdx.y;
+  const int ncols = with_g ? 2 * p : p;
+  if (i >= p || col >= ncols) return;
+  if (col < p && i > col) return;
+  const size_t cstride = (size_t)2 * p * p;
+  const double s = sum_chunks<T>(part + (size_t)col * p + i, nchunks, cstride);
+  if (col < p) {
+    B[i + (size_t)col * p] = s;
+    B[col + (size_t)i * p] = s;
+  } else {
+    C[i + (size_t)(col - p) * p] = s;
+  }
+}
+
+// Sum over the chunks of one partial entry by one warp: lanes stride over the
+// chunks in order, then a fixed butterfly (every lane returns the same value).
+template <typename T>
+__device__ inline double warp_chunk_sum(const T* __restrict__ src, int nchunks, size_t cstride) {
+  T v = T(0);
+  for (int c = threadIdx.x & 31; c < nchunks; c += 32) v += src[(size_t)c * cstride];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return (double)v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+gram_finalize_kernel(int p, int nchunks, const T* __restrict__ part, double* __restrict__ Bout,
+                     double* __restrict__ L0out, T* __restrict__ Mt, T* __restrict__ L0t,
+                     double* __restrict__ feas_row, const DevState* __restrict__ st, IterParams prm) {
+  if (st != nullptr && st->stop != kRunning) return;
+  extern __shared__ double sh[];
+  double* Brow = sh;          // B_ij
+  double* Crow = sh + p;      // C_ij
+  double* Ccol = sh + 2 * p;  // C_ji
+  __shared__ double scratch[33];
+  const int i = blockIdx.x;
+  const size_t cstride = (size_t)2 * p * p;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  // 3p sums (row i of B, row i and column i of C), one warp each
+  for (int sidx = warp; sidx < 3 * p; sidx += nw) {
+    const int j = sidx % p, which = sidx / p;
+    const T* src = which == 0 ? part + (size_t)max(i, j) * p + min(i, j)
+                 : which == 1 ? part + (size_t)(p + j) * p + i
+                              : part + (size_t)(p + i) * p + j;
+    const double v = warp_chunk_sum<T>(src, nchunks, cstride);
+    if (lane == 0) (which == 0 ? Brow : which == 1 ? Crow : Ccol)[j] = v;
+  }
+  __syncthreads();
+  double t1 = 0.0, t2 = 0.0, tf = 0.0;
+  for (int j = threadIdx.x; j < p; j += blockDim.x) {
+    const double bij = Brow[j];
+    t1 += bij * 0.5 * (Crow[j] + Ccol[j]);
+    t2 += bij * bij;
+    const double e = bij - (j == i ? 1.0 : 0.0);
+    tf += e * e;
+  }
+  const double s1 = block_sum(t1, scratch);
+  const double s2 = block_sum(t2, scratch);
+  const double sf = block_sum(tf, scratch);
+  const double beta = prm.beta;
+  const double d = prm.lambda2 ? (Crow[i] - s1 + beta * (s2 - Brow[i])) : 0.0;
+  for (int j = threadIdx.x; j < p; j += blockDim.x) {
+    const double delta = (j == i) ? 1.0 : 0.0;
+    const double l0 = 0.5 * (Crow[j] + Ccol[j]);
+    const double m = l0 + delta * d - beta * (Brow[j] - delta);
+    Mt[j + (size_t)i * p] = (T)m;
+    L0t[j + (size_t)i * p] = (T)l0;
+    if (Bout) Bout[j + (size_t)i * p] = Brow[j];
+    if (L0out) L0out[j + (size_t)i * p] = l0;
+  }
+  if (threadIdx.x == 0) feas_row[i] = sf;
+}
+
+// ---------------------------------------------------------------- launchers
+
+template <typename Tin, typename T>
+cudaError_t launch_gram_partial(int64_t n, int p, const Tin* X, int64_t ldx, const Tin* G,
+                                int64_t ldg, int64_t rows_per_chunk, int nchunks, T* part,
+                                const DevState* st, cudaStream_t s) {
+  const int nt = (p + kTile - 1) / kTile;
+  const int tiles = nt * (nt + 1) / 2 + (G ? nt * nt : 0);
+  dim3 grid(tiles, nchunks);
+  gram_partial_kernel<Tin, T><<<grid, kThreads, 0, s>>>(n, p, X, ldx, G, ldg, rows_per_chunk, part,
+                                                          st);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gram_reduce(int p, int nchunks, int with_g, const T* part, double* B,
+                               double* C, cudaStream_t s) {
+  dim3 block(32, 8);
+  dim3 grid((p + 31) / 32, ((with_g ? 2 * p : p) + 7) / 8);
+  gram_reduce_kernel<T><<<grid, block, 0, s>>>(p, nchunks, with_g, part, B, C);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gram_finalize(int p, int nchunks, const T* part, double* B, double* L0,
+                                 T* Mt, T* L0t, double* feas_row, const DevState* st,
+                                 IterParams prm, cudaStream_t s) {
+  const size_t smem = (size_t)3 * p * sizeof(double);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(gram_finalize_kernel<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  gram_finalize_kernel<T><<<p, 256, smem, s>>>(p, nchunks, part, B, L0, Mt, L0t, feas_row, st, prm);
+  return cudaGetLastError();
+}
+
+cudaError_t preload_gram_kernels() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_partial_kernel<float, float>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_partial_kernel<float, double>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_partial_kernel<double, double>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_reduce_kernel<float>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_reduce_kernel<double>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_finalize_kernel<float>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_finalize_kernel<double>);
+  return e;
+}
+
+template cudaError_t launch_gram_partial<float, float>(int64_t, int, const float*, int64_t,
+                                                       const float*, int64_t, int64_t, int, float*,
+                                                       const DevState*, cudaStream_t);
+template cudaError_t launch_gram_partial<float, double>(int64_t, int, const float*, int64_t,
+                                                        const float*, int64_t, int64_t, int, double*,
+                                                        const DevState*, cudaStream_t);
+template cudaError_t launch_gram_partial<double, double>(int64_t, int, const double*, int64_t,
+                                                         const double*, int64_t, int64_t, int,
+                                                         double*, const DevState*, cudaStream_t);
+template cudaError_t launch_gram_reduce<float>(int, int, int, const float*, double*, double*,
+                                               cudaStream_t);
+template cudaError_t launch_gram_reduce<double>(int, int, int, const double*, double*, double*,
+                                                cudaStream_t);
+template cudaError_t launch_gram_finalize<float>(int, int, const float*, double*, double*, float*,
+                                                 float*, double*, const DevState*, IterParams,
+                                                 cudaStream_t);
+template cudaError_t launch_gram_finalize<double>(int, int, const double*, double*, double*,
+                                                  double*, double*, double*, const DevState*,
+                                                  IterParams, cudaStream_t);
+
+}  // namespace plam

@@ -1,0 +1,279 @@
+// Gradients of the built-in objectives (Section 5.2; Table "cost", rows
+// "evaluate function").
+//
+// dense_grad_kernel     G = A X for f = 1/2 tr(X^T A X) (Problem 3), a tiled
+//                       64 x 64 GEMM over shared-memory stages of A and X.
+// hartree kernels       f = q tr(X^T L X) + (alpha/4) rho^T L^{-1} rho
+//                       (eq. KS-energy, Problem 1 with L = tridiag(-1,2,-1)),
+//                       G = 2 q L X + alpha Diag(y) X with y = L^{-1} rho.
+//   The Dirichlet Laplacian has the closed-form inverse (1-based indices)
+//       (L^{-1})_ij = min(i,j) (n+1-max(i,j)) / (n+1),
+//   so y_i = [ (n+1-i) P_i + i Q_i ] / (n+1) with the prefix / suffix sums
+//       P_i = sum_{j<=i} j rho_j,   Q_i = sum_{j>i} (n+1-j) rho_j,
+//   all terms non-negative (no cancellation).  Kernel 1 forms rho and the
+//   per-block sums of j rho_j and (n+1-j) rho_j; kernel 2 adds the sums of the
+//   preceding / following blocks in a fixed order, scans inside its block,
+//   forms y and writes G and the block's share of rho^T y (for f).  rho, y and
+//   the scans are double (O(n) work); G is computed in the storage type.
+// stencil_grad_kernel   G = (L3 + Diag(V)) X, L3 the 7-point Dirichlet
+//                       Laplacian (6 on the diagonal, -1 per neighbour inside
+//                       the grid), index i = x + nx (y + ny z).
+#include "plam_device.cuh"
+
+namespace plam {
+
+// ---------------------------------------------------------------- dense
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+dense_grad_kernel(int64_t n, int p, const T* __restrict__ A, int64_t lda, const T* __restrict__ X,
+                  int64_t ldx, T* __restrict__ G, int64_t ldg, const DevState* __restrict__ st) {
+  if (st != nullptr && st->stop != kRunning) return;
+  constexpr int KS = sizeof(T) == 8 ? 16 : kKStep;
+  const int64_t r0 = (int64_t)blockIdx.x * kTile;
+  const int c0 = blockIdx.y * kTile;
+  __shared__ T As[KS][kTile];
+  __shared__ T Bs[kTile][KS + 1];
+  const int t = threadIdx.x;
+  const int tx = t & 15, ty = t >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+  for (int64_t k0 = 0; k0 < n; k0 += KS) {
+    {
+      const int r = t & (kTile - 1);
+      const int64_t row = r0 + r;
+#pragma unroll
+      for (int s = 0; s < KS / 4; ++s) {
+        const int q = (t >> 6) + 4 * s;
+        const int64_t col = k0 + q;
+        As[q][r] = (row < n && col < n) ? A[row + col * lda] : T(0);
+      }
+    }
+    {
+      const int q = t & (KS - 1);
+      const int64_t kr = k0 + q;
+#pragma unroll
+      for (int s = 0; s < kTile * KS / kThreads; ++s) {
+        const int c = t / KS + (kThreads / KS) * s;
+        const int cc = c0 + c;
+        Bs[c][q] = (kr < n && cc < p) ? X[kr + (int64_t)cc * ldx] : T(0);
+      }
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int q = 0; q < KS; ++q) {
+      T a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = As[q][tx + 16 * u];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) b[v] = Bs[ty + 16 * v][q];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int c = c0 + ty + 16 * v;
+    if (c >= p) continue;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t r = r0 + tx + 16 * u;
+      if (r < n) G[r + (int64_t)c * ldg] = acc[u][v];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- Hartree (1D)
+
+constexpr int kHB = 256;   // rows per Hartree block
+
+int hartree_blocks(int64_t n) { return (int)((n + kHB - 1) / kHB); }
+
+template <typename T>
+__global__ void __launch_bounds__(kHB)
+hartree_density_kernel(int64_t n, int p, const T* __restrict__ X, int64_t ldx,
+                       double* __restrict__ rho, double* __restrict__ blk,
+                       const DevState* __restrict__ st) {
+  if (st != nullptr && st->stop != kRunning) return;
+  __shared__ double scratch[33];
+  const int64_t r = (int64_t)blockIdx.x * kHB + threadIdx.x;
+  double rv = 0.0;
+  if (r < n) {
+    T s = T(0);
+    for (int c = 0; c < p; ++c) {
+      const T x = X[r + (int64_t)c * ldx];
+      s = fma(x, x, s);
+    }
+    rv = (double)s;
+    rho[r] = rv;
+  }
+  const double i1 = (double)(r + 1);                 // 1-based index
+  const double w2 = (double)(n - r);                 // n + 1 - i
+  const double s1 = block_sum(r < n ? i1 * rv : 0.0, scratch);
+  const double s2 = block_sum(r < n ? w2 * rv : 0.0, scratch);
+  if (threadIdx.x == 0) {
+    blk[2 * blockIdx.x] = s1;
+    blk[2 * blockIdx.x + 1] = s2;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kHB)
+hartree_grad_kernel(int64_t n, int p, double alpha, double q, double inv_np1, const T* __restrict__ X,
+                    int64_t ldx,
+                    T* __restrict__ G, int64_t ldg, const double* __restrict__ rho,
+                    const double* __restrict__ blk, double* __restrict__ yout,
+                    double* __restrict__ fpart, const DevState* __restrict__ st) {
+  if (st != nullptr && st->stop != kRunning) return;
+  __shared__ double scratch[33];
+  __shared__ double wscan[2][kHB / 32];
+  const int b = blockIdx.x;
+  const int nb = gridDim.x;
+  // sums over the preceding blocks (P) and the following blocks (Q), fixed order
+  double pa = 0.0, qa = 0.0;
+  for (int j = threadIdx.x; j < nb; j += kHB) {
+    if (j < b) pa += blk[2 * j];
+    if (j > b) qa += blk[2 * j + 1];
+  }
+  const double Pbefore = block_sum(pa, scratch);
+  const double Qafter = block_sum(qa, scratch);
+  const int64_t r = (int64_t)b * kHB + threadIdx.x;
+  const double rv = (r < n) ? rho[r] : 0.0;
+  const double i1 = (double)(r + 1);
+  const double w2 = (double)(n - r);
+  // inclusive scan of i rho_i and of (n+1-i) rho_i inside the block
+  double a = (r < n) ? i1 * rv : 0.0;
+  double c = (r < n) ? w2 * rv : 0.0;
+  const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double ta = __shfl_up_sync(0xffffffffu, a, o);
+    const double tc = __shfl_up_sync(0xffffffffu, c, o);
+    if (l >= o) { a += ta; c += tc; }
+  }
+  if (l == 31) { wscan[0][w] = a; wscan[1][w] = c; }
+  __syncthreads();
+  double wa = 0.0, wc = 0.0, ctot = 0.0;
+  for (int j = 0; j < kHB / 32; ++j) {
+    if (j < w) { wa += wscan[0][j]; wc += wscan[1][j]; }
+    ctot += wscan[1][j];
+  }
+  const double incl_a = a + wa;          // sum_{j <= i, j in block} j rho_j
+  const double incl_c = c + wc;          // sum_{j <= i, j in block} (n+1-j) rho_j
+  const double P = Pbefore + incl_a;
+  const double Q = Qafter + (ctot - incl_c);   // strictly after i
+  const double y = ((double)(n - r) * P + i1 * Q) * inv_np1;   // 1/(n+1) from the host
+  const double fy = block_sum((r < n) ? rv * y : 0.0, scratch);
+  if (threadIdx.x == 0 && fpart) fpart[b] = fy;
+  if (r >= n) return;
+  if (yout) yout[r] = y;
+  const T ty = (T)(alpha * y);
+  const T q2 = (T)(2.0 * q);
+  for (int cc = 0; cc < p; ++cc) {
+    const T* xc = X + (int64_t)cc * ldx;
+    const T x = xc[r];
+    const T xm = (r > 0) ? xc[r - 1] : T(0);
+    const T xp = (r + 1 < n) ? xc[r + 1] : T(0);
+    const T lx = (x + x) - xm - xp;
+    G[r + (int64_t)cc * ldg] = fma(q2, lx, ty * x);
+  }
+}
+
+// ---------------------------------------------------------------- 3D stencil
+
+template <typename T>
+__global__ void stencil_grad_kernel(int nx, int ny, int nz, int p, const T* __restrict__ V,
+                                    const T* __restrict__ X, int64_t ldx, T* __restrict__ G,
+                                    int64_t ldg, const DevState* __restrict__ st) {
+  if (st != nullptr && st->stop != kRunning) return;
+  const int64_t n = (int64_t)nx * ny * nz;
+  const int64_t sxy = (int64_t)nx * ny;
+  const int c = blockIdx.y;
+  const T* xc = X + (int64_t)c * ldx;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t z = r / sxy;
+    const int64_t rem = r - z * sxy;
+    const int64_t y = rem / nx;
+    const int64_t x = rem - y * nx;
+    const T xv = xc[r];
+    T nb = T(0);
+    if (x > 0) nb += xc[r - 1];
+    if (x + 1 < nx) nb += xc[r + 1];
+    if (y > 0) nb += xc[r - nx];
+    if (y + 1 < ny) nb += xc[r + nx];
+    if (z > 0) nb += xc[r - sxy];
+    if (z + 1 < nz) nb += xc[r + sxy];
+    const T d = T(6) + (V ? V[r] : T(0));
+    G[r + (int64_t)c * ldg] = fma(d, xv, -nb);
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+
+template <typename T>
+cudaError_t launch_dense_grad(int64_t n, int p, const T* A, int64_t lda, const T* X, int64_t ldx,
+                              T* G, int64_t ldg, const DevState* st, cudaStream_t s) {
+  dim3 grid((unsigned)((n + kTile - 1) / kTile), (p + kTile - 1) / kTile);
+  dense_grad_kernel<T><<<grid, kThreads, 0, s>>>(n, p, A, lda, X, ldx, G, ldg, st);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_hartree_grad(int64_t n, int p, double alpha, double q, const T* X, int64_t ldx,
+                                T* G, int64_t ldg, double* rho, double* blk, double* y,
+                                double* fpart, const DevState* st, cudaStream_t s) {
+  const int nb = hartree_blocks(n);
+  hartree_density_kernel<T><<<nb, kHB, 0, s>>>(n, p, X, ldx, rho, blk, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  hartree_grad_kernel<T><<<nb, kHB, 0, s>>>(n, p, alpha, q, 1.0 / (double)(n + 1), X, ldx, G, ldg,
+                                             rho, blk, y, fpart, st);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_stencil_grad(int nx, int ny, int nz, int p, const T* V, const T* X, int64_t ldx,
+                                T* G, int64_t ldg, const DevState* st, cudaStream_t s) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  const int threads = 256;
+  int64_t bx = (n + threads - 1) / threads;
+  if (bx > 4096) bx = 4096;
+  dim3 grid((unsigned)bx, p);
+  stencil_grad_kernel<T><<<grid, threads, 0, s>>>(nx, ny, nz, p, V, X, ldx, G, ldg, st);
+  return cudaGetLastError();
+}
+
+cudaError_t preload_objective_kernels() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, dense_grad_kernel<float>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, dense_grad_kernel<double>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, hartree_density_kernel<float>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, hartree_density_kernel<double>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, hartree_grad_kernel<float>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, hartree_grad_kernel<double>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, stencil_grad_kernel<float>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, stencil_grad_kernel<double>);
+  return e;
+}
+
+#define PLAM_INST(T)                                                                              \
+  template cudaError_t launch_dense_grad<T>(int64_t, int, const T*, int64_t, const T*, int64_t,   \
+                                            T*, int64_t, const DevState*, cudaStream_t);          \
+  template cudaError_t launch_hartree_grad<T>(int64_t, int, double, double, const T*, int64_t,    \
+                                              T*, int64_t, double*, double*, double*, double*,    \
+                                              const DevState*, cudaStream_t);                     \
+  template cudaError_t launch_stencil_grad<T>(int, int, int, int, const T*, const T*, int64_t, T*, \
+                                              int64_t, const DevState*, cudaStream_t);
+PLAM_INST(float)
+PLAM_INST(double)
+#undef PLAM_INST
+
+}  // namespace plam

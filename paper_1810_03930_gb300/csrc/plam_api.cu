@@ -1,0 +1,689 @@
+// Host side of the C ABI declared in include/plam.h: handle and workspace
+// management, the launch sequence of one PLAM / PCAL iteration, the
+// graph-captured solve loop and the final orthonormalisation.
+//
+// One iteration (Algorithms 2 and 3) is the kernel sequence
+//   objective gradient  G = grad f(X)                        (k_objective.cu)
+//   gram_partial        row-chunk partials of X^T [X | G]     (k_gram.cu)
+//   gram_finalize       B, Psi(C), d (eq. lambda2), M, feasibility rows
+//   update              R = G - X M, K = G - X Psi(C), dots   (k_update.cu)
+//   step_size           KKT test, eta (Section 5.1), PCAL column norms
+//   primal_update       X <- X - R/eta  or  (X - R/eta) / nu
+// All control (iteration counter, stop flag, eta, buffer parity) lives in a
+// device-side state record, so the sequence has no host synchronisation and
+// plam_solve replays it from a captured CUDA graph, reading the stop flag
+// back once per replay.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/plam.h"
+#include "plam_common.cuh"
+
+using namespace plam;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+plam_status_t cuda_fail(cudaError_t e, const char* what) {
+  snprintf(g_err, sizeof(g_err), "%s: %s", what, cudaGetErrorString(e));
+  return PLAM_ERR_CUDA;
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);       \
+  } while (0)
+
+int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+}  // namespace
+
+struct plam_handle_s {
+  int64_t n = 0, p = 0;
+  plam_objective_t obj{};
+  plam_params_t prm{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  int prec = 0;
+  size_t esz = 8;
+  int64_t ldw = 0;
+  void* G = nullptr;
+  void* R[2] = {nullptr, nullptr};
+  void* part = nullptr;
+  double* part64 = nullptr;
+  int nchunks = 1;
+  int64_t rows_per_chunk = 0;
+  double* B = nullptr;      // p x p
+  double* L0 = nullptr;     // p x p
+  double* C = nullptr;      // p x p scratch for plam_grams
+  void* Mt = nullptr;
+  void* L0t = nullptr;
+  double* feas_row = nullptr;
+  void* colpart = nullptr;
+  void* totpart = nullptr;
+  int nrt = 0, nct = 0;
+  double* sums = nullptr;
+  unsigned int* ticket = nullptr;
+  DevState* st = nullptr;
+  double* nubuf = nullptr;
+  void* coef = nullptr;
+  double* hist = nullptr;
+  int hist_cap = 0;
+  double* rho = nullptr;
+  double* blk = nullptr;
+  double* y = nullptr;
+  double* fpart = nullptr;
+  int nfpart = 0;
+  double* W = nullptr;
+  double* Z = nullptr;
+  int* info = nullptr;
+  double* feas_dev = nullptr;
+  double* Qtmp = nullptr;
+  double* dotpart = nullptr;
+  DevState* st_host = nullptr;
+  int* info_host = nullptr;
+  double* scal_host = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  const void* graph_X = nullptr;
+  int64_t graph_ldx = 0;
+  int graph_variant = -1;
+  int graph_kernels = 0;
+  int64_t launches = 0;
+};
+
+namespace {
+
+constexpr int kDotBlocks = 256;
+
+// ||.||-free helper: per-block partial sums of <X, G> (storage type per thread,
+// double per block), then a fixed-order sum on the host side of the copy.
+template <typename T>
+__global__ void dot_partial_kernel(int64_t n, int p, const T* __restrict__ X, int64_t ldx,
+                                   const T* __restrict__ G, int64_t ldg, double* __restrict__ out) {
+  __shared__ double red[33];
+  T s = T(0);
+  const int64_t total = n * p;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / n, r = e - c * n;
+    s = fma(X[r + c * ldx], G[r + c * ldg], s);
+  }
+  double v = (double)s;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    out[blockIdx.x] = t;
+  }
+}
+
+plam_status_t validate_params(const plam_params_t* prm) {
+  if (!prm) return PLAM_ERR_INVALID;
+  if (prm->variant != PLAM_VARIANT_PLAM && prm->variant != PLAM_VARIANT_PCAL) return PLAM_ERR_INVALID;
+  if (prm->lambda_rule != PLAM_LAMBDA1 && prm->lambda_rule != PLAM_LAMBDA2) return PLAM_ERR_INVALID;
+  if (prm->eta_rule < PLAM_ETA_ABB || prm->eta_rule > PLAM_ETA_DIFF) return PLAM_ERR_INVALID;
+  if (prm->precision != PLAM_PREC_FP64 && prm->precision != PLAM_PREC_FP32) return PLAM_ERR_INVALID;
+  if (!(prm->beta >= 0.0) || !std::isfinite(prm->beta)) return PLAM_ERR_INVALID;
+  if (!(prm->tol >= 0.0) || prm->maxit < 0) return PLAM_ERR_INVALID;
+  if (prm->final_orth < 0 || prm->final_orth > 2 || prm->graph_iters < 0) return PLAM_ERR_INVALID;
+  return PLAM_OK;
+}
+
+bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
+
+template <typename T>
+IterParams iter_params(const plam_handle_s* h, int variant, int lambda2) {
+  IterParams ip{};
+  ip.n = h->n;
+  ip.p = (int)h->p;
+  ip.variant = variant;
+  ip.lambda2 = lambda2;
+  ip.eta_rule = h->prm.eta_rule;
+  ip.maxit = h->prm.maxit;
+  ip.hist_cap = h->hist_cap;
+  ip.beta = h->prm.beta;
+  ip.eta0_user = h->prm.eta0;
+  ip.gamma = h->prm.eta_gamma;
+  ip.tol = h->prm.tol;
+  ip.hartree_alpha = (h->obj.kind == PLAM_OBJ_HARTREE1D) ? h->obj.alpha : 0.0;
+  return ip;
+}
+
+// Objective gradient into G (ld ldg); returns the number of kernels launched or -1.
+template <typename T>
+int launch_objective(plam_handle_s* h, const T* X, int64_t ldx, T* G, int64_t ldg,
+                     const DevState* st, cudaStream_t s, cudaError_t* err) {
+  const int p = (int)h->p;
+  switch (h->obj.kind) {
+    case PLAM_OBJ_DENSE:
+      *err = launch_dense_grad<T>(h->n, p, (const T*)h->obj.A, h->obj.lda, X, ldx, G, ldg, st, s);
+      return 1;
+    case PLAM_OBJ_HARTREE1D:
+      *err = launch_hartree_grad<T>(h->n, p, h->obj.alpha, h->obj.quad_scale, X, ldx, G, ldg, h->rho,
+                                    h->blk, h->y, h->fpart, st, s);
+      return 2;
+    case PLAM_OBJ_STENCIL3D:
+      *err = launch_stencil_grad<T>(h->obj.nx, h->obj.ny, h->obj.nz, p, (const T*)h->obj.V, X, ldx,
+                                    G, ldg, st, s);
+      return 1;
+  }
+  *err = cudaErrorInvalidValue;
+  return -1;
+}
+
+// The kernel sequence of one iteration on stream s; returns kernels launched.
+// When `ev` is given, ev[i] is recorded before kernel group i and ev[6] after
+// the last one (kernel attribution, plam_time_kernels).
+template <typename T>
+plam_status_t launch_iteration(plam_handle_s* h, T* X, int64_t ldx, int variant, int lambda2,
+                               cudaStream_t s, int* nk, cudaEvent_t* ev = nullptr) {
+  const int p = (int)h->p;
+  const IterParams ip = iter_params<T>(h, variant, lambda2);
+  T* G = (T*)h->G;
+  cudaError_t e;
+  if (ev) CK(cudaEventRecord(ev[0], s));
+  int k = launch_objective<T>(h, X, ldx, G, h->ldw, h->st, s, &e);
+  if (k < 0 || e != cudaSuccess) return cuda_fail(e, "objective gradient");
+  if (ev) CK(cudaEventRecord(ev[1], s));
+  CK((launch_gram_partial<T, T>(h->n, p, X, ldx, G, h->ldw, h->rows_per_chunk, h->nchunks,
+                                 (T*)h->part, h->st, s)));
+  if (ev) CK(cudaEventRecord(ev[2], s));
+  CK(launch_gram_finalize<T>(p, h->nchunks, (const T*)h->part, h->B, h->L0, (T*)h->Mt, (T*)h->L0t,
+                             h->feas_row, h->st, ip, s));
+  if (ev) CK(cudaEventRecord(ev[3], s));
+  CK(launch_update<T>(h->n, p, X, ldx, G, h->ldw, (T*)h->R[0], (T*)h->R[1], h->ldw,
+                      (const T*)h->Mt, (const T*)h->L0t, (const T*)h->coef, h->st, (T*)h->colpart,
+                      (T*)h->totpart, s));
+  if (ev) CK(cudaEventRecord(ev[4], s));
+  CK(launch_step_size<T>(h->nrt, h->nct, (const T*)h->colpart, (const T*)h->totpart, h->feas_row,
+                         h->fpart, h->obj.kind == PLAM_OBJ_HARTREE1D ? h->nfpart : 0, h->sums,
+                         h->ticket, h->st, h->nubuf, (T*)h->coef, h->hist, ip, s));
+  if (ev) CK(cudaEventRecord(ev[5], s));
+  CK(launch_primal_update<T>(h->n, p, X, ldx, (const T*)h->R[0], (const T*)h->R[1], h->ldw,
+                             (const T*)h->coef, h->st, variant, s));
+  if (ev) CK(cudaEventRecord(ev[6], s));
+  *nk = k + 5;
+  return PLAM_OK;
+}
+
+plam_status_t dispatch_iteration(plam_handle_s* h, void* X, int64_t ldx, int variant, int lambda2,
+                                 cudaStream_t s, int* nk, cudaEvent_t* ev = nullptr) {
+  if (h->prec == PLAM_PREC_FP64)
+    return launch_iteration<double>(h, (double*)X, ldx, variant, lambda2, s, nk, ev);
+  return launch_iteration<float>(h, (float*)X, ldx, variant, lambda2, s, nk, ev);
+}
+
+plam_status_t reset_state(plam_handle_s* h) {
+  CK(cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream));
+  CK(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), h->stream));
+  CK(cudaMemsetAsync(h->nubuf, 0, 2 * h->p * sizeof(double), h->stream));
+  CK(cudaMemsetAsync(h->coef, 0, 2 * (2 * h->p + 1) * h->esz, h->stream));
+  return PLAM_OK;
+}
+
+plam_status_t read_state(plam_handle_s* h, plam_info_t* info, int* stop) {
+  CK(cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const DevState& s = *h->st_host;
+  if (stop) *stop = s.stop;
+  if (info) {
+    info->iters = s.k;
+    info->converged = (s.stop == kConverged);
+    info->f = s.f;
+    info->kkt_rel = s.kkt;
+    info->feas = s.feas;
+    info->eta = s.eta;
+    info->K0 = s.K0;
+    info->eta0 = s.eta0;
+    info->status = (s.stop == kDiverged) ? PLAM_ERR_DIVERGED
+                   : (s.stop == kMaxit)  ? PLAM_ERR_NOT_CONVERGED
+                                         : PLAM_OK;
+  }
+  return PLAM_OK;
+}
+
+plam_status_t step_common(plam_handle_t h, void* X, int64_t ldx, plam_info_t* info, int variant,
+                          int lambda2) {
+  if (!h || !X || ldx < h->n || !aligned(X, h->esz)) return PLAM_ERR_INVALID;
+  int nk = 0;
+  plam_status_t st = dispatch_iteration(h, X, ldx, variant, lambda2, h->stream, &nk);
+  if (st != PLAM_OK) return st;
+  h->launches += nk;
+  int stop = 0;
+  if (info) {
+    info->f_orth = info->kkt_orth = info->feas_orth = NAN;
+  }
+  st = read_state(h, info, &stop);
+  if (st != PLAM_OK) return st;
+  if (stop == kDiverged) return PLAM_ERR_DIVERGED;
+  return PLAM_OK;
+}
+
+void free_handle(plam_handle_s* h) {
+  if (!h) return;
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  void* dev[] = {h->G, h->R[0], h->R[1], h->part, h->part64, h->B, h->L0, h->C, h->Mt, h->L0t,
+                 h->feas_row, h->colpart, h->totpart, h->sums, h->ticket, h->st, h->nubuf, h->coef,
+                 h->hist,
+                 h->rho, h->blk, h->y, h->fpart, h->W, h->Z, h->info, h->feas_dev, h->Qtmp,
+                 h->dotpart};
+  for (void* p : dev)
+    if (p) cudaFree(p);
+  if (h->st_host) cudaFreeHost(h->st_host);
+  if (h->info_host) cudaFreeHost(h->info_host);
+  if (h->scal_host) cudaFreeHost(h->scal_host);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+}
+
+template <typename T>
+plam_status_t orthonormalize_impl(plam_handle_s* h, const T* X, int64_t ldx, double* Xout,
+                                  int64_t ldo, int passes, double* feas) {
+  const int p = (int)h->p;
+  cudaStream_t s = h->stream;
+  const double* src64 = nullptr;
+  for (int pass = 0; pass < passes; ++pass) {
+    if (pass == 0) {
+      CK((launch_gram_partial<T, double>(h->n, p, X, ldx, (const T*)nullptr, 0, h->rows_per_chunk,
+                                          h->nchunks, h->part64, nullptr, s)));
+    } else {
+      CK((launch_gram_partial<double, double>(h->n, p, src64, h->ldw, (const double*)nullptr, 0,
+                                               h->rows_per_chunk, h->nchunks, h->part64, nullptr,
+                                               s)));
+    }
+    CK(launch_gram_reduce<double>(p, h->nchunks, 0, h->part64, h->B, nullptr, s));
+    CK(launch_cholesky_inverse(p, h->B, h->W, h->Z, h->info, s));
+    CK(cudaMemcpyAsync(h->info_host, h->info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    h->launches += 3;
+    if (*h->info_host != 0) {
+      snprintf(g_err, sizeof(g_err), "Cholesky pivot %d not positive", *h->info_host);
+      return PLAM_ERR_CHOLESKY;
+    }
+    if (pass == 0) {
+      if (passes == 1) {
+        CK(launch_apply_rinv<T>(h->n, p, X, ldx, h->Z, Xout, ldo, s));
+      } else {
+        CK(launch_apply_rinv<T>(h->n, p, X, ldx, h->Z, h->Qtmp, h->ldw, s));
+        src64 = h->Qtmp;
+      }
+    } else {
+      CK(launch_apply_rinv<double>(h->n, p, src64, h->ldw, h->Z, Xout, ldo, s));
+    }
+    h->launches += 1;
+  }
+  if (feas) {
+    CK((launch_gram_partial<double, double>(h->n, p, Xout, ldo, (const double*)nullptr, 0,
+                                             h->rows_per_chunk, h->nchunks, h->part64, nullptr, s)));
+    CK(launch_gram_reduce<double>(p, h->nchunks, 0, h->part64, h->B, nullptr, s));
+    CK(launch_feas(p, h->B, h->feas_dev, s));
+    CK(cudaMemcpyAsync(h->scal_host, h->feas_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    h->launches += 3;
+    *feas = h->scal_host[0];
+  }
+  return PLAM_OK;
+}
+
+template <typename T>
+plam_status_t energy_impl(plam_handle_s* h, const T* X, int64_t ldx, T* G, int64_t ldg, double* f) {
+  cudaError_t e;
+  const int k = launch_objective<T>(h, X, ldx, G, ldg, nullptr, h->stream, &e);
+  if (k < 0 || e != cudaSuccess) return cuda_fail(e, "objective gradient");
+  h->launches += k;
+  if (f) {
+    dot_partial_kernel<T><<<kDotBlocks, 256, 0, h->stream>>>(h->n, (int)h->p, X, ldx, G, ldg,
+                                                              h->dotpart);
+    CK(cudaGetLastError());
+    h->launches += 1;
+    const int nf = h->obj.kind == PLAM_OBJ_HARTREE1D ? h->nfpart : 0;
+    CK(cudaMemcpyAsync(h->scal_host, h->dotpart, kDotBlocks * sizeof(double), cudaMemcpyDeviceToHost,
+                       h->stream));
+    if (nf > 0)
+      CK(cudaMemcpyAsync(h->scal_host + kDotBlocks, h->fpart, nf * sizeof(double),
+                         cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    double xg = 0.0, hy = 0.0;
+    for (int i = 0; i < kDotBlocks; ++i) xg += h->scal_host[i];
+    for (int i = 0; i < nf; ++i) hy += h->scal_host[kDotBlocks + i];
+    *f = 0.5 * xg - 0.25 * (h->obj.kind == PLAM_OBJ_HARTREE1D ? h->obj.alpha : 0.0) * hy;
+  }
+  return PLAM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+plam_status_t plam_default_params(plam_params_t* prm) {
+  if (!prm) return PLAM_ERR_INVALID;
+  memset(prm, 0, sizeof(*prm));
+  prm->variant = PLAM_VARIANT_PCAL;
+  prm->lambda_rule = PLAM_LAMBDA2;
+  prm->beta = 1.0;
+  prm->eta_rule = PLAM_ETA_ABB;
+  prm->eta0 = 0.0;
+  prm->eta_gamma = 0.0;
+  prm->tol = 1e-8;
+  prm->maxit = 3000;
+  prm->precision = PLAM_PREC_FP64;
+  prm->final_orth = 1;
+  prm->graph_iters = 16;
+  return PLAM_OK;
+}
+
+plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_objective_t* obj,
+                          const plam_params_t* prm, void* stream) {
+  if (!out) return PLAM_ERR_INVALID;
+  *out = nullptr;
+  if (!obj || p < 1 || n < 2 * p || p > 65535) return PLAM_ERR_INVALID;
+  if (validate_params(prm) != PLAM_OK) return PLAM_ERR_INVALID;
+  const size_t esz = prm->precision == PLAM_PREC_FP64 ? 8 : 4;
+  switch (obj->kind) {
+    case PLAM_OBJ_DENSE:
+      if (!obj->A || obj->lda < n || !aligned(obj->A, esz)) return PLAM_ERR_INVALID;
+      break;
+    case PLAM_OBJ_HARTREE1D:
+      if (!std::isfinite(obj->alpha) || !std::isfinite(obj->quad_scale)) return PLAM_ERR_INVALID;
+      break;
+    case PLAM_OBJ_STENCIL3D:
+      if (obj->nx < 1 || obj->ny < 1 || obj->nz < 1 ||
+          (int64_t)obj->nx * obj->ny * obj->nz != n || (obj->V && !aligned(obj->V, esz)))
+        return PLAM_ERR_INVALID;
+      break;
+    default:
+      return PLAM_ERR_INVALID;
+  }
+  plam_handle_s* h = new (std::nothrow) plam_handle_s();
+  if (!h) return PLAM_ERR_NOMEM;
+  h->n = n;
+  h->p = p;
+  h->obj = *obj;
+  h->prm = *prm;
+  h->stream = (cudaStream_t)stream;
+  h->prec = prm->precision;
+  h->esz = esz;
+  h->ldw = round_up(n, 32);
+  const int pi = (int)p;
+  const int nt = (pi + kTile - 1) / kTile;
+  const int tiles = nt * (nt + 1) / 2 + nt * nt;
+  const int64_t target_ctas = 2 * 152;
+  int64_t nch = (target_ctas + tiles - 1) / tiles;
+  const int64_t max_ch = (n + kKStep - 1) / kKStep;
+  if (nch > max_ch) nch = max_ch;
+  if (nch < 1) nch = 1;
+  h->rows_per_chunk = round_up((n + nch - 1) / nch, kKStep);
+  h->nchunks = (int)((n + h->rows_per_chunk - 1) / h->rows_per_chunk);
+  h->nrt = (int)((n + kTile - 1) / kTile);
+  h->nct = nt;
+  h->hist_cap = prm->maxit + 2;
+  const size_t np_bytes = (size_t)h->ldw * p * esz;
+  const size_t pp = (size_t)p * p;
+  auto alloc = [&](void** ptr, size_t bytes) -> bool {
+    return cudaMalloc(ptr, bytes == 0 ? 16 : bytes) == cudaSuccess;
+  };
+  bool ok = alloc(&h->G, np_bytes) && alloc(&h->R[0], np_bytes) && alloc(&h->R[1], np_bytes) &&
+            alloc(&h->part, (size_t)h->nchunks * 2 * pp * esz) &&
+            alloc((void**)&h->part64, (size_t)h->nchunks * 2 * pp * sizeof(double)) &&
+            alloc((void**)&h->B, pp * sizeof(double)) && alloc((void**)&h->L0, pp * sizeof(double)) &&
+            alloc((void**)&h->C, pp * sizeof(double)) && alloc(&h->Mt, pp * esz) &&
+            alloc(&h->L0t, pp * esz) && alloc((void**)&h->feas_row, p * sizeof(double)) &&
+            alloc(&h->colpart, (size_t)h->nrt * kColDots * p * esz) &&
+            alloc(&h->totpart, (size_t)h->nrt * h->nct * kTotDots * esz) &&
+            alloc((void**)&h->sums, (kColDots * p + kTotDots) * sizeof(double)) &&
+            alloc((void**)&h->ticket, sizeof(unsigned int)) &&
+            alloc((void**)&h->st, sizeof(DevState)) &&
+            alloc((void**)&h->nubuf, 2 * p * sizeof(double)) &&
+            alloc(&h->coef, 2 * (2 * p + 1) * esz) &&
+            alloc((void**)&h->hist, (size_t)h->hist_cap * 5 * sizeof(double)) &&
+            alloc((void**)&h->W, pp * sizeof(double)) && alloc((void**)&h->Z, pp * sizeof(double)) &&
+            alloc((void**)&h->info, sizeof(int)) && alloc((void**)&h->feas_dev, sizeof(double)) &&
+            alloc((void**)&h->dotpart, kDotBlocks * sizeof(double));
+  if (ok && obj->kind == PLAM_OBJ_HARTREE1D) {
+    h->nfpart = hartree_blocks(n);
+    ok = alloc((void**)&h->rho, n * sizeof(double)) && alloc((void**)&h->y, n * sizeof(double)) &&
+         alloc((void**)&h->blk, 2 * (size_t)h->nfpart * sizeof(double)) &&
+         alloc((void**)&h->fpart, (size_t)h->nfpart * sizeof(double));
+  }
+  if (ok && prm->final_orth == 2) ok = alloc((void**)&h->Qtmp, (size_t)h->ldw * p * sizeof(double));
+  if (ok) {
+    ok = cudaMallocHost((void**)&h->st_host, sizeof(DevState)) == cudaSuccess &&
+         cudaMallocHost((void**)&h->info_host, sizeof(int)) == cudaSuccess &&
+         cudaMallocHost((void**)&h->scal_host,
+                        (kDotBlocks + (size_t)h->nfpart + 8) * sizeof(double)) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    free_handle(h);
+    return PLAM_ERR_NOMEM;
+  }
+  {
+    cudaError_t e = preload_gram_kernels();
+    if (e == cudaSuccess) e = preload_update_kernels();
+    if (e == cudaSuccess) e = preload_objective_kernels();
+    if (e != cudaSuccess) {
+      free_handle(h);
+      return cuda_fail(e, "kernel preload");
+    }
+  }
+  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    free_handle(h);
+    return cuda_fail(cudaGetLastError(), "cudaStreamCreate");
+  }
+  if (reset_state(h) != PLAM_OK || cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    free_handle(h);
+    return PLAM_ERR_CUDA;
+  }
+  *out = h;
+  return PLAM_OK;
+}
+
+plam_status_t plam_destroy(plam_handle_t h) {
+  if (!h) return PLAM_ERR_INVALID;
+  cudaStreamSynchronize(h->stream);
+  free_handle(h);
+  return PLAM_OK;
+}
+
+plam_status_t plam_reset(plam_handle_t h) {
+  if (!h) return PLAM_ERR_INVALID;
+  return reset_state(h);
+}
+
+plam_status_t plam_step(plam_handle_t h, void* X, int64_t ldx, plam_info_t* info) {
+  return step_common(h, X, ldx, info, PLAM_VARIANT_PLAM, 0);
+}
+
+plam_status_t pcal_step(plam_handle_t h, void* X, int64_t ldx, plam_info_t* info) {
+  if (!h) return PLAM_ERR_INVALID;
+  return step_common(h, X, ldx, info, PLAM_VARIANT_PCAL, h->prm.lambda_rule == PLAM_LAMBDA2);
+}
+
+plam_status_t plam_orthonormalize(plam_handle_t h, const void* X, int64_t ldx, double* Xout,
+                                  int64_t ldo, int passes, double* feas) {
+  if (!h || !X || !Xout || ldx < h->n || ldo < h->n || passes < 1 || passes > 2)
+    return PLAM_ERR_INVALID;
+  if (!aligned(X, h->esz) || !aligned(Xout, 8)) return PLAM_ERR_INVALID;
+  if (h->prec == PLAM_PREC_FP32 && (const void*)Xout == X) return PLAM_ERR_INVALID;
+  if (passes == 2 && !h->Qtmp) {
+    if (cudaMalloc((void**)&h->Qtmp, (size_t)h->ldw * h->p * sizeof(double)) != cudaSuccess)
+      return PLAM_ERR_NOMEM;
+  }
+  if (h->prec == PLAM_PREC_FP64)
+    return orthonormalize_impl<double>(h, (const double*)X, ldx, Xout, ldo, passes, feas);
+  return orthonormalize_impl<float>(h, (const float*)X, ldx, Xout, ldo, passes, feas);
+}
+
+plam_status_t plam_solve(plam_handle_t h, void* X, int64_t ldx, double* Xout, int64_t ldo,
+                         plam_info_t* info) {
+  if (!h || !X || ldx < h->n || !aligned(X, h->esz)) return PLAM_ERR_INVALID;
+  if (Xout && ldo < h->n) return PLAM_ERR_INVALID;
+  const int variant = h->prm.variant;
+  const int lambda2 = (variant == PLAM_VARIANT_PCAL && h->prm.lambda_rule == PLAM_LAMBDA2);
+  plam_status_t st = reset_state(h);
+  if (st != PLAM_OK) return st;
+  const int gi = h->prm.graph_iters;
+  int stop = kRunning;
+  if (gi > 0) {
+    if (!h->graph || h->graph_X != X || h->graph_ldx != ldx || h->graph_variant != variant) {
+      if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+      }
+      // capture graph_iters iterations on the private capture stream
+      CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+      int total = 0;
+      for (int i = 0; i < gi; ++i) {
+        int nk = 0;
+        st = dispatch_iteration(h, X, ldx, variant, lambda2, h->cap_stream, &nk);
+        if (st != PLAM_OK) break;
+        total += nk;
+      }
+      cudaGraph_t g = nullptr;
+      cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
+      if (st != PLAM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+      ce = cudaGraphInstantiate(&h->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+      h->graph_X = X;
+      h->graph_ldx = ldx;
+      h->graph_variant = variant;
+      h->graph_kernels = total;
+    }
+    const int max_launch = h->prm.maxit / gi + 2;
+    for (int l = 0; l < max_launch; ++l) {
+      CK(cudaGraphLaunch(h->graph, h->stream));
+      h->launches += h->graph_kernels;
+      st = read_state(h, nullptr, &stop);
+      if (st != PLAM_OK) return st;
+      if (stop != kRunning) break;
+    }
+  } else {
+    for (int it = 0; it <= h->prm.maxit; ++it) {
+      int nk = 0;
+      st = dispatch_iteration(h, X, ldx, variant, lambda2, h->stream, &nk);
+      if (st != PLAM_OK) return st;
+      h->launches += nk;
+      if ((it & 15) == 15 || it == h->prm.maxit) {
+        st = read_state(h, nullptr, &stop);
+        if (st != PLAM_OK) return st;
+        if (stop != kRunning) break;
+      }
+    }
+    st = read_state(h, nullptr, &stop);
+    if (st != PLAM_OK) return st;
+  }
+  plam_info_t tmp;
+  plam_info_t* inf = info ? info : &tmp;
+  st = read_state(h, inf, &stop);
+  if (st != PLAM_OK) return st;
+  inf->f_orth = inf->kkt_orth = inf->feas_orth = NAN;
+  if (stop == kDiverged) return PLAM_ERR_DIVERGED;
+  if (h->prm.final_orth > 0 && Xout) {
+    double feas = NAN;
+    st = plam_orthonormalize(h, X, ldx, Xout, ldo, h->prm.final_orth, &feas);
+    if (st != PLAM_OK) return st;
+    inf->feas_orth = feas;
+  }
+  return stop == kConverged ? PLAM_OK : PLAM_ERR_NOT_CONVERGED;
+}
+
+plam_status_t plam_energy_grad(plam_handle_t h, const void* X, int64_t ldx, void* G, int64_t ldg,
+                               double* f) {
+  if (!h || !X || !G || ldx < h->n || ldg < h->n) return PLAM_ERR_INVALID;
+  if (!aligned(X, h->esz) || !aligned(G, h->esz)) return PLAM_ERR_INVALID;
+  if (h->prec == PLAM_PREC_FP64)
+    return energy_impl<double>(h, (const double*)X, ldx, (double*)G, ldg, f);
+  return energy_impl<float>(h, (const float*)X, ldx, (float*)G, ldg, f);
+}
+
+plam_status_t plam_grams(plam_handle_t h, const void* X, int64_t ldx, const void* G, int64_t ldg,
+                         double* B, double* C) {
+  if (!h || !X || !B || ldx < h->n || (G && (ldg < h->n || !C))) return PLAM_ERR_INVALID;
+  const int p = (int)h->p;
+  if (h->prec == PLAM_PREC_FP64) {
+    CK((launch_gram_partial<double, double>(h->n, p, (const double*)X, ldx, (const double*)G, ldg,
+                                             h->rows_per_chunk, h->nchunks, (double*)h->part,
+                                             nullptr, h->stream)));
+    CK(launch_gram_reduce<double>(p, h->nchunks, G != nullptr, (const double*)h->part, B, C,
+                                  h->stream));
+  } else {
+    CK((launch_gram_partial<float, float>(h->n, p, (const float*)X, ldx, (const float*)G, ldg,
+                                           h->rows_per_chunk, h->nchunks, (float*)h->part, nullptr,
+                                           h->stream)));
+    CK(launch_gram_reduce<float>(p, h->nchunks, G != nullptr, (const float*)h->part, B, C,
+                                 h->stream));
+  }
+  h->launches += 2;
+  CK(cudaStreamSynchronize(h->stream));
+  return PLAM_OK;
+}
+
+plam_status_t plam_time_kernels(plam_handle_t h, void* X, int64_t ldx, int iters, double* ms,
+                                int* done) {
+  if (!h || !X || !ms || !done || iters < 0 || ldx < h->n || !aligned(X, h->esz))
+    return PLAM_ERR_INVALID;
+  const int variant = h->prm.variant;
+  const int lambda2 = (variant == PLAM_VARIANT_PCAL && h->prm.lambda_rule == PLAM_LAMBDA2);
+  cudaEvent_t ev[7];
+  for (int i = 0; i < 7; ++i) CK(cudaEventCreate(&ev[i]));
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  int it = 0;
+  plam_status_t st = PLAM_OK;
+  for (; it < iters; ++it) {
+    int stop = 0;
+    st = read_state(h, nullptr, &stop);
+    if (st != PLAM_OK || stop != kRunning) break;
+    int nk = 0;
+    st = dispatch_iteration(h, X, ldx, variant, lambda2, h->stream, &nk, ev);
+    if (st != PLAM_OK) break;
+    h->launches += nk;
+    cudaError_t e = cudaEventSynchronize(ev[6]);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "cudaEventSynchronize");
+      break;
+    }
+    for (int i = 0; i < 6; ++i) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+      acc[i] += t;
+    }
+  }
+  for (int i = 0; i < 7; ++i) cudaEventDestroy(ev[i]);
+  for (int i = 0; i < 6; ++i) ms[i] = it > 0 ? acc[i] / it : 0.0;
+  *done = it;
+  return st;
+}
+
+plam_status_t plam_history(plam_handle_t h, double* out, int cap, int* count) {
+  if (!h || !out || !count || cap < 0) return PLAM_ERR_INVALID;
+  CK(cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  int nrec = h->st_host->nrec;
+  if (nrec > cap) nrec = cap;
+  if (nrec > 0)
+    CK(cudaMemcpy(out, h->hist, (size_t)nrec * 5 * sizeof(double), cudaMemcpyDeviceToHost));
+  *count = nrec;
+  return PLAM_OK;
+}
+
+int64_t plam_kernel_launches(plam_handle_t h) { return h ? h->launches : -1; }
+
+const char* plam_last_error(void) { return g_err; }
+
+int plam_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,125 @@
+// Shared declarations of the PLAM / PCAL CUDA kernels (sm_103a).
+//
+// Layout conventions: every n x p matrix is column-major with a leading
+// dimension; p x p matrices are column-major with leading dimension p.  The
+// element ("storage") type T is double in FP64 mode and float in FP32 mode.
+// FP32 mode keeps double arithmetic to the O(p^2) algebra and the scalars,
+// because GB300 runs FP64 at 1/64 of the FP32 rate.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace plam {
+
+constexpr int kThreads = 256;     // threads of the tiled kernels (16 x 16 micro-tile grid)
+constexpr int kTile = 64;         // output tile edge of the tiled kernels
+constexpr int kKStep = 32;        // rows (Gram) or inner index (update) per shared-memory stage
+constexpr int kFlushRows = 256;   // FP32 running sums are flushed into a compensated sum after this many terms
+
+// Stop codes written by the step-size kernel.
+enum StopCode { kRunning = 0, kConverged = 1, kMaxit = 2, kDiverged = 3 };
+
+// Per-solve device state (one instance per handle, in device memory).
+struct DevState {
+  int k;          // updates performed
+  int stop;       // StopCode
+  int nrec;       // history records written
+  int eta_rule_used;
+  double K0;      // ||G0 - X0 Psi(G0^T X0)||_F
+  double eta;     // eta used by the latest update
+  double eta_prev;
+  double eta0;
+  double kkt;     // relative KKT value at the latest evaluated iterate
+  double feas;    // ||X^T X - I||_F there
+  double f;       // f there
+  double ss, sy, yy;  // latest Barzilai-Borwein inner products
+};
+
+// Parameters of one iteration, passed by value.
+struct IterParams {
+  int64_t n;
+  int p;
+  int variant;      // 0 PLAM, 1 PCAL
+  int lambda2;      // 1: PCAL multiplier of eq. (lambda2)
+  int eta_rule;     // PLAM_ETA_*
+  int maxit;
+  int hist_cap;     // records available in the history buffer
+  double beta;
+  double eta0_user; // <= 0: automatic
+  double gamma;     // constant rule
+  double tol;
+  double hartree_alpha;  // f correction term for the Hartree objective (0 otherwise)
+};
+
+// Number of per-column dot products written by the update kernel and the
+// number of whole-matrix sums (see update_kernel).
+constexpr int kColDots = 3;   // ||X_c||^2, <X_c,R_c>, ||R_c||^2
+constexpr int kTotDots = 6;   // <S,S>, <S,Y>, <Y,Y>, ||K||^2, ||G||^2, <X,G>
+
+// ---------------------------------------------------------------- launchers
+// Each returns the cudaError_t of the launch (cudaGetLastError).
+
+// part: nchunks x 2p x p partial Grams in the arithmetic type T (Tin: input type).
+template <typename Tin, typename T>
+cudaError_t launch_gram_partial(int64_t n, int p, const Tin* X, int64_t ldx, const Tin* G,
+                                int64_t ldg, int64_t rows_per_chunk, int nchunks, T* part,
+                                const DevState* st, cudaStream_t s);
+template <typename T>
+cudaError_t launch_gram_reduce(int p, int nchunks, int with_g, const T* part, double* B,
+                               double* C, cudaStream_t s);
+template <typename T>
+cudaError_t launch_gram_finalize(int p, int nchunks, const T* part, double* B, double* L0,
+                                 T* Mt, T* L0t, double* feas_row, const DevState* st,
+                                 IterParams prm, cudaStream_t s);
+
+// R0/R1: the two residual buffers (R^k goes to buffer k mod 2).  nubuf: 2 x p
+// column norms and coef: 2 x (2p + 1) scales [1/eta, 1/nu_c, 1 - nu_c] in the
+// storage type (iteration k writes buffer k mod 2).  colpart: nrt x 3 x p,
+// totpart: nrt x nct x 6 partial sums in the storage type.
+template <typename T>
+cudaError_t launch_update(int64_t n, int p, const T* X, int64_t ldx, const T* G, int64_t ldg,
+                          T* R0, T* R1, int64_t ldr, const T* Mt, const T* L0t, const T* coef,
+                          const DevState* st, T* colpart, T* totpart, cudaStream_t s);
+// sums: 3p + 6 doubles of scratch; ticket: one zero-initialised counter.
+template <typename T>
+cudaError_t launch_step_size(int nrt, int nct, const T* colpart, const T* totpart,
+                             const double* feas_row, const double* fpart, int nfpart, double* sums,
+                             unsigned int* ticket, DevState* st, double* nubuf, T* coef,
+                             double* hist, IterParams prm, cudaStream_t s);
+template <typename T>
+cudaError_t launch_primal_update(int64_t n, int p, T* X, int64_t ldx, const T* R0, const T* R1,
+                                 int64_t ldr, const T* coef, const DevState* st, int variant,
+                                 cudaStream_t s);
+
+// Objectives.  `fpart` receives per-block partial sums that the step-size
+// kernel adds into f (Hartree: rho^T y); may be null.
+template <typename T>
+cudaError_t launch_dense_grad(int64_t n, int p, const T* A, int64_t lda, const T* X, int64_t ldx,
+                              T* G, int64_t ldg, const DevState* st, cudaStream_t s);
+template <typename T>
+cudaError_t launch_hartree_grad(int64_t n, int p, double alpha, double q, const T* X, int64_t ldx,
+                                T* G, int64_t ldg, double* rho, double* blk, double* y,
+                                double* fpart, const DevState* st, cudaStream_t s);
+int hartree_blocks(int64_t n);
+template <typename T>
+cudaError_t launch_stencil_grad(int nx, int ny, int nz, int p, const T* V, const T* X, int64_t ldx,
+                                T* G, int64_t ldg, const DevState* st, cudaStream_t s);
+
+// Final orthonormalisation.  W: p x p work (B is copied into it), Z: p x p
+// output R^{-1} (upper triangular), info: 0 or 1 + the failing pivot.
+cudaError_t launch_cholesky_inverse(int p, const double* B, double* W, double* Z, int* info,
+                                    cudaStream_t s);
+template <typename T>
+cudaError_t launch_apply_rinv(int64_t n, int p, const T* X, int64_t ldx, const double* Z,
+                              double* Q, int64_t ldq, cudaStream_t s);
+// out[0] = ||B - I||_F (one CTA).
+cudaError_t launch_feas(int p, const double* B, double* out, cudaStream_t s);
+
+// Force the module load of every kernel (lazy loading must not happen inside
+// a stream capture).
+cudaError_t preload_gram_kernels();
+cudaError_t preload_update_kernels();
+cudaError_t preload_objective_kernels();
+
+}  // namespace plam

@@ -1,0 +1,41 @@
+"""Writes the stored expected values under tests/golden/ by calling only the oracle.
+
+  hartree1d_n20000_p50_optimum.json   f* of the 1D Hartree workload (n = 20000, p = 50,
+                                      alpha = 1, q = 1/4, seeded orthonormal start): the
+                                      oracle's PCAL (beta = 1e3) run to relative KKT 1e-9,
+                                      then orthonormalised (Householder QR).
+
+Run from the repository root:  python tests/golden/make_golden.py
+"""
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+from oracle import objectives as oo  # noqa: E402
+from oracle import plam as op  # noqa: E402
+from workloads import workload_hartree1d  # noqa: E402
+
+
+def hartree_optimum():
+    w = workload_hartree1d()
+    obj = oo.HartreeObjective(w.n, w.alpha, w.quad_scale)
+    t0 = time.time()
+    r = op.solve(obj, w.X0, variant="pcal", beta=1000.0, tol=1e-9, maxit=20000, record=False)
+    assert r.converged
+    return {"workload": w.name, "n": w.n, "p": w.p, "alpha": w.alpha, "quad_scale": w.quad_scale,
+            "beta": 1000.0, "tol_kkt_rel": 1e-9, "f_star": r.f_orth, "kkt_orth": r.kkt_orth,
+            "feas_orth": r.feas_orth, "K0": r.K0, "oracle_iters": r.iters,
+            "oracle_seconds": round(time.time() - t0, 1),
+            "source": "oracle/plam.py solve() run by tests/golden/make_golden.py"}
+
+
+if __name__ == "__main__":
+    d = hartree_optimum()
+    with open(os.path.join(HERE, "hartree1d_n20000_p50_optimum.json"), "w") as fh:
+        json.dump(d, fh, indent=1)
+    print(d)

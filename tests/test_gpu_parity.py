@@ -1,0 +1,402 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (derived from the arithmetic; FP64 unit roundoff 1.1e-16, FP32 6e-8):
+  FP64 mode  single kernels rel 1e-12 (Hartree gradient 1e-10: the oracle's banded LU
+             solve of L y = rho carries kappa(L) u ~ (4 n^2/pi^2) u relative error),
+             one full iteration rel 1e-11, eta over the first 20 iterations rel 1e-9,
+             converged objective rel 1e-10 against the exact or tightly converged optimum
+  FP32 mode  Grams 2e-6 of the entry scale, gradients rel 2e-6, converged objective
+             rel 1e-6 against the optimum (the bound the benchmark metric states)
+Iteration counts of full solves are compared within +-25%: the Barzilai-Borwein
+sequence is chaotic in rounding (the oracle itself moves from 374 to 343..403
+iterations on the dense trace problem when X0 is perturbed by 1e-16..1e-14).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import kernels as ok
+from oracle import objectives as oo
+from oracle import plam as op
+from tests.gpu_helpers import gpu_solver, rel_err, to_dev, to_host
+from workloads import (gaussian_symmetric, orthonormal_start, rng_for, workload_dense_trace,
+                       workload_hartree1d, workload_stencil3d)
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+
+torch = pytest.importorskip("torch")
+
+
+def _dense(n, p, seed=0):
+    w = workload_dense_trace(n, p)
+    return w
+
+
+# ---------------------------------------------------------------- Grams (split-K, fixed order)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,p", [(1003, 1), (1003, 3), (2051, 20), (4099, 50), (3001, 65), (2600, 129)])
+def test_grams_match_definition(precision, n, p):
+    rng = np.random.default_rng(n + p)
+    X = rng.standard_normal((n, p))
+    G = rng.standard_normal((n, p))
+    if precision == "fp32":
+        X = X.astype(np.float32).astype(np.float64)
+        G = G.astype(np.float32).astype(np.float64)
+    w = workload_hartree1d(n=n, p=p) if 2 * p <= n else None
+    s = gpu_solver(w, precision)
+    Xd, Gd = to_dev(X, s), to_dev(G, s)
+    B, Cm = s.grams(Xd, Gd)
+    Bref, Cref = ok.grams(X, G)
+    scale = np.sqrt(n)   # entries are sums of n products of unit-variance numbers
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    assert np.abs(B.cpu().numpy() - Bref).max() <= tol * scale * max(1.0, np.abs(Bref).max() / scale)
+    assert np.abs(Cm.cpu().numpy() - Cref).max() <= tol * scale * max(1.0, np.abs(Cref).max() / scale)
+    # bitwise reproducible (fixed reduction order)
+    B2, C2 = s.grams(Xd, Gd)
+    assert torch.equal(B, B2) and torch.equal(Cm, C2)
+    s.close()
+
+
+# ---------------------------------------------------------------- objectives
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("kind", ["dense", "hartree1d", "stencil3d"])
+def test_energy_grad_matches_oracle(precision, kind):
+    if kind == "dense":
+        w = workload_dense_trace(333, 7)
+    elif kind == "hartree1d":
+        w = workload_hartree1d(n=3001, p=9)
+    else:
+        w = workload_stencil3d(m=11, p=5)
+    obj = oo.objective_for(w)
+    X = w.X0 + 0.01 * rng_for(12, 3).standard_normal(w.X0.shape)
+    if precision == "fp32":
+        X = X.astype(np.float32).astype(np.float64)
+    s = gpu_solver(w, precision)
+    Xd = to_dev(X, s)
+    Gd = s.new_matrix()
+    f = s.energy_grad(Xd, Gd)
+    G = to_host(Gd, w.n)
+    if precision == "fp32" and kind == "dense":
+        obj = oo.TraceObjective(w.A.astype(np.float32).astype(np.float64))
+    if precision == "fp32" and kind == "stencil3d":
+        obj = oo.Stencil3DObjective(w.m, w.V.astype(np.float32).astype(np.float64))
+    Gref = obj.grad(X)
+    fref = obj.value(X)
+    tol = (1e-10 if kind == "hartree1d" else 1e-12) if precision == "fp64" else 2e-6
+    assert rel_err(G, Gref) <= tol
+    assert abs(f - fref) <= tol * max(1.0, abs(fref)) * 10
+    s.close()
+
+
+# ---------------------------------------------------------------- one iteration
+
+
+@pytest.mark.parametrize("variant,rule", [("plam", "lambda1"), ("pcal", "lambda2"), ("pcal", "lambda1")])
+@pytest.mark.parametrize("n,p", [(301, 7), (1000, 20), (777, 65)])
+def test_one_iteration_matches_oracle_fp64(variant, rule, n, p):
+    w = workload_dense_trace(n, p)
+    obj = oo.TraceObjective(w.A)
+    X0 = w.X0 + 0.02 * rng_for(13, 1).standard_normal(w.X0.shape)   # infeasible start
+    beta = 1.5
+    ref = op.solve(obj, X0, variant=variant, beta=beta, lambda_rule=rule, tol=0.0, maxit=1)
+    s = gpu_solver(w, "fp64", variant=variant, lambda_rule=rule, beta=beta, tol=0.0, maxit=1)
+    Xd = to_dev(X0, s)
+    st, info = s.step(Xd, variant)
+    assert st == 0
+    X1 = to_host(Xd, n)
+    assert rel_err(X1, ref.X) <= 1e-11
+    h0 = ref.history[0]
+    assert abs(info.kkt_rel - h0.kkt) <= 1e-12
+    assert abs(info.feas - h0.feas) <= 1e-11 * max(1.0, h0.feas)
+    assert abs(info.f - h0.f) <= 1e-12 * max(1.0, abs(h0.f))
+    assert abs(info.eta - h0.eta) <= 1e-12 * h0.eta
+    assert info.iters == 1
+    s.close()
+
+
+@pytest.mark.parametrize("variant", ["plam", "pcal"])
+def test_first_twenty_step_sizes_match_oracle_fp64(variant):
+    """The ABB sequence (Section 5.1) is unpinned by the paper; pin GPU vs oracle on identical inputs."""
+    w = workload_dense_trace(500, 20)
+    obj = oo.TraceObjective(w.A)
+    ref = op.solve(obj, w.X0, variant=variant, beta=1.0, tol=0.0, maxit=20)
+    s = gpu_solver(w, "fp64", variant=variant, beta=1.0, tol=0.0, maxit=20, final_orth=0)
+    Xd = to_dev(w.X0, s)
+    st, info = s.solve(Xd)
+    hist = s.history()
+    assert hist.shape[0] == 21
+    eta_ref = np.array([h.eta for h in ref.history[:20]])
+    kkt_ref = np.array([h.kkt for h in ref.history])
+    f_ref = np.array([h.f for h in ref.history])
+    np.testing.assert_allclose(hist[:20, 4], eta_ref, rtol=1e-9)
+    np.testing.assert_allclose(hist[:, 2], kkt_ref, rtol=1e-8)
+    np.testing.assert_allclose(hist[:, 1], f_ref, rtol=1e-11)
+    assert rel_err(to_host(Xd, w.n), ref.X) <= 1e-9
+    s.close()
+
+
+# ---------------------------------------------------------------- full solves
+
+
+@pytest.mark.parametrize("variant", ["plam", "pcal"])
+def test_dense_trace_solve_fp64(variant):
+    """Configuration 1: n=500, p=20, beta=1, ABB, KKT 1e-8; objective = 1/2 sum of the 20 smallest eigenvalues."""
+    w = workload_dense_trace(500, 20)
+    obj = oo.TraceObjective(w.A)
+    ev = np.linalg.eigvalsh(w.A)
+    ref = op.solve(obj, w.X0, variant=variant, beta=1.0, tol=1e-8, maxit=3000, record=False)
+    s = gpu_solver(w, "fp64", variant=variant, beta=1.0, tol=1e-8, maxit=3000, final_orth=1)
+    Xd = to_dev(w.X0, s)
+    Qd = s.new_matrix(dtype=torch.float64)
+    st, info = s.solve(Xd, Qd)
+    assert st == 0 and info.converged and info.kkt_rel < 1e-8
+    assert abs(info.iters - ref.iters) <= 0.25 * ref.iters
+    Q = to_host(Qd, w.n)
+    fstar = 0.5 * ev[:20].sum()
+    assert abs(obj.value(Q) - fstar) <= 1e-10 * abs(fstar)
+    assert info.feas_orth <= 1e-12
+    assert op.feasibility(Q) <= 1e-12
+    # subspaces: each is within ||KKT|| / gap of the exact eigenspace (Davis-Kahan)
+    Qr = ref.X_orth
+    gap = ev[20] - ev[19]
+    bound = 2.0 * (info.kkt_rel + ref.kkt_orth) * ref.K0 / gap
+    assert np.linalg.norm(Q - Qr @ (Qr.T @ Q), 2) <= bound
+    s.close()
+
+
+@pytest.fixture(scope="module")
+def hartree_2000_optimum():
+    """f* of the n = 2000, p = 50 Hartree problem: the oracle converged to KKT 1e-10."""
+    w = workload_hartree1d(n=2000, p=50)
+    obj = oo.HartreeObjective(w.n, w.alpha, w.quad_scale)
+    ref = op.solve(obj, w.X0, variant="pcal", beta=1000.0, tol=1e-10, maxit=20000, record=False)
+    assert ref.converged
+    return w, obj, ref
+
+
+@pytest.mark.parametrize("precision,tol,ftol", [("fp64", 1e-9, 1e-10), ("fp32", 1e-6, 1e-6),
+                                                ("fp32", 1e-7, 1e-7)])
+def test_hartree_solve_reduced(hartree_2000_optimum, precision, tol, ftol):
+    """Configuration 2 at n = 2000: PCAL, beta = 1e3; objective vs the optimum f*."""
+    w, obj, ref = hartree_2000_optimum
+    s = gpu_solver(w, precision, variant="pcal", beta=1000.0, tol=tol, maxit=20000, final_orth=1)
+    Xd = to_dev(w.X0, s)
+    Qd = s.new_matrix(dtype=torch.float64)
+    st, info = s.solve(Xd, Qd)
+    assert st == 0 and info.converged
+    Q = to_host(Qd, w.n)
+    assert abs(obj.value(Q) - ref.f_orth) <= ftol * abs(ref.f_orth)
+    assert info.feas_orth <= 1e-12 and op.feasibility(Q) <= 1e-12
+    s.close()
+
+
+def _hartree_golden():
+    import json
+    import os
+    return json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "hartree1d_n20000_p50_optimum.json")))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("tol,ftol", [(1e-6, 1e-4), (1e-7, 1e-6)])
+def test_hartree_full_size(precision, tol, ftol):
+    """The benchmark workload (n = 20000, p = 50) against the stored optimum f* (oracle at KKT 1e-9).
+    At relative KKT 1e-6 the objective is only fixed to ~4e-5 (the oracle itself stops at
+    f = 2786.9595 vs f* = 2786.8454); the error falls quadratically with the tolerance, and at
+    1e-7 the mixed path must meet the 1e-6 objective bound."""
+    g = _hartree_golden()
+    w = workload_hartree1d()
+    obj = oo.HartreeObjective(w.n, w.alpha, w.quad_scale)
+    s = gpu_solver(w, precision, variant="pcal", beta=1000.0, tol=tol, maxit=3000, final_orth=1)
+    Xd = to_dev(w.X0, s)
+    Qd = s.new_matrix(dtype=torch.float64)
+    st, info = s.solve(Xd, Qd)
+    assert st == 0 and info.converged
+    Q = to_host(Qd, w.n)
+    assert abs(obj.value(Q) - g["f_star"]) <= ftol * abs(g["f_star"])
+    assert op.feasibility(Q) <= 1e-12
+    G = obj.grad(Q)
+    assert np.linalg.norm(op.kkt_residual(G, Q)) / g["K0"] <= 2.0 * tol
+    assert abs(info.K0 - g["K0"]) <= 1e-5 * g["K0"]
+    s.close()
+
+
+def test_stencil3d_constant_potential_closed_form():
+    m, p, c = 8, 4, 0.37
+    one = [2 - 2 * math.cos(math.pi * t / (m + 1)) for t in range(1, m + 1)]
+    ev = sorted(one[a] + one[b] + one[d] + c for a in range(m) for b in range(m) for d in range(m))
+    from workloads import Workload
+    w = Workload(name="const", kind="stencil3d", n=m ** 3, p=p, m=m, V=np.full(m ** 3, c),
+                 X0=orthonormal_start(m ** 3, p, rng_for(14, 1)))
+    s = gpu_solver(w, "fp64", variant="pcal", beta=12.47, tol=1e-10, maxit=20000, final_orth=1)
+    Xd = to_dev(w.X0, s)
+    Qd = s.new_matrix(dtype=torch.float64)
+    st, info = s.solve(Xd, Qd)
+    assert st == 0
+    Q = to_host(Qd, w.n)
+    obj = oo.Stencil3DObjective(m, w.V)
+    assert abs(obj.value(Q) - 0.5 * sum(ev[:p])) <= 1e-9 * 0.5 * sum(ev[:p])
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_stencil3d_random_potential_matches_oracle(precision):
+    w = workload_stencil3d(m=12, p=6)
+    obj = oo.Stencil3DObjective(w.m, w.V)
+    beta = obj.hess_norm_bound() + 0.1
+    tol = 1e-8 if precision == "fp64" else 1e-5
+    ref = op.solve(obj, w.X0, variant="pcal", beta=beta, tol=tol, maxit=20000, record=False)
+    s = gpu_solver(w, precision, variant="pcal", beta=beta, tol=tol, maxit=20000, final_orth=1)
+    Xd = to_dev(w.X0, s)
+    Qd = s.new_matrix(dtype=torch.float64)
+    st, info = s.solve(Xd, Qd)
+    assert st == 0
+    Q = to_host(Qd, w.n)
+    ftol = 1e-10 if precision == "fp64" else 1e-6
+    ev = np.linalg.eigvalsh(obj.H.toarray())
+    assert abs(obj.value(Q) - 0.5 * ev[:w.p].sum()) <= ftol * abs(0.5 * ev[:w.p].sum()) * 10
+    assert abs(obj.value(Q) - ref.f_orth) <= ftol * abs(ref.f_orth) * 10
+    s.close()
+
+
+# ---------------------------------------------------------------- orthonormalisation
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("passes", [1, 2])
+def test_orthonormalize_matches_householder_qr(precision, passes):
+    n, p = 1501, 33
+    rng = np.random.default_rng(7)
+    X = orthonormal_start(n, p, rng) + 1e-3 * rng.standard_normal((n, p))
+    if precision == "fp32":
+        X = X.astype(np.float32).astype(np.float64)
+    w = workload_hartree1d(n=n, p=p)
+    s = gpu_solver(w, precision)
+    Xd = to_dev(X, s)
+    Qd = s.new_matrix(dtype=torch.float64)
+    feas = s.orthonormalize(Xd, Qd, passes=passes)
+    Q = to_host(Qd, n)
+    Qref = op.orthonormalize(X)
+    assert np.abs(Q - Qref).max() <= 1e-12
+    assert feas <= 1e-13 and op.feasibility(Q) <= 1e-13
+    s.close()
+
+
+def test_orthonormalize_reports_rank_deficiency():
+    from paper_1810_03930_gb300 import _lib
+    n, p = 200, 5
+    X = orthonormal_start(n, p, np.random.default_rng(1))
+    X[:, 3] = X[:, 1]
+    s = gpu_solver(workload_hartree1d(n=n, p=p), "fp64")
+    Xd = to_dev(X, s)
+    Qd = s.new_matrix(dtype=torch.float64)
+    st, _ = _lib.plam_orthonormalize(s.h, Xd.data_ptr(), Xd.stride(0), Qd.data_ptr(), Qd.stride(0), 1)
+    assert st == _lib.PLAM_ERR_CHOLESKY
+    s.close()
+
+
+# ---------------------------------------------------------------- edge cases and control
+
+
+def test_graph_and_plain_loops_are_bitwise_identical():
+    w = workload_dense_trace(500, 20)
+    out = []
+    for gi in (16, 0, 6):
+        s = gpu_solver(w, "fp64", variant="pcal", beta=1.0, tol=1e-8, graph_iters=gi, final_orth=0)
+        Xd = to_dev(w.X0, s)
+        st, info = s.solve(Xd)
+        out.append((info.iters, Xd.clone()))
+        s.close()
+    assert out[0][0] == out[1][0] == out[2][0]
+    assert torch.equal(out[0][1], out[1][1]) and torch.equal(out[0][1], out[2][1])
+
+
+def test_minimum_width_and_single_column():
+    for n, p in ((2, 1), (10, 5), (65, 1)):
+        A = gaussian_symmetric(n, np.random.default_rng(n))
+        X0 = orthonormal_start(n, p, np.random.default_rng(n + 1))
+        from workloads import Workload
+        w = Workload(name="edge", kind="dense", n=n, p=p, X0=X0, A=A)
+        s = gpu_solver(w, "fp64", variant="pcal", beta=abs(np.linalg.eigvalsh(A)).max() + 0.1,
+                       tol=1e-9, maxit=20000, final_orth=1)
+        Xd = to_dev(X0, s)
+        Qd = s.new_matrix(dtype=torch.float64)
+        st, info = s.solve(Xd, Qd)
+        assert st == 0, (n, p)
+        Q = to_host(Qd, n)
+        ev = np.linalg.eigvalsh(A)
+        assert abs(0.5 * np.sum(Q * (A @ Q)) - 0.5 * ev[:p].sum()) <= 1e-8 * max(1.0, abs(ev[:p]).sum())
+        s.close()
+
+
+def test_stationary_start_converges_in_zero_iterations():
+    """A start with K0 = 0 exactly (unit vectors of a diagonal A) is returned as converged."""
+    n, p = 100, 4
+    A = np.diag(np.random.default_rng(3).standard_normal(n))
+    X0 = np.zeros((n, p), order="F")
+    X0[np.arange(p), np.arange(p)] = 1.0
+    from workloads import Workload
+    w = Workload(name="stationary", kind="dense", n=n, p=p, X0=X0, A=np.asfortranarray(A))
+    s = gpu_solver(w, "fp64", tol=1e-8)
+    Xd = to_dev(w.X0, s)
+    st, info = s.solve(Xd)
+    assert st == 0 and info.converged and info.iters == 0 and info.K0 == 0.0
+    assert torch.equal(Xd, to_dev(X0, s))
+    s.close()
+
+
+def test_maxit_zero_and_not_converged():
+    w = workload_dense_trace(200, 5)
+    s = gpu_solver(w, "fp64", tol=1e-12, maxit=0)
+    Xd = to_dev(w.X0, s)
+    st, info = s.solve(Xd)
+    assert st == 2 and info.iters == 0 and not info.converged
+    s.close()
+    s = gpu_solver(w, "fp64", tol=1e-14, maxit=7)
+    Xd = to_dev(w.X0, s)
+    st, info = s.solve(Xd)
+    assert st == 2 and info.iters == 7
+    s.close()
+
+
+def test_divergence_is_reported_and_iterate_stays_finite():
+    """A huge first step (eta0 tiny) with PLAM overflows; the run stops with PLAM_ERR_DIVERGED."""
+    w = workload_dense_trace(200, 5)
+    s = gpu_solver(w, "fp64", variant="plam", beta=1e6, eta0=1e-300, tol=1e-10, maxit=50)
+    Xd = to_dev(w.X0, s)
+    st, info = s.solve(Xd)
+    assert st == 3
+    assert torch.isfinite(Xd).all()
+    s.close()
+
+
+def test_invalid_arguments_on_device():
+    from paper_1810_03930_gb300 import _lib
+    w = workload_dense_trace(100, 4)
+    s = gpu_solver(w, "fp64")
+    Xd = to_dev(w.X0, s)
+    st, _ = _lib.plam_step(s.h, Xd.data_ptr(), 50)          # ldx < n
+    assert st == _lib.PLAM_ERR_INVALID
+    st, _ = _lib.plam_step(s.h, Xd.data_ptr() + 4, 100)     # misaligned for double
+    assert st == _lib.PLAM_ERR_INVALID
+    assert s.kernel_launches() == 0
+    st, info = s.step(Xd)
+    assert s.kernel_launches() > 0
+    s.close()
+
+
+def test_leading_dimension_padding():
+    w = workload_dense_trace(300, 6)
+    obj = oo.TraceObjective(w.A)
+    ref = op.solve(obj, w.X0, variant="pcal", beta=1.0, tol=0.0, maxit=3)
+    s = gpu_solver(w, "fp64", variant="pcal", beta=1.0, tol=0.0, maxit=3, final_orth=0)
+    Xd = to_dev(w.X0, s, ld=320)
+    Xd[:, 300:] = float("nan")       # padding must never be read
+    st, info = s.solve(Xd)
+    assert rel_err(to_host(Xd, 300), ref.X) <= 1e-11
+    s.close()
