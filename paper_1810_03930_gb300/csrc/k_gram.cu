@@ -17,9 +17,9 @@
 // gram_reduce_kernel: B and C (double) from the partials, summed over chunks
 // in chunk order (bitwise reproducible; FP32 partials with Kahan compensation).
 //
-// gram_finalize_kernel: the same reduction (one warp per entry, lanes striding
-// over the chunks, fixed butterfly) fused with the p x p part of one
-// iteration (one CTA per row i of the symmetric matrices):
+// gram_chunk_reduce_kernel + gram_finalize_kernel: the same reduction
+// (coalesced, fixed order) followed by the p x p part of one iteration (one
+// CTA per row i of the symmetric matrices):
 //   Lambda0 = Psi(C)                                  eq. (Lambda1)
 //   d_i = diag(X^T grad_X L_beta(X, Lambda0))_i        eq. (lambda2)
 //       = C_ii - sum_k B_ik Lambda0_ik + beta (sum_k B_ik^2 - B_ii)
@@ -166,45 +166,65 @@ __global__ void gram_reduce_kernel(int p, int nchunks, int with_g, const T* __re
   }
 }
 
-// Sum over the chunks of one partial entry by one warp: lanes stride over the
-// chunks in order, then a fixed butterfly (every lane returns the same value).
-template <typename T>
-__device__ inline double warp_chunk_sum(const T* __restrict__ src, int nchunks, size_t cstride) {
-  T v = T(0);
-  for (int c = threadIdx.x & 31; c < nchunks; c += 32) v += src[(size_t)c * cstride];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return (double)v;
-}
+// Cross-chunk reduction of the partial Grams, coalesced: each CTA owns 32
+// consecutive entries of the 2p x p partial layout (lane = entry), its 8 warps
+// sum the chunks c = w, w + 8, ... in increasing order, and the 8 warp sums
+// are added in warp order (bitwise reproducible).  Entries of the lower
+// triangle of B are never formed and are skipped.  red: 2p x p, double.
+constexpr int kRedWarps = 8;
 
 template <typename T>
-__global__ void __launch_bounds__(256)
-gram_finalize_kernel(int p, int nchunks, const T* __restrict__ part, double* __restrict__ Bout,
+__global__ void __launch_bounds__(32 * kRedWarps)
+gram_chunk_reduce_kernel(int p, int nchunks, const T* __restrict__ part, double* __restrict__ red,
+                         const DevState* __restrict__ st) {
+  if (st != nullptr && st->stop != kRunning) return;
+  __shared__ T ws[kRedWarps][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const size_t E = (size_t)2 * p * p;
+  const size_t e = (size_t)blockIdx.x * 32 + lane;
+  const bool live = e < E && !((int)(e / p) < p && (int)(e % p) > (int)(e / p));
+  T v = T(0);
+  if (live) {
+#pragma unroll 4
+    for (int c = w; c < nchunks; c += kRedWarps) v += part[(size_t)c * E + e];
+  }
+  ws[w][lane] = v;
+  __syncthreads();
+  if (w == 0 && live) {
+    T s = T(0);
+#pragma unroll
+    for (int i = 0; i < kRedWarps; ++i) s += ws[i][lane];
+    red[e] = (double)s;
+  }
+}
+
+// p x p part of one iteration from the reduced Grams (one CTA per row i; B is
+// read through its upper triangle, B_ij = red[max(i,j) p + min(i,j)]).
+template <typename T>
+__global__ void __launch_bounds__(128)
+gram_finalize_kernel(int p, const double* __restrict__ red, double* __restrict__ Bout,
                      double* __restrict__ L0out, T* __restrict__ Mt, T* __restrict__ L0t,
                      double* __restrict__ feas_row, const DevState* __restrict__ st, IterParams prm) {
   if (st != nullptr && st->stop != kRunning) return;
   extern __shared__ double sh[];
   double* Brow = sh;          // B_ij
-  double* Crow = sh + p;      // C_ij
-  double* Ccol = sh + 2 * p;  // C_ji
+  double* Lrow = sh + p;      // Psi(C)_ij
   __shared__ double scratch[33];
+  __shared__ double cii;
   const int i = blockIdx.x;
-  const size_t cstride = (size_t)2 * p * p;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  // 3p sums (row i of B, row i and column i of C), one warp each
-  for (int sidx = warp; sidx < 3 * p; sidx += nw) {
-    const int j = sidx % p, which = sidx / p;
-    const T* src = which == 0 ? part + (size_t)max(i, j) * p + min(i, j)
-                 : which == 1 ? part + (size_t)(p + j) * p + i
-                              : part + (size_t)(p + i) * p + j;
-    const double v = warp_chunk_sum<T>(src, nchunks, cstride);
-    if (lane == 0) (which == 0 ? Brow : which == 1 ? Crow : Ccol)[j] = v;
+  for (int j = threadIdx.x; j < p; j += blockDim.x) {
+    const double b = red[(size_t)max(i, j) * p + min(i, j)];
+    const double cij = red[(size_t)(p + j) * p + i];
+    const double cji = red[(size_t)(p + i) * p + j];
+    Brow[j] = b;
+    Lrow[j] = 0.5 * (cij + cji);
+    if (j == i) cii = cij;
   }
   __syncthreads();
   double t1 = 0.0, t2 = 0.0, tf = 0.0;
   for (int j = threadIdx.x; j < p; j += blockDim.x) {
     const double bij = Brow[j];
-    t1 += bij * 0.5 * (Crow[j] + Ccol[j]);
+    t1 += bij * Lrow[j];
     t2 += bij * bij;
     const double e = bij - (j == i ? 1.0 : 0.0);
     tf += e * e;
@@ -213,15 +233,14 @@ gram_finalize_kernel(int p, int nchunks, const T* __restrict__ part, double* __r
   const double s2 = block_sum(t2, scratch);
   const double sf = block_sum(tf, scratch);
   const double beta = prm.beta;
-  const double d = prm.lambda2 ? (Crow[i] - s1 + beta * (s2 - Brow[i])) : 0.0;
+  const double d = prm.lambda2 ? (cii - s1 + beta * (s2 - Brow[i])) : 0.0;
   for (int j = threadIdx.x; j < p; j += blockDim.x) {
     const double delta = (j == i) ? 1.0 : 0.0;
-    const double l0 = 0.5 * (Crow[j] + Ccol[j]);
-    const double m = l0 + delta * d - beta * (Brow[j] - delta);
+    const double m = Lrow[j] + delta * d - beta * (Brow[j] - delta);
     Mt[j + (size_t)i * p] = (T)m;
-    L0t[j + (size_t)i * p] = (T)l0;
+    L0t[j + (size_t)i * p] = (T)Lrow[j];
     if (Bout) Bout[j + (size_t)i * p] = Brow[j];
-    if (L0out) L0out[j + (size_t)i * p] = l0;
+    if (L0out) L0out[j + (size_t)i * p] = Lrow[j];
   }
   if (threadIdx.x == 0) feas_row[i] = sf;
 }
@@ -250,16 +269,21 @@ cudaError_t launch_gram_reduce(int p, int nchunks, int with_g, const T* part, do
 }
 
 template <typename T>
-cudaError_t launch_gram_finalize(int p, int nchunks, const T* part, double* B, double* L0,
-                                 T* Mt, T* L0t, double* feas_row, const DevState* st,
+cudaError_t launch_gram_finalize(int p, int nchunks, const T* part, double* red, double* B,
+                                 double* L0, T* Mt, T* L0t, double* feas_row, const DevState* st,
                                  IterParams prm, cudaStream_t s) {
-  const size_t smem = (size_t)3 * p * sizeof(double);
+  const size_t E = (size_t)2 * p * p;
+  gram_chunk_reduce_kernel<T><<<(unsigned)((E + 31) / 32), 32 * kRedWarps, 0, s>>>(p, nchunks, part,
+                                                                                 red, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = (size_t)2 * p * sizeof(double);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(gram_finalize_kernel<T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(gram_finalize_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     if (e != cudaSuccess) return e;
   }
-  gram_finalize_kernel<T><<<p, 256, smem, s>>>(p, nchunks, part, B, L0, Mt, L0t, feas_row, st, prm);
+  gram_finalize_kernel<T><<<p, 128, smem, s>>>(p, red, B, L0, Mt, L0t, feas_row, st, prm);
   return cudaGetLastError();
 }
 
@@ -273,6 +297,8 @@ cudaError_t preload_gram_kernels() {
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_reduce_kernel<double>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_finalize_kernel<float>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_finalize_kernel<double>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_chunk_reduce_kernel<float>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_chunk_reduce_kernel<double>);
   return e;
 }
 
@@ -289,11 +315,11 @@ template cudaError_t launch_gram_reduce<float>(int, int, int, const float*, doub
                                                cudaStream_t);
 template cudaError_t launch_gram_reduce<double>(int, int, int, const double*, double*, double*,
                                                 cudaStream_t);
-template cudaError_t launch_gram_finalize<float>(int, int, const float*, double*, double*, float*,
-                                                 float*, double*, const DevState*, IterParams,
-                                                 cudaStream_t);
+template cudaError_t launch_gram_finalize<float>(int, int, const float*, double*, double*, double*,
+                                                 float*, float*, double*, const DevState*,
+                                                 IterParams, cudaStream_t);
 template cudaError_t launch_gram_finalize<double>(int, int, const double*, double*, double*,
-                                                  double*, double*, double*, const DevState*,
-                                                  IterParams, cudaStream_t);
+                                                  double*, double*, double*, double*,
+                                                  const DevState*, IterParams, cudaStream_t);
 
 }  // namespace plam

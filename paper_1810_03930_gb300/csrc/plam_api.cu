@@ -62,6 +62,7 @@ struct plam_handle_s {
   double* B = nullptr;      // p x p
   double* L0 = nullptr;     // p x p
   double* C = nullptr;      // p x p scratch for plam_grams
+  double* red = nullptr;    // 2p x p reduced Grams [B | C] of the iteration
   void* Mt = nullptr;
   void* L0t = nullptr;
   double* feas_row = nullptr;
@@ -197,8 +198,8 @@ plam_status_t launch_iteration(plam_handle_s* h, T* X, int64_t ldx, int variant,
   CK((launch_gram_partial<T, T>(h->n, p, X, ldx, G, h->ldw, h->rows_per_chunk, h->nchunks,
                                  (T*)h->part, h->st, s)));
   if (ev) CK(cudaEventRecord(ev[2], s));
-  CK(launch_gram_finalize<T>(p, h->nchunks, (const T*)h->part, h->B, h->L0, (T*)h->Mt, (T*)h->L0t,
-                             h->feas_row, h->st, ip, s));
+  CK(launch_gram_finalize<T>(p, h->nchunks, (const T*)h->part, h->red, h->B, h->L0, (T*)h->Mt,
+                             (T*)h->L0t, h->feas_row, h->st, ip, s));
   if (ev) CK(cudaEventRecord(ev[3], s));
   CK(launch_update<T>(h->n, p, X, ldx, G, h->ldw, (T*)h->R[0], (T*)h->R[1], h->ldw,
                       (const T*)h->Mt, (const T*)h->L0t, (const T*)h->coef, h->st, (T*)h->colpart,
@@ -211,7 +212,7 @@ plam_status_t launch_iteration(plam_handle_s* h, T* X, int64_t ldx, int variant,
   CK(launch_primal_update<T>(h->n, p, X, ldx, (const T*)h->R[0], (const T*)h->R[1], h->ldw,
                              (const T*)h->coef, h->st, variant, s));
   if (ev) CK(cudaEventRecord(ev[6], s));
-  *nk = k + 5;
+  *nk = k + 6;
   return PLAM_OK;
 }
 
@@ -271,7 +272,7 @@ plam_status_t step_common(plam_handle_t h, void* X, int64_t ldx, plam_info_t* in
 void free_handle(plam_handle_s* h) {
   if (!h) return;
   if (h->graph) cudaGraphExecDestroy(h->graph);
-  void* dev[] = {h->G, h->R[0], h->R[1], h->part, h->part64, h->B, h->L0, h->C, h->Mt, h->L0t,
+  void* dev[] = {h->G, h->R[0], h->R[1], h->part, h->part64, h->B, h->L0, h->C, h->red, h->Mt, h->L0t,
                  h->feas_row, h->colpart, h->totpart, h->sums, h->ticket, h->st, h->nubuf, h->coef,
                  h->hist,
                  h->rho, h->blk, h->y, h->fpart, h->W, h->Z, h->info, h->feas_dev, h->Qtmp,
@@ -436,6 +437,7 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
             alloc((void**)&h->part64, (size_t)h->nchunks * 2 * pp * sizeof(double)) &&
             alloc((void**)&h->B, pp * sizeof(double)) && alloc((void**)&h->L0, pp * sizeof(double)) &&
             alloc((void**)&h->C, pp * sizeof(double)) && alloc(&h->Mt, pp * esz) &&
+            alloc((void**)&h->red, 2 * pp * sizeof(double)) &&
             alloc(&h->L0t, pp * esz) && alloc((void**)&h->feas_row, p * sizeof(double)) &&
             alloc(&h->colpart, (size_t)h->nrt * kColDots * p * esz) &&
             alloc(&h->totpart, (size_t)h->nrt * h->nct * kTotDots * esz) &&

@@ -68,9 +68,10 @@ cudaError_t launch_gram_partial(int64_t n, int p, const Tin* X, int64_t ldx, con
 template <typename T>
 cudaError_t launch_gram_reduce(int p, int nchunks, int with_g, const T* part, double* B,
                                double* C, cudaStream_t s);
+// red: 2p x p doubles of scratch for the reduced Grams [B | C].
 template <typename T>
-cudaError_t launch_gram_finalize(int p, int nchunks, const T* part, double* B, double* L0,
-                                 T* Mt, T* L0t, double* feas_row, const DevState* st,
+cudaError_t launch_gram_finalize(int p, int nchunks, const T* part, double* red, double* B,
+                                 double* L0, T* Mt, T* L0t, double* feas_row, const DevState* st,
                                  IterParams prm, cudaStream_t s);
 
 // R0/R1: the two residual buffers (R^k goes to buffer k mod 2).  nubuf: 2 x p
