@@ -200,6 +200,24 @@ plam_status_t plam_grams(plam_handle_t h, const void* X, int64_t ldx, const void
 plam_status_t plam_time_kernels(plam_handle_t h, void* X, int64_t ldx, int iters, double* ms,
                                 int* done);
 
+/* The Grams of plam_grams (B = X^T X, and C = X^T G when G is not NULL; FP64
+ * p x p column-major device outputs, leading dimension p) without a handle and
+ * without allocating any device memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate -- applications whose
+ * device memory belongs to another memory manager with a fixed budget, or
+ * latency-critical loops where cudaMalloc's implicit device synchronisation is
+ * not acceptable.  The split-K partial sums use an 8 MiB array that the
+ * library reserves statically on every device that loads it, until the
+ * process exits; requests with 2 p^2 partial sums of one chunk above that
+ * (p > 1024 in FP32 mode, p > 724 in FP64 mode) return PLAM_ERR_INVALID.
+ * precision: PLAM_PREC_FP64 (X, G double) or PLAM_PREC_FP32 (float).  The
+ * first call on a device looks up the array's device address (do it before
+ * any stream capture).  The work is ordered on `stream` and the call returns
+ * without synchronising.  All calls share the one array: calls whose kernels
+ * overlap on the GPU race and must be serialised by the caller. */
+plam_status_t plam_grams_noalloc(int64_t n, int64_t p, int precision, const void* X, int64_t ldx,
+                                 const void* G, int64_t ldg, double* B, double* C, void* stream);
+
 /* Copies up to `cap` per-iteration records (k, f, kkt_rel, feas, eta as 5
  * doubles each, in that order) of the current run to host memory `out`;
  * *count receives the number written. */

@@ -72,6 +72,8 @@ SIGNATURES = {
                                    C.POINTER(C.c_double)]),
     "plam_grams": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                              C.c_void_p, C.c_void_p]),
+    "plam_grams_noalloc": (C.c_int, [C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_int64,
+                                     C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "plam_time_kernels": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int,
                                     C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "plam_history": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]),
@@ -174,6 +176,12 @@ def plam_energy_grad(h, X: int, ldx: int, G: int, ldg: int, want_f=True):
 def plam_grams(h, X: int, ldx: int, G: int | None, ldg: int, B: int, Cm: int | None):
     return load().plam_grams(h, C.c_void_p(X), ldx, C.c_void_p(G or 0), ldg, C.c_void_p(B),
                              C.c_void_p(Cm or 0))
+
+
+def plam_grams_noalloc(n: int, p: int, precision: int, X: int, ldx: int, G: int | None, ldg: int,
+                       B: int, Cm: int | None, stream: int = 0):
+    return load().plam_grams_noalloc(n, p, precision, C.c_void_p(X), ldx, C.c_void_p(G or 0), ldg,
+                                     C.c_void_p(B), C.c_void_p(Cm or 0), C.c_void_p(stream))
 
 
 KERNEL_GROUPS = ("objective", "gram_partial", "gram_finalize", "update", "step_size", "primal_update")

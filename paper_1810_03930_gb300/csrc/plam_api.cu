@@ -34,6 +34,14 @@ plam_status_t cuda_fail(cudaError_t e, const char* what) {
   return PLAM_ERR_CUDA;
 }
 
+}  // namespace
+
+void plam::set_last_error(const char* what, const char* detail) {
+  snprintf(g_err, sizeof(g_err), "%s: %s", what, detail);
+}
+
+namespace {
+
 #define CK(call)                                              \
   do {                                                        \
     cudaError_t e_ = (call);                                  \

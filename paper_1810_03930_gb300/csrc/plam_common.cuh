@@ -117,6 +117,9 @@ cudaError_t launch_apply_rinv(int64_t n, int p, const T* X, int64_t ldx, const d
 // out[0] = ||B - I||_F (one CTA).
 cudaError_t launch_feas(int p, const double* B, double* out, cudaStream_t s);
 
+// Message returned by plam_last_error() on this host thread ("what: detail").
+void set_last_error(const char* what, const char* detail);
+
 // Force the module load of every kernel (lazy loading must not happen inside
 // a stream capture).
 cudaError_t preload_gram_kernels();
