@@ -52,7 +52,7 @@ typedef enum {
   PLAM_ERR_NOT_CONVERGED = 2,  /* maxit iterations performed without meeting tol */
   PLAM_ERR_DIVERGED = 3,       /* non-finite KKT value, step size or column norm */
   PLAM_ERR_CHOLESKY = 4,       /* X^T X not numerically positive definite */
-  PLAM_ERR_TIMEOUT = 5,        /* a bounded device-side wait expired */
+  PLAM_ERR_TIMEOUT = 5,        /* a bounded device-side wait (resident engine barrier) expired */
   PLAM_ERR_CUDA = 6,           /* a CUDA runtime call failed */
   PLAM_ERR_NOMEM = 7,          /* device or pinned host allocation failed */
   PLAM_ERR_UNSUPPORTED = 8     /* valid request that this build does not implement */
@@ -77,6 +77,13 @@ enum { PLAM_PREC_FP64 = 0, PLAM_PREC_FP32 = 1 };
  *   STENCIL3D  f = 1/2 tr(X^T (L3 + Diag(V)) X), L3 the 7-point Dirichlet
  *              Laplacian on nx*ny*nz points, index i = x + nx*(y + ny*z). */
 enum { PLAM_OBJ_DENSE = 0, PLAM_OBJ_HARTREE1D = 1, PLAM_OBJ_STENCIL3D = 2 };
+/* How plam_solve runs the loop.  GRAPH: the kernel sequence of one iteration,
+ * replayed from a captured CUDA graph (any size).  RESIDENT: one cooperative
+ * persistent launch for the whole solve, each SM keeping its rows of X, G/R
+ * and the previous R in shared memory (FP32 mode, p <= 64, HARTREE1D or
+ * DENSE, and the rows per SM must fit; otherwise PLAM_ERR_UNSUPPORTED).
+ * AUTO: RESIDENT when it applies, else GRAPH. */
+enum { PLAM_ENGINE_AUTO = 0, PLAM_ENGINE_GRAPH = 1, PLAM_ENGINE_RESIDENT = 2 };
 
 typedef struct {
   int variant;          /* PLAM_VARIANT_* used by plam_solve (plam_step/pcal_step choose their own) */
@@ -90,6 +97,7 @@ typedef struct {
   int precision;        /* PLAM_PREC_* */
   int final_orth;       /* 0: none, 1: one Cholesky-QR pass, 2: two passes (CholQR2) */
   int graph_iters;      /* iterations per captured CUDA graph in plam_solve; 0 = plain launches */
+  int engine;           /* plam_solve engine: PLAM_ENGINE_AUTO, _GRAPH or _RESIDENT */
 } plam_params_t;
 
 typedef struct {

@@ -31,13 +31,14 @@ PLAM_LAMBDA1, PLAM_LAMBDA2 = 0, 1
 PLAM_ETA_ABB, PLAM_ETA_BB1, PLAM_ETA_BB2, PLAM_ETA_CONST, PLAM_ETA_DIFF = 0, 1, 2, 3, 4
 PLAM_PREC_FP64, PLAM_PREC_FP32 = 0, 1
 PLAM_OBJ_DENSE, PLAM_OBJ_HARTREE1D, PLAM_OBJ_STENCIL3D = 0, 1, 2
+PLAM_ENGINE_AUTO, PLAM_ENGINE_GRAPH, PLAM_ENGINE_RESIDENT = 0, 1, 2
 
 
 class plam_params_t(C.Structure):
     _fields_ = [("variant", C.c_int), ("lambda_rule", C.c_int), ("beta", C.c_double),
                 ("eta_rule", C.c_int), ("eta0", C.c_double), ("eta_gamma", C.c_double),
                 ("tol", C.c_double), ("maxit", C.c_int), ("precision", C.c_int),
-                ("final_orth", C.c_int), ("graph_iters", C.c_int)]
+                ("final_orth", C.c_int), ("graph_iters", C.c_int), ("engine", C.c_int)]
 
 
 class plam_objective_t(C.Structure):

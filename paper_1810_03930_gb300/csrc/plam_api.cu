@@ -17,6 +17,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -104,6 +105,17 @@ struct plam_handle_s {
   int graph_variant = -1;
   int graph_kernels = 0;
   int64_t launches = 0;
+  // resident engine (allocated at creation when the problem qualifies)
+  int r_nblk = 0, r_rows = 0, r_rp = 0;
+  size_t r_smem = 0;
+  float* r_halo = nullptr;
+  double* r_blk = nullptr;
+  float* r_part = nullptr;
+  float* r_red = nullptr;
+  float* r_dots = nullptr;
+  double* r_dred = nullptr;
+  unsigned int* r_bar = nullptr;
+  int* r_err = nullptr;
 };
 
 namespace {
@@ -144,6 +156,7 @@ plam_status_t validate_params(const plam_params_t* prm) {
   if (!(prm->beta >= 0.0) || !std::isfinite(prm->beta)) return PLAM_ERR_INVALID;
   if (!(prm->tol >= 0.0) || prm->maxit < 0) return PLAM_ERR_INVALID;
   if (prm->final_orth < 0 || prm->final_orth > 2 || prm->graph_iters < 0) return PLAM_ERR_INVALID;
+  if (prm->engine < PLAM_ENGINE_AUTO || prm->engine > PLAM_ENGINE_RESIDENT) return PLAM_ERR_INVALID;
   return PLAM_OK;
 }
 
@@ -255,6 +268,7 @@ plam_status_t read_state(plam_handle_s* h, plam_info_t* info, int* stop) {
     info->eta0 = s.eta0;
     info->status = (s.stop == kDiverged) ? PLAM_ERR_DIVERGED
                    : (s.stop == kMaxit)  ? PLAM_ERR_NOT_CONVERGED
+                   : (s.stop == kTimeout) ? PLAM_ERR_TIMEOUT
                                          : PLAM_OK;
   }
   return PLAM_OK;
@@ -284,7 +298,8 @@ void free_handle(plam_handle_s* h) {
                  h->feas_row, h->colpart, h->totpart, h->sums, h->ticket, h->st, h->nubuf, h->coef,
                  h->hist,
                  h->rho, h->blk, h->y, h->fpart, h->W, h->Z, h->info, h->feas_dev, h->Qtmp,
-                 h->dotpart};
+                 h->dotpart, h->r_halo, h->r_blk, h->r_part, h->r_red, h->r_dots, h->r_dred,
+                 h->r_bar, h->r_err};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (h->st_host) cudaFreeHost(h->st_host);
@@ -387,6 +402,7 @@ plam_status_t plam_default_params(plam_params_t* prm) {
   prm->precision = PLAM_PREC_FP64;
   prm->final_orth = 1;
   prm->graph_iters = 16;
+  prm->engine = PLAM_ENGINE_AUTO;
   return PLAM_OK;
 }
 
@@ -465,6 +481,31 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
          alloc((void**)&h->fpart, (size_t)h->nfpart * sizeof(double));
   }
   if (ok && prm->final_orth == 2) ok = alloc((void**)&h->Qtmp, (size_t)h->ldw * p * sizeof(double));
+  if (ok && prm->engine != PLAM_ENGINE_GRAPH && prm->precision == PLAM_PREC_FP32 &&
+      (obj->kind == PLAM_OBJ_HARTREE1D || obj->kind == PLAM_OBJ_DENSE)) {
+    int dev = 0, sms = 0, optin = 0, coop = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop) {
+      resident_plan(n, (int)p, sms, (size_t)optin, &h->r_nblk, &h->r_rows, &h->r_rp, &h->r_smem);
+    }
+    if (h->r_nblk > 0) {
+      const size_t S = 3 * (size_t)p + 7;
+      ok = alloc((void**)&h->r_halo, (size_t)h->r_nblk * 2 * p * sizeof(float)) &&
+           alloc((void**)&h->r_blk, (size_t)h->r_nblk * 2 * sizeof(double)) &&
+           alloc((void**)&h->r_part, (size_t)h->r_nblk * 2 * pp * sizeof(float)) &&
+           alloc((void**)&h->r_red, 2 * pp * sizeof(float)) &&
+           alloc((void**)&h->r_dots, (size_t)h->r_nblk * S * sizeof(float)) &&
+           alloc((void**)&h->r_dred, S * sizeof(double)) &&
+           alloc((void**)&h->r_bar, 2 * sizeof(unsigned int)) && alloc((void**)&h->r_err, sizeof(int));
+    }
+  }
+  if (ok && prm->engine == PLAM_ENGINE_RESIDENT && h->r_nblk == 0) {
+    free_handle(h);
+    snprintf(g_err, sizeof(g_err), "resident engine does not apply to this problem");
+    return PLAM_ERR_UNSUPPORTED;
+  }
   if (ok) {
     ok = cudaMallocHost((void**)&h->st_host, sizeof(DevState)) == cudaSuccess &&
          cudaMallocHost((void**)&h->info_host, sizeof(int)) == cudaSuccess &&
@@ -480,6 +521,7 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
     cudaError_t e = preload_gram_kernels();
     if (e == cudaSuccess) e = preload_update_kernels();
     if (e == cudaSuccess) e = preload_objective_kernels();
+    if (e == cudaSuccess && h->r_nblk > 0) e = preload_resident_kernels();
     if (e != cudaSuccess) {
       free_handle(h);
       return cuda_fail(e, "kernel preload");
@@ -543,7 +585,32 @@ plam_status_t plam_solve(plam_handle_t h, void* X, int64_t ldx, double* Xout, in
   if (st != PLAM_OK) return st;
   const int gi = h->prm.graph_iters;
   int stop = kRunning;
-  if (gi > 0) {
+  if (h->r_nblk > 0) {
+    // resident engine: the whole loop in one cooperative launch
+    ResidentLaunch L{};
+    L.n = h->n; L.p = (int)h->p; L.nblk = h->r_nblk; L.rows = h->r_rows; L.rp = h->r_rp;
+    L.smem = h->r_smem; L.kind = h->obj.kind; L.A = (const float*)h->obj.A; L.lda = h->obj.lda;
+    L.alpha = h->obj.alpha; L.q = h->obj.quad_scale; L.X = (float*)X; L.ldx = ldx;
+    L.R0 = (float*)h->R[0]; L.R1 = (float*)h->R[1]; L.ldr = h->ldw;
+    L.halo = h->r_halo; L.blk = h->r_blk; L.part = h->r_part; L.red = h->r_red; L.dots = h->r_dots;
+    L.dred = h->r_dred; L.bar = h->r_bar; L.err = h->r_err; L.st = h->st; L.nubuf = h->nubuf;
+    L.coef = (float*)h->coef; L.hist = h->hist;
+    L.prm = iter_params<float>(h, variant, lambda2);
+    // failure-detection test hook: extra expected arrivals that never come, so the
+    // bounded barrier wait runs out (no fault; the kernel returns a status)
+    const char* extra = getenv("PLAM_TEST_BARRIER_EXTRA");
+    L.bar_extra = extra ? atoi(extra) : 0;
+    CK(cudaMemsetAsync(h->r_bar, 0, 2 * sizeof(unsigned int), h->stream));
+    CK(cudaMemsetAsync(h->r_err, 0, sizeof(int), h->stream));
+    CK(launch_resident_solve(L, h->stream));
+    h->launches += 1;
+    st = read_state(h, nullptr, &stop);
+    if (st != PLAM_OK) return st;
+    if (stop == kTimeout) {
+      snprintf(g_err, sizeof(g_err), "resident engine: a grid barrier wait expired");
+      return PLAM_ERR_TIMEOUT;
+    }
+  } else if (gi > 0) {
     if (!h->graph || h->graph_X != X || h->graph_ldx != ldx || h->graph_variant != variant) {
       if (h->graph) {
         cudaGraphExecDestroy(h->graph);

@@ -18,7 +18,7 @@ constexpr int kKStep = 32;        // rows (Gram) or inner index (update) per sha
 constexpr int kFlushRows = 256;   // FP32 running sums are flushed into a compensated sum after this many terms
 
 // Stop codes written by the step-size kernel.
-enum StopCode { kRunning = 0, kConverged = 1, kMaxit = 2, kDiverged = 3 };
+enum StopCode { kRunning = 0, kConverged = 1, kMaxit = 2, kDiverged = 3, kTimeout = 4 };
 
 // Per-solve device state (one instance per handle, in device memory).
 struct DevState {
@@ -119,6 +119,40 @@ cudaError_t launch_feas(int p, const double* B, double* out, cudaStream_t s);
 
 // Message returned by plam_last_error() on this host thread ("what: detail").
 void set_last_error(const char* what, const char* detail);
+
+// Resident (persistent, cooperative) solve: FP32, p <= 64, Hartree or dense.
+struct ResidentLaunch {
+  int64_t n;
+  int p, nblk, rows, rp;
+  size_t smem;
+  int kind;
+  const float* A;
+  int64_t lda;
+  double alpha, q;
+  float* X;
+  int64_t ldx;
+  float* R0;
+  float* R1;
+  int64_t ldr;
+  float* halo;
+  double* blk;
+  float* part;
+  float* red;
+  float* dots;
+  double* dred;
+  unsigned int* bar;
+  int bar_extra;   // 0; a test raises it so that no barrier is ever released (bounded wait expires)
+  int* err;
+  DevState* st;
+  double* nubuf;
+  float* coef;
+  double* hist;
+  IterParams prm;
+};
+void resident_plan(int64_t n, int p, int sms, size_t smem_limit, int* nblk, int* rows, int* rp,
+                   size_t* smem);
+cudaError_t launch_resident_solve(const ResidentLaunch& L, cudaStream_t s);
+cudaError_t preload_resident_kernels();
 
 // Force the module load of every kernel (lazy loading must not happen inside
 // a stream capture).
