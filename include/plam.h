@@ -52,7 +52,7 @@ typedef enum {
   PLAM_ERR_NOT_CONVERGED = 2,  /* maxit iterations performed without meeting tol */
   PLAM_ERR_DIVERGED = 3,       /* non-finite KKT value, step size or column norm */
   PLAM_ERR_CHOLESKY = 4,       /* X^T X not numerically positive definite */
-  PLAM_ERR_TIMEOUT = 5,        /* a bounded device-side wait (resident engine barrier) expired */
+  PLAM_ERR_TIMEOUT = 5,        /* a bounded device-side wait (grid barrier, tensor-core pipeline) expired */
   PLAM_ERR_CUDA = 6,           /* a CUDA runtime call failed */
   PLAM_ERR_NOMEM = 7,          /* device or pinned host allocation failed */
   PLAM_ERR_UNSUPPORTED = 8     /* valid request that this build does not implement */
@@ -98,6 +98,12 @@ typedef struct {
   int final_orth;       /* 0: none, 1: one Cholesky-QR pass, 2: two passes (CholQR2) */
   int graph_iters;      /* iterations per captured CUDA graph in plam_solve; 0 = plain launches */
   int engine;           /* plam_solve engine: PLAM_ENGINE_AUTO, _GRAPH or _RESIDENT */
+  int tensor_cores;     /* FP32 mode Grams on tcgen05 (kind::tf32, operands rounded to nearest TF32):
+                           0 off; 1 TF32, switching to compensated 3xTF32 (hi*hi + hi*lo + lo*hi) once
+                           the relative KKT value is below refine_switch; 2 always 3xTF32; -1 auto
+                           (= 1 when p >= 128).  Needs 16-byte aligned X and G with leading dimensions
+                           that are multiples of 4, otherwise the CUDA-core Grams run */
+  double refine_switch; /* relative KKT value below which the tensor-core Grams are compensated */
 } plam_params_t;
 
 typedef struct {

@@ -60,7 +60,8 @@ class Solver:
     def __init__(self, n, p, kind, *, A=None, alpha=1.0, quad_scale=0.25, grid=None, V=None,
                  variant="pcal", lambda_rule="lambda2", beta=1.0, eta_rule="abb", eta0=0.0,
                  eta_gamma=0.0, tol=1e-8, maxit=3000, precision="fp64", final_orth=1,
-                 graph_iters=16, engine="auto", stream=None):
+                 graph_iters=16, engine="auto", tensor_cores="auto", refine_switch=1e-3,
+                 stream=None):
         torch = _torch()
         self.n, self.p = int(n), int(p)
         self.precision = precision
@@ -78,6 +79,8 @@ class Solver:
         prm.final_orth = int(final_orth)
         prm.graph_iters = int(graph_iters)
         prm.engine = {"auto": 0, "graph": 1, "resident": 2}[engine]
+        prm.tensor_cores = {"auto": -1, "off": 0, "on": 1, "tf32": 1, "3xtf32": 2}[tensor_cores]
+        prm.refine_switch = float(refine_switch)
         self.params = prm
         obj = _lib.plam_objective_t()
         self._keep = []

@@ -38,7 +38,8 @@ class plam_params_t(C.Structure):
     _fields_ = [("variant", C.c_int), ("lambda_rule", C.c_int), ("beta", C.c_double),
                 ("eta_rule", C.c_int), ("eta0", C.c_double), ("eta_gamma", C.c_double),
                 ("tol", C.c_double), ("maxit", C.c_int), ("precision", C.c_int),
-                ("final_orth", C.c_int), ("graph_iters", C.c_int), ("engine", C.c_int)]
+                ("final_orth", C.c_int), ("graph_iters", C.c_int), ("engine", C.c_int),
+                ("tensor_cores", C.c_int), ("refine_switch", C.c_double)]
 
 
 class plam_objective_t(C.Structure):

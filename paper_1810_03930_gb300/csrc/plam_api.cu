@@ -116,6 +116,10 @@ struct plam_handle_s {
   double* r_dred = nullptr;
   unsigned int* r_bar = nullptr;
   int* r_err = nullptr;
+  // tensor-core Grams (FP32 mode)
+  int use_tc = 0;
+  TcGramPlan tc{};
+  int* tc_err = nullptr;
 };
 
 namespace {
@@ -157,6 +161,8 @@ plam_status_t validate_params(const plam_params_t* prm) {
   if (!(prm->tol >= 0.0) || prm->maxit < 0) return PLAM_ERR_INVALID;
   if (prm->final_orth < 0 || prm->final_orth > 2 || prm->graph_iters < 0) return PLAM_ERR_INVALID;
   if (prm->engine < PLAM_ENGINE_AUTO || prm->engine > PLAM_ENGINE_RESIDENT) return PLAM_ERR_INVALID;
+  if (prm->tensor_cores < -1 || prm->tensor_cores > 2) return PLAM_ERR_INVALID;
+  if (!(prm->refine_switch >= 0.0)) return PLAM_ERR_INVALID;
   return PLAM_OK;
 }
 
@@ -216,10 +222,17 @@ plam_status_t launch_iteration(plam_handle_s* h, T* X, int64_t ldx, int variant,
   int k = launch_objective<T>(h, X, ldx, G, h->ldw, h->st, s, &e);
   if (k < 0 || e != cudaSuccess) return cuda_fail(e, "objective gradient");
   if (ev) CK(cudaEventRecord(ev[1], s));
-  CK((launch_gram_partial<T, T>(h->n, p, X, ldx, G, h->ldw, h->rows_per_chunk, h->nchunks,
-                                 (T*)h->part, h->st, s)));
+  int nch = h->nchunks;
+  if (sizeof(T) == 4 && h->use_tc && tc_gram_supported(X, ldx, G, h->ldw)) {
+    CK(launch_tc_gram(h->n, p, (const float*)X, ldx, (const float*)G, h->ldw, h->tc, (float*)h->part,
+                      h->tc_err, h->st, h->prm.refine_switch, h->prm.tensor_cores == 2, s));
+    nch = h->tc.nchunks;
+  } else {
+    CK((launch_gram_partial<T, T>(h->n, p, X, ldx, G, h->ldw, h->rows_per_chunk, h->nchunks,
+                                   (T*)h->part, h->st, s)));
+  }
   if (ev) CK(cudaEventRecord(ev[2], s));
-  CK(launch_gram_finalize<T>(p, h->nchunks, (const T*)h->part, h->red, h->B, h->L0, (T*)h->Mt,
+  CK(launch_gram_finalize<T>(p, nch, (const T*)h->part, h->red, h->B, h->L0, (T*)h->Mt,
                              (T*)h->L0t, h->feas_row, h->st, ip, s));
   if (ev) CK(cudaEventRecord(ev[3], s));
   CK(launch_update<T>(h->n, p, X, ldx, G, h->ldw, (T*)h->R[0], (T*)h->R[1], h->ldw,
@@ -249,12 +262,15 @@ plam_status_t reset_state(plam_handle_s* h) {
   CK(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), h->stream));
   CK(cudaMemsetAsync(h->nubuf, 0, 2 * h->p * sizeof(double), h->stream));
   CK(cudaMemsetAsync(h->coef, 0, 2 * (2 * h->p + 1) * h->esz, h->stream));
+  if (h->tc_err) CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream));
   return PLAM_OK;
 }
 
 plam_status_t read_state(plam_handle_s* h, plam_info_t* info, int* stop) {
   CK(cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  if (h->tc_err) CK(cudaMemcpyAsync(h->info_host, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (h->tc_err && *h->info_host != 0) h->st_host->stop = kTimeout;
   const DevState& s = *h->st_host;
   if (stop) *stop = s.stop;
   if (info) {
@@ -299,7 +315,7 @@ void free_handle(plam_handle_s* h) {
                  h->hist,
                  h->rho, h->blk, h->y, h->fpart, h->W, h->Z, h->info, h->feas_dev, h->Qtmp,
                  h->dotpart, h->r_halo, h->r_blk, h->r_part, h->r_red, h->r_dots, h->r_dred,
-                 h->r_bar, h->r_err};
+                 h->r_bar, h->r_err, h->tc_err};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (h->st_host) cudaFreeHost(h->st_host);
@@ -403,6 +419,8 @@ plam_status_t plam_default_params(plam_params_t* prm) {
   prm->final_orth = 1;
   prm->graph_iters = 16;
   prm->engine = PLAM_ENGINE_AUTO;
+  prm->tensor_cores = -1;
+  prm->refine_switch = 1e-3;
   return PLAM_OK;
 }
 
@@ -451,13 +469,20 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
   h->nrt = (int)((n + kTile - 1) / kTile);
   h->nct = nt;
   h->hist_cap = prm->maxit + 2;
+  if (prm->precision == PLAM_PREC_FP32 &&
+      (prm->tensor_cores >= 1 || (prm->tensor_cores == -1 && p >= 128))) {
+    tc_gram_plan(n, (int)p, 1, &h->tc);
+    h->use_tc = 1;
+  }
+  const int part_chunks = h->use_tc && h->tc.nchunks > h->nchunks ? h->tc.nchunks : h->nchunks;
   const size_t np_bytes = (size_t)h->ldw * p * esz;
   const size_t pp = (size_t)p * p;
   auto alloc = [&](void** ptr, size_t bytes) -> bool {
     return cudaMalloc(ptr, bytes == 0 ? 16 : bytes) == cudaSuccess;
   };
   bool ok = alloc(&h->G, np_bytes) && alloc(&h->R[0], np_bytes) && alloc(&h->R[1], np_bytes) &&
-            alloc(&h->part, (size_t)h->nchunks * 2 * pp * esz) &&
+            alloc(&h->part, (size_t)part_chunks * 2 * pp * esz) &&
+            alloc((void**)&h->tc_err, sizeof(int)) &&
             alloc((void**)&h->part64, (size_t)h->nchunks * 2 * pp * sizeof(double)) &&
             alloc((void**)&h->B, pp * sizeof(double)) && alloc((void**)&h->L0, pp * sizeof(double)) &&
             alloc((void**)&h->C, pp * sizeof(double)) && alloc(&h->Mt, pp * esz) &&
@@ -522,6 +547,7 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
     if (e == cudaSuccess) e = preload_update_kernels();
     if (e == cudaSuccess) e = preload_objective_kernels();
     if (e == cudaSuccess && h->r_nblk > 0) e = preload_resident_kernels();
+    if (e == cudaSuccess && h->use_tc) e = preload_tc_kernels();
     if (e != cudaSuccess) {
       free_handle(h);
       return cuda_fail(e, "kernel preload");
@@ -697,6 +723,23 @@ plam_status_t plam_grams(plam_handle_t h, const void* X, int64_t ldx, const void
                                              nullptr, h->stream)));
     CK(launch_gram_reduce<double>(p, h->nchunks, G != nullptr, (const double*)h->part, B, C,
                                   h->stream));
+  } else if (h->use_tc && tc_gram_supported(X, ldx, G, ldg)) {
+    TcGramPlan pl = h->tc;
+    if (!G) tc_gram_plan(h->n, p, 0, &pl);
+    if (pl.nchunks > h->tc.nchunks) pl = h->tc;   // the workspace is sized for the with-G plan
+    CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream));
+    CK(launch_tc_gram(h->n, p, (const float*)X, ldx, (const float*)G, ldg, pl, (float*)h->part,
+                      h->tc_err, nullptr, 0.0, h->prm.tensor_cores == 2, h->stream));
+    CK(launch_gram_reduce<float>(p, pl.nchunks, G != nullptr, (const float*)h->part, B, C,
+                                 h->stream));
+    CK(cudaMemcpyAsync(h->info_host, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->launches += 2;
+    if (*h->info_host != 0) {
+      snprintf(g_err, sizeof(g_err), "tensor-core Gram: a pipeline wait expired");
+      return PLAM_ERR_TIMEOUT;
+    }
+    return PLAM_OK;
   } else {
     CK((launch_gram_partial<float, float>(h->n, p, (const float*)X, ldx, (const float*)G, ldg,
                                            h->rows_per_chunk, h->nchunks, (float*)h->part, nullptr,

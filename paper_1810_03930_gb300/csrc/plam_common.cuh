@@ -154,6 +154,23 @@ void resident_plan(int64_t n, int p, int sms, size_t smem_limit, int* nblk, int*
 cudaError_t launch_resident_solve(const ResidentLaunch& L, cudaStream_t s);
 cudaError_t preload_resident_kernels();
 
+// Tensor-core (tcgen05, kind::tf32) Grams: split-K partials in the layout of
+// launch_gram_partial (float), reduced by launch_gram_finalize / _reduce.
+struct TcGramPlan {
+  int N, nmb, nnb, nbt, ntiles;
+  int64_t rows_per_chunk;
+  int nchunks;
+  size_t smem;
+};
+void tc_gram_plan(int64_t n, int p, int with_g, TcGramPlan* pl);
+bool tc_gram_supported(const void* X, int64_t ldx, const void* G, int64_t ldg);
+// st / refine_switch: compensated 3xTF32 once st->kkt < refine_switch (st may be
+// null); force3 = 1 always uses it.
+cudaError_t launch_tc_gram(int64_t n, int p, const float* X, int64_t ldx, const float* G,
+                           int64_t ldg, const TcGramPlan& pl, float* part, int* err,
+                           const DevState* st, double refine_switch, int force3, cudaStream_t s);
+cudaError_t preload_tc_kernels();
+
 // Force the module load of every kernel (lazy loading must not happen inside
 // a stream capture).
 cudaError_t preload_gram_kernels();
