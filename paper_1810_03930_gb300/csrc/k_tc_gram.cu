@@ -27,101 +27,13 @@
 #include <cuda.h>
 
 #include "plam_device.cuh"
+#include "tc_ptx.cuh"
 
 namespace plam {
 
 constexpr int kTcM = 128;          // rows of the accumulator (columns of X per tile)
 constexpr int kTcK = 32;           // rows of X per stage (128 bytes of FP32 per line)
 constexpr int kTcStages = 4;
-constexpr long long kTcSpin = 1ll << 26;
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait for the phase with the given parity; false (and *err raised)
-// when the limit expires or another thread already raised it.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
-  for (long long i = 0; i < kTcSpin; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 1023) == 1023 && *(volatile int*)err != 0) return false;
-  }
-  atomicExch(err, 1);
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
-                                            int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_addr(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 1024-byte
-// stride between 8-line atoms (leading offset unused for this layout).
-__device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;                 // leading byte offset (ignored), encoded 1
-  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset: 1024 B
-  d |= (uint64_t)1 << 46;                 // descriptor version for tcgen05
-  d |= (uint64_t)2 << 61;                 // layout: 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor of kind::tf32: D f32, A and B tf32, both K-major.
-__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) |
-         ((uint32_t)(m >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_addr(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
 
 struct TcGramArgs {
   int64_t n;
@@ -157,12 +69,6 @@ __device__ __forceinline__ void tc_tile(const TcGramArgs& a, int tile, int& mb, 
   }
 }
 
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-
 // The tensor cores read an FP32 operand as TF32 by dropping its low 13 bits
 // (a biased, round-toward-zero conversion).  Converter warps rewrite each
 // staged tile first: hi = round-to-nearest TF32 (in place, unbiased), and in
@@ -195,37 +101,10 @@ constexpr int kTcConvThreads = 64;   // warps 2 and 3
 constexpr int kTcThreads = 256;      // warps 0-7
 constexpr int kTcSegSplit = 1;       // stages per accumulation segment in compensated mode
 
-// 16 consecutive 32-bit columns of the calling thread's TMEM lane, without the wait.
-__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
-      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
-      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
-      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
-      "r"(r[15])
-      : "memory");
-}
-
 // TMEM columns: nacc accumulator regions of N columns, then one N-column
 // running total, rounded up to the power of two that tcgen05.alloc takes.
 __host__ __device__ inline int tc_nacc(int N) { return N <= 128 ? 2 : 1; }
-__host__ __device__ inline uint32_t tc_tmem_cols(int N) {
-  const int need = (tc_nacc(N) + 1) * N;
-  uint32_t c = 32;
-  while ((int)c < need) c <<= 1;
-  return c;
-}
+__host__ __device__ inline uint32_t tc_tmem_cols(int N) { return tmem_cols_for((tc_nacc(N) + 1) * N); }
 
 // The accumulator of tcgen05.mma rounds toward zero, so a long sum of
 // same-signed terms (a diagonal of X^T X) drifts low by about 2^-25 per
@@ -368,7 +247,7 @@ tc_gram_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     bool ok = true;
     for (int seg = 0; seg < nseg; ++seg) {
       const int r = seg % nacc;
-      if (!mbar_wait(&acc_full[r], (uint32_t)(seg / nacc) & 1u, a.err)) { ok = false; break; }
+      if (!mbar_wait_warp(&acc_full[r], (uint32_t)(seg / nacc) & 1u, a.err)) { ok = false; break; }
       tc_fence_after();
       const uint32_t acc = tmem + lane_off + (uint32_t)(r * a.N);
       const uint32_t tot = tmem + lane_off + total_col;
@@ -448,17 +327,26 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2D map of an n x p column-major float matrix: box of 32 rows x `cols` columns, 128-byte swizzle.
-static bool encode_map(CUtensorMap* m, const float* ptr, int64_t n, int p, int64_t ld, int cols) {
+bool tma_encoder_available() { return encode_fn() != nullptr; }
+
+bool encode_map_f32(CUtensorMap* m, const float* ptr, uint64_t dim0, uint64_t dim1, uint64_t ld,
+                    uint32_t box0, uint32_t box1, bool swizzle128) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)p};
+  cuuint64_t dims[2] = {(cuuint64_t)dim0, (cuuint64_t)dim1};
   cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
-  cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)cols};
+  cuuint32_t box[2] = {box0, box1};
   cuuint32_t estr[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ptr), dims, strides, box,
-            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// 2D map of an n x p column-major float matrix: box of 32 rows x `cols` columns, 128-byte swizzle.
+static bool encode_map(CUtensorMap* m, const float* ptr, int64_t n, int p, int64_t ld, int cols) {
+  return encode_map_f32(m, ptr, (uint64_t)n, (uint64_t)p, (uint64_t)ld, (uint32_t)kTcK,
+                        (uint32_t)cols, true);
 }
 
 void tc_gram_plan(int64_t n, int p, int with_g, TcGramPlan* pl) {
@@ -481,7 +369,7 @@ void tc_gram_plan(int64_t n, int p, int with_g, TcGramPlan* pl) {
 }
 
 bool tc_gram_supported(const void* X, int64_t ldx, const void* G, int64_t ldg) {
-  return encode_fn() != nullptr && ((uintptr_t)X % 16) == 0 && (ldx % 4) == 0 &&
+  return tma_encoder_available() && ((uintptr_t)X % 16) == 0 && (ldx % 4) == 0 &&
          (G == nullptr || (((uintptr_t)G % 16) == 0 && (ldg % 4) == 0));
 }
 

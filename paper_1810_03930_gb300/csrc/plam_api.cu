@@ -120,6 +120,9 @@ struct plam_handle_s {
   int use_tc = 0;
   TcGramPlan tc{};
   int* tc_err = nullptr;
+  // tensor-core update GEMM (FP32 mode)
+  TcUpdatePlan tcu{};
+  float* msplit = nullptr;
 };
 
 namespace {
@@ -235,11 +238,23 @@ plam_status_t launch_iteration(plam_handle_s* h, T* X, int64_t ldx, int variant,
   CK(launch_gram_finalize<T>(p, nch, (const T*)h->part, h->red, h->B, h->L0, (T*)h->Mt,
                              (T*)h->L0t, h->feas_row, h->st, ip, s));
   if (ev) CK(cudaEventRecord(ev[3], s));
-  CK(launch_update<T>(h->n, p, X, ldx, G, h->ldw, (T*)h->R[0], (T*)h->R[1], h->ldw,
-                      (const T*)h->Mt, (const T*)h->L0t, (const T*)h->coef, h->st, (T*)h->colpart,
-                      (T*)h->totpart, s));
+  int nrt = h->nrt, nct = h->nct;
+  if (sizeof(T) == 4 && h->use_tc && tc_update_supported(X, ldx)) {
+    CK(launch_tc_update(h->n, p, (const float*)X, ldx, (const float*)G, h->ldw, (float*)h->R[0],
+                        (float*)h->R[1], h->ldw, (const float*)h->Mt, (const float*)h->L0t, h->tcu,
+                        h->msplit, (const float*)h->coef, h->st, (float*)h->colpart,
+                        (float*)h->totpart, h->tc_err, h->prm.refine_switch,
+                        h->prm.tensor_cores == 2, s));
+    nrt = h->tcu.nrt;
+    nct = h->tcu.nct;
+    k += 1;   // the TF32 split of M and Psi(C)
+  } else {
+    CK(launch_update<T>(h->n, p, X, ldx, G, h->ldw, (T*)h->R[0], (T*)h->R[1], h->ldw,
+                        (const T*)h->Mt, (const T*)h->L0t, (const T*)h->coef, h->st,
+                        (T*)h->colpart, (T*)h->totpart, s));
+  }
   if (ev) CK(cudaEventRecord(ev[4], s));
-  CK(launch_step_size<T>(h->nrt, h->nct, (const T*)h->colpart, (const T*)h->totpart, h->feas_row,
+  CK(launch_step_size<T>(nrt, nct, (const T*)h->colpart, (const T*)h->totpart, h->feas_row,
                          h->fpart, h->obj.kind == PLAM_OBJ_HARTREE1D ? h->nfpart : 0, h->sums,
                          h->ticket, h->st, h->nubuf, (T*)h->coef, h->hist, ip, s));
   if (ev) CK(cudaEventRecord(ev[5], s));
@@ -315,7 +330,7 @@ void free_handle(plam_handle_s* h) {
                  h->hist,
                  h->rho, h->blk, h->y, h->fpart, h->W, h->Z, h->info, h->feas_dev, h->Qtmp,
                  h->dotpart, h->r_halo, h->r_blk, h->r_part, h->r_red, h->r_dots, h->r_dred,
-                 h->r_bar, h->r_err, h->tc_err};
+                 h->r_bar, h->r_err, h->tc_err, h->msplit};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (h->st_host) cudaFreeHost(h->st_host);
@@ -472,6 +487,7 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
   if (prm->precision == PLAM_PREC_FP32 &&
       (prm->tensor_cores >= 1 || (prm->tensor_cores == -1 && p >= 128))) {
     tc_gram_plan(n, (int)p, 1, &h->tc);
+    tc_update_plan(n, (int)p, &h->tcu);
     h->use_tc = 1;
   }
   const int part_chunks = h->use_tc && h->tc.nchunks > h->nchunks ? h->tc.nchunks : h->nchunks;
@@ -483,6 +499,7 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
   bool ok = alloc(&h->G, np_bytes) && alloc(&h->R[0], np_bytes) && alloc(&h->R[1], np_bytes) &&
             alloc(&h->part, (size_t)part_chunks * 2 * pp * esz) &&
             alloc((void**)&h->tc_err, sizeof(int)) &&
+            (!h->use_tc || alloc((void**)&h->msplit, (size_t)4 * h->tcu.ldm * p * sizeof(float))) &&
             alloc((void**)&h->part64, (size_t)h->nchunks * 2 * pp * sizeof(double)) &&
             alloc((void**)&h->B, pp * sizeof(double)) && alloc((void**)&h->L0, pp * sizeof(double)) &&
             alloc((void**)&h->C, pp * sizeof(double)) && alloc(&h->Mt, pp * esz) &&
@@ -548,6 +565,7 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
     if (e == cudaSuccess) e = preload_objective_kernels();
     if (e == cudaSuccess && h->r_nblk > 0) e = preload_resident_kernels();
     if (e == cudaSuccess && h->use_tc) e = preload_tc_kernels();
+    if (e == cudaSuccess && h->use_tc) e = preload_tc_update_kernels();
     if (e != cudaSuccess) {
       free_handle(h);
       return cuda_fail(e, "kernel preload");

@@ -170,6 +170,26 @@ cudaError_t launch_tc_gram(int64_t n, int p, const float* X, int64_t ldx, const 
                            int64_t ldg, const TcGramPlan& pl, float* part, int* err,
                            const DevState* st, double refine_switch, int force3, cudaStream_t s);
 cudaError_t preload_tc_kernels();
+bool tma_encoder_available();
+
+// Tensor-core update GEMM (FP32 storage): R = G - X M and the KKT residual,
+// with the column and tile dots of launch_update (nrt x 3 x p and
+// nrt x nct x 6 partials, nrt = ceil(n / 128), nct = ceil(p / N)).
+// msplit: 4 x ldm x p floats of scratch for the TF32 parts of M and Psi(C).
+struct TcUpdatePlan {
+  int N, nct, nrt, ldm;
+  uint32_t pipe_bytes;
+  size_t smem;
+};
+void tc_update_plan(int64_t n, int p, TcUpdatePlan* pl);
+bool tc_update_supported(const void* X, int64_t ldx);
+cudaError_t launch_tc_update(int64_t n, int p, const float* X, int64_t ldx, const float* G,
+                             int64_t ldg, float* R0, float* R1, int64_t ldr, const float* Mt,
+                             const float* L0t, const TcUpdatePlan& pl, float* msplit,
+                             const float* coef, const DevState* st, float* colpart,
+                             float* totpart, int* err, double refine_switch, int force3,
+                             cudaStream_t s);
+cudaError_t preload_tc_update_kernels();
 
 // Force the module load of every kernel (lazy loading must not happen inside
 // a stream capture).

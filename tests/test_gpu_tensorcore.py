@@ -137,3 +137,61 @@ def test_tensor_core_solve_reaches_eigenvalue_sum(p, tc):
     assert abs(obj.value(Q) - fstar) <= 1e-6 * abs(fstar)
     assert np.linalg.norm(Q.T @ Q - np.eye(p)) <= 1e-12
     s.close()
+
+
+# ---------------------------------------------------------------- tensor-core update GEMM
+
+
+def _dense_case(n, p, seed):
+    from workloads import workload_dense_trace
+    w = workload_dense_trace(n, p)
+    X0 = w.X0 + 0.02 * np.random.default_rng(seed).standard_normal(w.X0.shape)   # infeasible start
+    return w, X0
+
+
+@pytest.mark.parametrize("n,p", [(3001, 130), (2048, 256), (1000, 40), (777, 1)])
+@pytest.mark.parametrize("variant", ["plam", "pcal"])
+@pytest.mark.parametrize("tc,tol", [("3xtf32", 2e-5), ("tf32", 4e-3)])
+def test_tensor_core_update_three_iterations(n, p, variant, tc, tol):
+    """Three FP32 iterations with the tcgen05 update GEMM R = G - X M (eq. S1) and its epilogue
+    dots (column norms for PCAL's closed form, the Barzilai-Borwein sums of Section 5.1, the KKT
+    residual of Section 3.3) against the FP64 oracle: the steps X^3 - X^0, the step sizes eta^0..2
+    and the relative KKT values agree to the accuracy of the operand rounding (TF32: 2^-11;
+    compensated 3xTF32: FP32 level).  Row blocks of 128 with a ragged tail, column tiles of 128
+    with a ragged tail (p = 130), a single column (p = 1)."""
+    from oracle import objectives as oo
+    from oracle import plam as op
+    from tests.gpu_helpers import gpu_solver, rel_err, to_host
+    w, X0 = _dense_case(n, p, 17)
+    obj = oo.TraceObjective(w.A)
+    beta = 1.5
+    ref = op.solve(obj, X0, variant=variant, beta=beta, tol=0.0, maxit=3)
+    s = gpu_solver(w, "fp32", variant=variant, beta=beta, tol=0.0, maxit=3, final_orth=0,
+                   tensor_cores=tc, refine_switch=0.0, engine="graph")
+    Xd = to_dev(X0, s, ld=(n + 31) // 32 * 32)
+    st, info = s.solve(Xd)
+    hist = s.history()
+    X3 = to_host(Xd, n)
+    X0f = X0.astype(np.float32).astype(np.float64)
+    assert rel_err(X3 - X0f, ref.X - X0) <= 5 * tol
+    eta_ref = np.array([h.eta for h in ref.history[:3]])
+    kkt_ref = np.array([h.kkt for h in ref.history])
+    np.testing.assert_allclose(hist[:3, 4], eta_ref, rtol=5 * tol)
+    np.testing.assert_allclose(hist[:, 2], kkt_ref, rtol=5 * tol)
+    s.close()
+
+
+def test_tensor_core_update_replaces_the_cuda_core_update():
+    """With tensor cores on, one iteration launches the TF32 split of M and the tcgen05 update
+    in place of the CUDA-core update kernel (one launch more than the CUDA-core sequence)."""
+    from tests.gpu_helpers import gpu_solver
+    w, X0 = _dense_case(1024, 128, 3)
+    counts = {}
+    for tc in ("off", "tf32"):
+        s = gpu_solver(w, "fp32", variant="pcal", beta=1.5, tol=0.0, maxit=1, tensor_cores=tc,
+                       engine="graph")
+        Xd = to_dev(X0, s, ld=1024)
+        s.step(Xd)
+        counts[tc] = s.kernel_launches()
+        s.close()
+    assert counts["tf32"] == counts["off"] + 1
