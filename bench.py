@@ -35,6 +35,11 @@ WORKLOADS = {
     "hartree1d": dict(kind="hartree1d", n=20000, p=50, alpha=1.0, quad_scale=0.25, beta=1000.0,
                       tol=1e-6, name="hartree1d_n20000_p50"),
     "dense": dict(kind="dense", n=500, p=20, beta=1.0, tol=1e-6, name="dense_trace_n500_p20"),
+    # 3D Laplacian plus potential on a 64^3 grid, p = 256: FP32 with tensor-core Grams and
+    # update (TF32, compensated 3xTF32 below KKT 1e-3); KKT 1e-5 is where the FP32 path meets
+    # 1e-6 of the optimum.  The FP64 path is timed over its first 30 iterations only.
+    "stencil3d": dict(kind="stencil3d", m=64, n=262144, p=256, beta=1.0, tol=1e-5,
+                      name="stencil3d_n262144_p256", fp64_maxit=30),
 }
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
@@ -199,18 +204,24 @@ def golden_fstar(name):
 
 # ---------------------------------------------------------------- our arm
 
-def make_solver(wl, precision, torch, engine="auto", final_orth=1):
+def make_solver(wl, precision, torch, engine="auto", final_orth=1, maxit=3000):
     from paper_1810_03930_gb300 import Solver
-    kw = dict(variant="pcal", lambda_rule="lambda2", beta=wl["beta"], tol=wl["tol"], maxit=3000,
+    kw = dict(variant="pcal", lambda_rule="lambda2", beta=wl["beta"], tol=wl["tol"], maxit=maxit,
               precision=precision, final_orth=final_orth, graph_iters=16, engine=engine)
+    if wl["kind"] == "stencil3d":
+        m = wl["m"]
+        return Solver(wl["n"], wl["p"], "stencil3d", grid=(m, m, m), V=wl["V"], **kw)
     if wl["kind"] == "hartree1d":
         return Solver(wl["n"], wl["p"], "hartree1d", alpha=wl["alpha"], quad_scale=wl["quad_scale"], **kw)
     return Solver(wl["n"], wl["p"], "dense", A=wl["A"], **kw)
 
 
 def load_inputs(wl):
-    from workloads import workload_dense_trace, workload_hartree1d
-    if wl["kind"] == "hartree1d":
+    from workloads import workload_dense_trace, workload_hartree1d, workload_stencil3d
+    if wl["kind"] == "stencil3d":
+        w = workload_stencil3d(m=wl["m"], p=wl["p"])
+        wl["V"] = w.V
+    elif wl["kind"] == "hartree1d":
         w = workload_hartree1d(n=wl["n"], p=wl["p"], alpha=wl["alpha"], quad_scale=wl["quad_scale"])
     else:
         w = workload_dense_trace(wl["n"], wl["p"])
@@ -218,7 +229,7 @@ def load_inputs(wl):
     return w
 
 
-def timed_solves(solver, X0d, steps, flush, torch, host=None):
+def timed_solves(solver, X0d, steps, flush, torch, host=None, allow_maxit=False):
     """Run `steps` solves; returns (list of ms, list of iters, last Q, last info, launches)."""
     Xw = torch.empty_like(X0d)
     Q = solver.new_matrix(dtype=torch.float64)
@@ -243,7 +254,7 @@ def timed_solves(solver, X0d, steps, flush, torch, host=None):
             Qh.copy_(Q, non_blocking=True)
         e1.record()
         torch.cuda.synchronize()
-        if st not in (0,):
+        if st not in ((0, 2) if allow_maxit else (0,)):
             raise RuntimeError(f"solve did not converge: status {st}, info {info.as_dict()}")
         ms.append(e0.elapsed_time(e1))
         its.append(info.iters)
@@ -327,10 +338,23 @@ def run_ours(args, rank, world, local):
         sol_t.close()
     # ---- FP64 GPU path beside it
     X0d64 = colmajor_to_device(w.X0, torch.float64)
-    timed_solves(sol64, X0d64, 1, flush, torch)
-    ms64, its64, _, info64, _ = timed_solves(sol64, X0d64, max(1, args.fp64_steps), flush, torch)
-    fp64 = {"time_to_kkt_s": statistics.mean(ms64) / 1e3, "iters_per_solve": statistics.mean(its64),
-            "iters_per_s": sum(its64) / (sum(ms64) / 1e3)}
+    if wl.get("fp64_maxit"):
+        # bounded: the first fp64_maxit iterations; time-to-KKT at the mixed path's count
+        sol64b = make_solver(wl, "fp64", torch, final_orth=0, maxit=wl["fp64_maxit"])
+        timed_solves(sol64b, X0d64, 1, flush, torch, allow_maxit=True)
+        ms64, its64, _, _, _ = timed_solves(sol64b, X0d64, 1, flush, torch, allow_maxit=True)
+        sol64b.close()
+        rate64 = sum(its64) / (sum(ms64) / 1e3)
+        fp64 = {"iters_per_s": rate64, "iters_timed": sum(its64),
+                "time_to_kkt_s": statistics.mean(its) / rate64,
+                "time_to_kkt_note": "extrapolated: mixed-path iteration count / FP64 iteration rate "
+                                    f"over its first {wl['fp64_maxit']} iterations"}
+    else:
+        timed_solves(sol64, X0d64, 1, flush, torch)
+        ms64, its64, _, info64, _ = timed_solves(sol64, X0d64, max(1, args.fp64_steps), flush, torch)
+        fp64 = {"time_to_kkt_s": statistics.mean(ms64) / 1e3,
+                "iters_per_solve": statistics.mean(its64),
+                "iters_per_s": sum(its64) / (sum(ms64) / 1e3)}
     # ---- which engine ran the metric: the resident engine is one launch per solve
     launches_per_solve = launches / max(1, args.steps)
     engine = "resident" if launches_per_solve <= 12 else "graph"
@@ -368,10 +392,14 @@ def run_ours(args, rank, world, local):
     kb = kernel_bytes(wl, 4)
     dom = max(kms, key=lambda k: kms[k])
     achieved_g = kb[dom] / (kms[dom] * 1e-3) / 1e9
-    kernel_names = {"objective": "hartree_grad", "gram_partial": "gram_partial",
-                    "gram_finalize": "gram_finalize", "update": "update", "step_size": "step_size",
-                    "primal_update": "primal_update"}
-    roofline_graph = {"bound": "hbm", "kernel": dom, "achieved": achieved_g, "peak": peak_hbm,
+    tc = wl["kind"] == "stencil3d"          # p >= 128: the tensor-core Grams and update run
+    kernel_names = {"objective": {"hartree1d": "hartree_grad", "stencil3d": "stencil_grad"}.get(
+                        wl["kind"], "dense_grad"),
+                    "gram_partial": "tc_gram" if tc else "gram_partial",
+                    "gram_finalize": "gram_finalize", "update": "tc_update" if tc else "update",
+                    "step_size": "step_size", "primal_update": "primal_update"}
+    roofline_graph = {"bound": "hbm", "kernel": kernel_names[dom], "achieved": achieved_g,
+                      "peak": peak_hbm,
                       "unit": "GB/s", "frac": achieved_g / peak_hbm, "peak_source": peak_kind,
                       "traffic": recorded_traffic(kernel_names[dom], wl["name"]),
                       "alg_bytes_per_launch": kb[dom], "launch_ms": kms[dom]}
@@ -388,8 +416,10 @@ def run_ours(args, rank, world, local):
     out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": wl["name"], "objective": "1/4 tr(X^T L X) + alpha/4 rho^T L^-1 rho"
-                      if wl["kind"] == "hartree1d" else "1/2 tr(X^T A X)",
+           "config": {"workload": wl["name"], "objective": {
+                          "hartree1d": "1/4 tr(X^T L X) + alpha/4 rho^T L^-1 rho",
+                          "stencil3d": "1/2 tr(X^T (L3 + Diag(V)) X), 7-point Dirichlet L3 on 64^3, "
+                                       "V iid U[0,1]"}.get(wl["kind"], "1/2 tr(X^T A X)"),
                       "n": wl["n"], "p": wl["p"], "solver": "PCAL eq.(lambda2), ABB",
                       "beta": wl["beta"], "tol_kkt_rel": wl["tol"], "final_orth": "FP64 Cholesky-QR",
                       "l2": "flushed before every step (256 MB write)",

@@ -75,7 +75,8 @@ enum { PLAM_PREC_FP64 = 0, PLAM_PREC_FP32 = 1 };
  *   HARTREE1D  f = q tr(X^T L X) + (alpha/4) rho^T L^{-1} rho,     (Problem 1, KS form eq. KS-energy)
  *              rho = diag(X X^T), L = tridiag(-1,2,-1) Dirichlet
  *   STENCIL3D  f = 1/2 tr(X^T (L3 + Diag(V)) X), L3 the 7-point Dirichlet
- *              Laplacian on nx*ny*nz points, index i = x + nx*(y + ny*z). */
+ *              Laplacian on nx*ny*nz points, index i = x + nx*(y + ny*z);
+ *              nx*ny*nz must equal n and stay below 2^31. */
 enum { PLAM_OBJ_DENSE = 0, PLAM_OBJ_HARTREE1D = 1, PLAM_OBJ_STENCIL3D = 2 };
 /* How plam_solve runs the loop.  GRAPH: the kernel sequence of one iteration,
  * replayed from a captured CUDA graph (any size).  RESIDENT: one cooperative

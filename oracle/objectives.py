@@ -19,6 +19,10 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
   QuadLinearObjective Problem 2 (eq. OCQP): f = 1/2 tr(X^T A X) + tr(G^T X).
   DenseHartreeObjective Problem 1 exactly (eq. nonlinear): dense symmetric L and
                      its pseudo-inverse L^+ (numpy.linalg.pinv), coefficient q.
+  trace_min_optimum  the optimum of a trace problem f = 1/2 tr(X^T H X) over
+                     X^T X = I_p: half the sum of the p smallest eigenvalues of H
+                     (Ky Fan), by a shift-invert Lanczos eigensolve (ARPACK) of a
+                     sparse H.
 """
 from __future__ import annotations
 
@@ -167,3 +171,19 @@ def objective_for(w) -> object:
     if w.kind == "stencil3d":
         return Stencil3DObjective(w.m, w.V)
     raise ValueError(w.kind)
+
+
+def trace_min_optimum(H, p: int, shift: float | None = None):
+    """min { 1/2 tr(X^T H X) : X^T X = I_p } = 1/2 (lambda_1 + ... + lambda_p) for symmetric H
+    (Ky Fan's minimum principle), with the p smallest eigenvalues from ARPACK in shift-invert
+    mode about `shift` (default: a Gershgorin lower bound of the spectrum, so that the
+    eigenvalues nearest the shift are the smallest ones).  Returns (f*, eigenvalues)."""
+    import scipy.sparse.linalg as spla
+    H = sp.csc_matrix(H)
+    if shift is None:
+        d = H.diagonal()
+        off = np.asarray(abs(H).sum(axis=1)).ravel() - np.abs(d)
+        shift = float(np.min(d - off)) - 1e-3
+    ev = spla.eigsh(H, k=p, sigma=shift, which="LM", return_eigenvectors=False)
+    ev = np.sort(ev)
+    return 0.5 * float(ev.sum()), ev

@@ -187,31 +187,57 @@ hartree_grad_kernel(int64_t n, int p, double alpha, double q, double inv_np1, co
 
 // ---------------------------------------------------------------- 3D stencil
 
+// One CTA of 32 x 8 threads owns a 32 (x) x 8 (y) tile of one column of X
+// and marches through kStencilZ planes of z, keeping the planes z - 1, z and
+// z + 1 of its point in registers; x neighbours come from the adjacent lanes
+// of the warp (a warp is one x row), y neighbours through the L1 cache.  Each
+// element of X is read once from DRAM and G is written once.
+constexpr int kStencilZ = 16;
+
 template <typename T>
-__global__ void stencil_grad_kernel(int nx, int ny, int nz, int p, const T* __restrict__ V,
-                                    const T* __restrict__ X, int64_t ldx, T* __restrict__ G,
-                                    int64_t ldg, const DevState* __restrict__ st) {
+__global__ void __launch_bounds__(256)
+stencil_grad_kernel(int nx, int ny, int nz, int p, const T* __restrict__ V,
+                    const T* __restrict__ X, int64_t ldx, T* __restrict__ G, int64_t ldg,
+                    const DevState* __restrict__ st) {
   if (st != nullptr && st->stop != kRunning) return;
-  const int64_t n = (int64_t)nx * ny * nz;
-  const int64_t sxy = (int64_t)nx * ny;
-  const int c = blockIdx.y;
-  const T* xc = X + (int64_t)c * ldx;
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
-       r += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t z = r / sxy;
-    const int64_t rem = r - z * sxy;
-    const int64_t y = rem / nx;
-    const int64_t x = rem - y * nx;
-    const T xv = xc[r];
-    T nb = T(0);
-    if (x > 0) nb += xc[r - 1];
-    if (x + 1 < nx) nb += xc[r + 1];
-    if (y > 0) nb += xc[r - nx];
-    if (y + 1 < ny) nb += xc[r + nx];
-    if (z > 0) nb += xc[r - sxy];
-    if (z + 1 < nz) nb += xc[r + sxy];
-    const T d = T(6) + (V ? V[r] : T(0));
-    G[r + (int64_t)c * ldg] = fma(d, xv, -nb);
+  const int nzb = (nz + kStencilZ - 1) / kStencilZ;
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * 8 + threadIdx.y;
+  const bool in = x < nx && y < ny;
+  const int sxy = nx * ny;
+  for (int zc = blockIdx.z; zc < nzb * p; zc += gridDim.z) {
+    const int c = zc / nzb;
+    const int z0 = (zc - c * nzb) * kStencilZ;
+    const int z1 = min(nz, z0 + kStencilZ);
+    const T* xc = X + (int64_t)c * ldx;
+    T* gc = G + (int64_t)c * ldg;
+    int i = x + nx * (y + ny * z0);
+    T prev = T(0), cur = T(0);
+    if (in) {
+      prev = z0 > 0 ? __ldg(xc + i - sxy) : T(0);
+      cur = __ldg(xc + i);
+    }
+#pragma unroll 4
+    for (int z = z0; z < z1; ++z, i += sxy) {
+      T next = T(0), ym = T(0), yp = T(0), v = T(0);
+      if (in) {
+        if (z + 1 < nz) next = __ldg(xc + i + sxy);
+        if (y > 0) ym = __ldg(xc + i - nx);
+        if (y + 1 < ny) yp = __ldg(xc + i + nx);
+        if (V) v = __ldg(V + i);
+      }
+      T xm = __shfl_up_sync(0xffffffffu, cur, 1);
+      T xp = __shfl_down_sync(0xffffffffu, cur, 1);
+      if (threadIdx.x == 0) xm = (in && x > 0) ? __ldg(xc + i - 1) : T(0);
+      if (threadIdx.x == 31) xp = (in && x + 1 < nx) ? __ldg(xc + i + 1) : T(0);
+      if (x + 1 >= nx) xp = T(0);
+      if (in) {
+        const T nb = ((((xm + xp) + ym) + yp) + prev) + next;
+        gc[i] = fma(T(6) + v, cur, -nb);
+      }
+      prev = cur;
+      cur = next;
+    }
   }
 }
 
@@ -241,12 +267,11 @@ cudaError_t launch_hartree_grad(int64_t n, int p, double alpha, double q, const 
 template <typename T>
 cudaError_t launch_stencil_grad(int nx, int ny, int nz, int p, const T* V, const T* X, int64_t ldx,
                                 T* G, int64_t ldg, const DevState* st, cudaStream_t s) {
-  const int64_t n = (int64_t)nx * ny * nz;
-  const int threads = 256;
-  int64_t bx = (n + threads - 1) / threads;
-  if (bx > 4096) bx = 4096;
-  dim3 grid((unsigned)bx, p);
-  stencil_grad_kernel<T><<<grid, threads, 0, s>>>(nx, ny, nz, p, V, X, ldx, G, ldg, st);
+  const int nzb = (nz + kStencilZ - 1) / kStencilZ;
+  int64_t gz = (int64_t)nzb * p;
+  if (gz > 65535) gz = 65535;
+  dim3 grid((unsigned)((nx + 31) / 32), (unsigned)((ny + 7) / 8), (unsigned)gz);
+  stencil_grad_kernel<T><<<grid, dim3(32, 8), 0, s>>>(nx, ny, nz, p, V, X, ldx, G, ldg, st);
   return cudaGetLastError();
 }
 

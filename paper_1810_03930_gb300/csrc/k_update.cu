@@ -334,11 +334,27 @@ step_size_kernel(int nrt, int nct, const T* __restrict__ colpart, const T* __res
   }
 }
 
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { typedef float4 type; static constexpr int n = 4; };
+template <> struct Vec16<double> { typedef double2 type; static constexpr int n = 2; };
+
+__device__ __forceinline__ float4 axpy_scale(float4 x, float4 r, float ie, float inu) {
+  return make_float4((x.x - r.x * ie) * inu, (x.y - r.y * ie) * inu, (x.z - r.z * ie) * inu,
+                     (x.w - r.w * ie) * inu);
+}
+__device__ __forceinline__ double2 axpy_scale(double2 x, double2 r, double ie, double inu) {
+  return make_double2((x.x - r.x * ie) * inu, (x.y - r.y * ie) * inu);
+}
+
+// vec = 1: columns start on 16-byte boundaries, so each thread moves whole
+// 16-byte vectors (four floats or two doubles) and the tail of a column, if
+// any, is done element by element.
 template <typename T>
-__global__ void primal_update_kernel(int64_t n, int p, T* __restrict__ X, int64_t ldx,
-                                     const T* __restrict__ R0, const T* __restrict__ R1, int64_t ldr,
-                                     const T* __restrict__ coef, const DevState* __restrict__ st,
-                                     int variant) {
+__global__ void __launch_bounds__(256)
+primal_update_kernel(int64_t n, int p, T* __restrict__ X, int64_t ldx,
+                     const T* __restrict__ R0, const T* __restrict__ R1, int64_t ldr,
+                     const T* __restrict__ coef, const DevState* __restrict__ st, int variant,
+                     int vec) {
   if (st->stop != kRunning) return;
   const int km1 = st->k - 1;                 // the step kernel already counted this update
   const T* R = (km1 & 1) ? R1 : R0;
@@ -348,10 +364,18 @@ __global__ void primal_update_kernel(int64_t n, int p, T* __restrict__ X, int64_
   const T inu = (variant == 1) ? cf[1 + c] : T(1);
   T* xc = X + (int64_t)c * ldx;
   const T* rc = R + (int64_t)c * ldr;
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
-       r += (int64_t)gridDim.x * blockDim.x) {
-    xc[r] = (xc[r] - rc[r] * ie) * inu;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (vec) {
+    typedef typename Vec16<T>::type V;
+    constexpr int W = Vec16<T>::n;
+    const int64_t nv = n / W;
+    V* xv = reinterpret_cast<V*>(xc);
+    const V* rv = reinterpret_cast<const V*>(rc);
+    for (int64_t i = r; i < nv; i += stride) xv[i] = axpy_scale(xv[i], __ldg(rv + i), ie, inu);
+    r += nv * W;
   }
+  for (; r < n; r += stride) xc[r] = (xc[r] - rc[r] * ie) * inu;
 }
 
 // ---------------------------------------------------------------- launchers
@@ -393,7 +417,10 @@ cudaError_t launch_primal_update(int64_t n, int p, T* X, int64_t ldx, const T* R
   if (bx > cap) bx = cap;
   if (bx < 1) bx = 1;
   dim3 grid((unsigned)bx, p);
-  primal_update_kernel<T><<<grid, threads, 0, s>>>(n, p, X, ldx, R0, R1, ldr, coef, st, variant);
+  const int vec = (ldx * (int64_t)sizeof(T)) % 16 == 0 && (ldr * (int64_t)sizeof(T)) % 16 == 0 &&
+                  (uintptr_t)X % 16 == 0 && (uintptr_t)R0 % 16 == 0 && (uintptr_t)R1 % 16 == 0;
+  primal_update_kernel<T><<<grid, threads, 0, s>>>(n, p, X, ldx, R0, R1, ldr, coef, st, variant,
+                                                   vec);
   return cudaGetLastError();
 }
 

@@ -455,7 +455,8 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
       break;
     case PLAM_OBJ_STENCIL3D:
       if (obj->nx < 1 || obj->ny < 1 || obj->nz < 1 ||
-          (int64_t)obj->nx * obj->ny * obj->nz != n || (obj->V && !aligned(obj->V, esz)))
+          (int64_t)obj->nx * obj->ny * obj->nz != n || n > 2147483647 ||
+          (obj->V && !aligned(obj->V, esz)))
         return PLAM_ERR_INVALID;
       break;
     default:

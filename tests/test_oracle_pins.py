@@ -368,3 +368,22 @@ def test_orth_step_table_pattern(variant):
     assert r.feas_orth < 1e-13
     assert abs(r.f_orth - r.f_stop) / abs(r.f_stop) < 1e-7
     assert abs(r.kkt_orth - r.kkt_stop) <= 0.05 * r.kkt_stop
+
+
+def test_trace_min_optimum_against_dense_eigensolve_and_closed_form():
+    """oracle.objectives.trace_min_optimum (shift-invert Lanczos) against (i) a dense LAPACK
+    eigensolve of a random-potential 3D stencil and (ii) the closed-form spectrum of the
+    constant-potential Dirichlet Laplacian, 2 - 2 cos(pi t / (m + 1)) summed over three axes."""
+    rng = np.random.default_rng(42)
+    m, p = 7, 12
+    V = rng.uniform(0.0, 1.0, m ** 3)
+    H = oo.Stencil3DObjective(m, V).H
+    f, ev = oo.trace_min_optimum(H, p)
+    ev_dense = np.linalg.eigvalsh(H.toarray())
+    np.testing.assert_allclose(ev, ev_dense[:p], rtol=1e-11, atol=1e-11)
+    assert abs(f - 0.5 * ev_dense[:p].sum()) <= 1e-11 * abs(f)
+    c = 0.3
+    one = [2 - 2 * math.cos(math.pi * t / (m + 1)) for t in range(1, m + 1)]
+    closed = sorted(one[a] + one[b] + one[d] + c for a in range(m) for b in range(m) for d in range(m))
+    f2, _ = oo.trace_min_optimum(oo.Stencil3DObjective(m, np.full(m ** 3, c)).H, p)
+    assert abs(f2 - 0.5 * sum(closed[:p])) <= 1e-11 * f2
