@@ -8,10 +8,11 @@
 // storage), so a TMA box of 32 rows x 128 (or N) columns with 128-byte
 // swizzle lands in shared memory exactly in the canonical K-major SW128
 // layout: one 128-byte line per column, 8-line atoms of 1024 bytes.
-//   warp 0, one thread : TMA producer, 4-stage ring of (A, B) tiles
-//   warp 1, one thread : MMA issuer, 4 x tcgen05.mma (K = 8 each) per stage,
-//                        tcgen05.commit releases the stage
-//   warps 2-3          : convert each landed stage to round-to-nearest TF32 (and
+//   warp 0, one thread : TMA producer, ring of 6 (A, B) pairs (3 stages of
+//                        hi + lo pairs in compensated mode)
+//   warp 1, one thread : MMA issuer, 4 x tcgen05.mma (K = 8 each) per stage
+//                        (12 when compensated), tcgen05.commit releases it
+//   warps 2-3, 8-11    : convert each landed stage to round-to-nearest TF32 (and
 //                        split it into hi + lo in compensated mode); warp 2
 //                        also allocates / frees tensor memory (TMEM)
 //   warps 4-7          : accumulator warps: add each finished accumulation
@@ -33,7 +34,7 @@ namespace plam {
 
 constexpr int kTcM = 128;          // rows of the accumulator (columns of X per tile)
 constexpr int kTcK = 32;           // rows of X per stage (128 bytes of FP32 per line)
-constexpr int kTcStages = 4;
+constexpr int kTcStages = 6;        // (A, B) pairs of shared memory: 6 plain stages or 3 compensated
 
 struct TcGramArgs {
   int64_t n;
@@ -97,8 +98,8 @@ __device__ __forceinline__ void convert_tile(float* tile, float* lo, int nfloat4
   }
 }
 
-constexpr int kTcConvThreads = 64;   // warps 2 and 3
-constexpr int kTcThreads = 256;      // warps 0-7
+constexpr int kTcConvThreads = 192;  // warps 2, 3 and 8-11
+constexpr int kTcThreads = 384;      // warps 0-11
 constexpr int kTcSegSplit = 1;       // stages per accumulation segment in compensated mode
 
 // TMEM columns: nacc accumulator regions of N columns, then one N-column
@@ -224,9 +225,9 @@ tc_gram_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       counters[1] = kt + 1;
     }
     mma_commit(done);   // arrives once every issued MMA has completed
-  } else if (warp == 2 || warp == 3) {
+  } else if (warp == 2 || warp == 3 || warp >= 8) {
     // converters: round to TF32 (and split) each landed stage in place
-    const int tid = threadIdx.x - 64;
+    const int tid = (warp < 8 ? warp - 2 : warp - 6) * 32 + lane;
     for (int kt = 0; kt < KT; ++kt) {
       const int s = kt % nst;
       const uint32_t ph = (uint32_t)(kt / nst) & 1u;
@@ -329,6 +330,14 @@ static EncodeTiledFn encode_fn() {
 
 bool tma_encoder_available() { return encode_fn() != nullptr; }
 
+int device_sm_count() {
+  int dev = 0, cnt = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&cnt, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || cnt < 1)
+    cnt = 1;
+  return cnt;
+}
+
 bool encode_map_f32(CUtensorMap* m, const float* ptr, uint64_t dim0, uint64_t dim1, uint64_t ld,
                     uint32_t box0, uint32_t box1, bool swizzle128) {
   EncodeTiledFn fn = encode_fn();
@@ -350,14 +359,15 @@ static bool encode_map(CUtensorMap* m, const float* ptr, int64_t n, int p, int64
 }
 
 void tc_gram_plan(int64_t n, int p, int with_g, TcGramPlan* pl) {
-  pl->N = p >= 256 ? 256 : ((p + 15) / 16) * 16;
+  pl->N = p >= 128 ? 128 : ((p + 15) / 16) * 16;
   pl->nmb = (p + kTcM - 1) / kTcM;
   pl->nnb = (p + pl->N - 1) / pl->N;
   int nbt = 0;
   for (int mb = 0; mb < pl->nmb; ++mb) nbt += pl->nnb - (mb * kTcM) / pl->N;
   pl->nbt = nbt;
   pl->ntiles = nbt + (with_g ? pl->nmb * pl->nnb : 0);
-  int64_t nch = (152 + pl->ntiles - 1) / pl->ntiles;     // one wave of one CTA per SM
+  // one wave of one CTA per SM: chunks x tiles <= SMs (a second, partial wave doubles the time)
+  int64_t nch = device_sm_count() / pl->ntiles;
   const int64_t max_ch = (n + kTcK - 1) / kTcK;
   if (nch > max_ch) nch = max_ch;
   if (nch < 1) nch = 1;

@@ -8,25 +8,31 @@
 // ||K||^2, ||G||^2, <X,G> for the Barzilai-Borwein step (Section 5.1), with
 // S_c = (1 - nu^{k-1}_c) X^k_c - R^{k-1}_c / eta^{k-1}, Y = R^k - R^{k-1}.
 //
-// One CTA computes a 128-row x N-column tile of both products, with both
-// accumulators (and their running totals) in tensor memory.  X is column-major,
-// so for this product its contiguous index (the row) is an M index, not the
-// contraction index.  TMA lands each 128-row x 32-column slice of X as it is,
-// and converter warps transpose it into the canonical K-major 128-byte-swizzle
-// layout while rounding it to nearest TF32 (and splitting off the TF32
-// remainder in compensated mode), so that every MMA operand uses the K-major
-// form.  M and Psi(C) arrive from a small kernel that stores their rounded
-// TF32 parts (hi, lo) once per iteration, and TMA loads those in K-major form.
-//   warp 0, one thread : TMA producer
-//   warp 1, one thread : MMA issuer (2 products x 1 or 3 MMAs per 8 inner indices)
-//   warps 2-3          : converters (transpose + round + split of X)
-//   warps 4-7          : accumulator warps; epilogue
-// Compensated (3xTF32) mode sums each 32-index segment from zero and adds it
-// into the running total with round-to-nearest FP32 arithmetic, because the
-// tensor-core accumulator truncates (see the Gram kernel).
+// K is formed as R - X E with E = Psi(C) - M (= beta (B - I) - Diag(d)), which
+// vanishes as the iterate converges: X E is then small against R and G, so it
+// is taken in plain TF32 while X M is compensated (3xTF32) near convergence.
 //
-// Every mbarrier wait is bounded; an expired wait raises *err, the CTA lets
-// its copies in flight land, frees its tensor memory and returns.
+// Persistent and warp-specialised: one CTA per SM walks 128-row x N-column
+// tiles of R; its tensor memory holds two tiles' accumulators (X M, X E), so
+// the epilogue of one tile overlaps the loads and MMAs of the next.
+//   warp 0, one thread   : TMA producer of the K-loop stages
+//   warp 1, one thread   : MMA issuer
+//   warps 2, 3, 8, 9     : converters.  X is column-major, so for this product
+//                          its contiguous index (the row) is an M index; TMA
+//                          lands each 128-row x 32-column slice as it is and
+//                          the converters transpose it in place into the
+//                          canonical K-major 128-byte-swizzle layout, rounded
+//                          to nearest TF32 (and split into hi + lo when
+//                          compensated)
+//   warps 4-7            : epilogue (TMEM lane quarter = warp mod 4); one of
+//                          them streams the tile's X, G and R^{k-1} through a
+//                          two-slot ring of 16-column TMA copies
+// M, its TF32 remainder and E arrive from a small kernel that stores their
+// rounded TF32 parts once per iteration.
+//
+// Every wait is bounded; an expired wait raises *err, every role leaves its
+// loop at the same point of the protocol, the CTA lets its copies in flight
+// land, frees its tensor memory and returns.
 #include "plam_device.cuh"
 #include "tc_ptx.cuh"
 
@@ -34,18 +40,15 @@ namespace plam {
 
 constexpr int kUpM = 128;          // rows of X per tile (TMEM lanes)
 constexpr int kUpK = 32;           // inner indices per stage
-constexpr int kUpThreads = 256;
-constexpr int kUpConvThreads = 64;
+constexpr int kUpThreads = 320;    // 10 warps
+constexpr int kUpConvThreads = 128;
 constexpr int kUpMaxStages = 4;
-constexpr int kUpAux = 256;        // barriers, TMEM address, counters
+constexpr int kUpChunk = 16;       // epilogue columns per ring slot
+constexpr int kUpAux = 256;        // barriers, TMEM address, flags
 
 struct TcUpdateArgs {
   int64_t n;
-  int p, N, nct;
-  const float* X;
-  int64_t ldx;
-  const float* G;
-  int64_t ldg;
+  int p, N, nct, ntiles;
   float* R0;
   float* R1;
   int64_t ldr;
@@ -54,7 +57,7 @@ struct TcUpdateArgs {
   float* colpart;
   float* totpart;
   int* err;
-  uint32_t pipe_bytes;     // shared memory available to the stages
+  uint32_t pipe_bytes;     // shared memory of the K-loop stages
   double refine_switch;
   int force3;
 };
@@ -95,15 +98,30 @@ __device__ __forceinline__ void warp_sum48(float (&v)[48], int lane) {
   for (int j = 0; j < 3; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], 1);
 }
 
-__device__ __forceinline__ uint32_t up_stage_bytes(int N, bool split) {
-  const uint32_t XR = kUpM * kUpK * 4, A = kUpM * kUpK * 4, BT = (uint32_t)N * kUpK * 4;
-  return split ? XR + 2 * A + 4 * BT : XR + A + 2 * BT;
+// Stage layout (bytes): plain [A hi = landed X][M hi][E hi];
+// compensated [A hi][A lo = landed X][M hi][E hi][M lo].
+__host__ __device__ inline uint32_t up_stage_bytes(int N, bool split) {
+  const uint32_t A = kUpM * kUpK * 4, BT = (uint32_t)N * kUpK * 4;
+  return split ? 2 * A + 3 * BT : A + 2 * BT;
+}
+__host__ __device__ inline uint32_t up_ring_bytes() { return 2u * 3u * kUpM * kUpChunk * 4u; }
+__host__ __device__ inline uint32_t up_red_bytes(int N) { return (12u * N + 24u) * 4u; }
+
+__device__ __forceinline__ void named_bar(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Converter thread index (0..127) of warps 2, 3, 8, 9.
+__device__ __forceinline__ int conv_tid(int warp, int lane) {
+  return (warp < 8 ? warp - 2 : warp - 6) * 32 + lane;
 }
 
 __global__ void __launch_bounds__(kUpThreads, 1)
 tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapMh,
-                 const __grid_constant__ CUtensorMap mapMl, const __grid_constant__ CUtensorMap mapLh,
-                 const __grid_constant__ CUtensorMap mapLl, TcUpdateArgs a) {
+                 const __grid_constant__ CUtensorMap mapMl, const __grid_constant__ CUtensorMap mapEh,
+                 const __grid_constant__ CUtensorMap mapXe, const __grid_constant__ CUtensorMap mapGe,
+                 const __grid_constant__ CUtensorMap mapR0e, const __grid_constant__ CUtensorMap mapR1e,
+                 TcUpdateArgs a) {
   if (a.st->stop != kRunning) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t pad = (1024u - (smem_addr(smem_raw) & 1023u)) & 1023u;
@@ -111,31 +129,33 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   const bool split = a.force3 || (a.refine_switch > 0.0 && a.st->k > 0 &&
                                   a.st->kkt < a.refine_switch);
   const int N = a.N;
-  const uint32_t XR = kUpM * kUpK * 4, AB = kUpM * kUpK * 4, BT = (uint32_t)N * kUpK * 4;
+  const uint32_t A = kUpM * kUpK * 4, BT = (uint32_t)N * kUpK * 4;
   const uint32_t STAGE = up_stage_bytes(N, split);
   int nst = (int)(a.pipe_bytes / STAGE);
   if (nst > kUpMaxStages) nst = kUpMaxStages;
-  // stage layout: [X as landed][A hi][A lo][B1 hi][B2 hi][B1 lo][B2 lo] (lo parts: split only)
-  const uint32_t oAh = XR, oAl = XR + AB;
-  const uint32_t oB1h = split ? XR + 2 * AB : XR + AB;
-  const uint32_t oB2h = oB1h + BT, oB1l = oB2h + BT, oB2l = oB1l + BT;
-  const uint32_t tx_bytes = XR + (split ? 4 : 2) * BT;
-  uint64_t* full = reinterpret_cast<uint64_t*>(base + a.pipe_bytes);
+  const uint32_t oAh = 0, oAl = A, oRaw = split ? A : 0;
+  const uint32_t oB1h = split ? 2 * A : A, oB2h = oB1h + BT, oB1l = oB2h + BT;
+  const uint32_t tx_bytes = A + (split ? 3u : 2u) * BT;
+  unsigned char* ring = base + a.pipe_bytes;                        // [2 slots][X | G | R^{k-1}]
+  const uint32_t EPC = kUpM * kUpChunk * 4;                          // one 128 x 16 operand chunk
+  float* colred = reinterpret_cast<float*>(ring + up_ring_bytes());  // [4][3][N]
+  float* wsum = colred + 12 * N;                                     // [4][6]
+  uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(colred) +
+                                               up_red_bytes(N));
   uint64_t* conv = full + kUpMaxStages;
   uint64_t* empty = conv + kUpMaxStages;
-  uint64_t* acc_full = empty + kUpMaxStages;
-  uint64_t* acc_empty = acc_full + 1;
-  uint64_t* done = acc_empty + 1;
+  uint64_t* tfull = empty + kUpMaxStages;    // [2] accumulators of a tile complete
+  uint64_t* tempty = tfull + 2;              // [2] epilogue has read them
+  uint64_t* epfull = tempty + 2;             // [2] ring slot landed
+  uint64_t* done = epfull + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
-  int* counters = reinterpret_cast<int*>(tmem_slot + 1);   // [issued, consumed]
-
-  const int rb = blockIdx.x / a.nct, ct = blockIdx.x % a.nct;
-  const int64_t r0 = (int64_t)rb * kUpM;
-  const int c0 = ct * N;
-  const int KT = (a.p + kUpK - 1) / kUpK;
-  const int nseg = split ? KT : 1;
+  int* flags = reinterpret_cast<int*>(tmem_slot + 1);   // [epilogue abort, converter abort,
+                                                        //  stages issued, ring chunks issued]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int KT = (a.p + kUpK - 1) / kUpK;
+  const int ntl = (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   const uint32_t ncols = tmem_cols_for(4 * N);
+  const int kst = a.st->k;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kUpMaxStages; ++s) {
@@ -143,11 +163,13 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       mbar_init(&conv[s], kUpConvThreads);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 128);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 128);
+      mbar_init(&epfull[b], 1);
+    }
     mbar_init(done, 1);
-    counters[0] = 0;
-    counters[1] = 0;
+    flags[0] = 0; flags[1] = 0; flags[2] = 0; flags[3] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 2) {
@@ -161,189 +183,177 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  // TMEM columns: [acc X M][acc X Psi(C)][total X M][total X Psi(C)]
-  const uint32_t cAcc1 = 0, cAcc2 = (uint32_t)N, cTot1 = 2u * N, cTot2 = 3u * N;
 
-  if (warp == 0 && lane == 0) {
-    for (int kt = 0; kt < KT; ++kt) {
-      const int s = kt % nst;
-      const uint32_t ph = (uint32_t)(kt / nst) & 1u;
-      if (!mbar_wait(&empty[s], ph ^ 1u, a.err)) break;
-      unsigned char* sb = base + s * STAGE;
-      mbar_arrive_expect_tx(&full[s], tx_bytes);
-      const int k0 = kt * kUpK;
-      tma_load_2d(sb, &mapX, &full[s], (int)r0, k0);
-      tma_load_2d(sb + oB1h, &mapMh, &full[s], k0, c0);
-      tma_load_2d(sb + oB2h, &mapLh, &full[s], k0, c0);
-      if (split) {
-        tma_load_2d(sb + oB1l, &mapMl, &full[s], k0, c0);
-        tma_load_2d(sb + oB2l, &mapLl, &full[s], k0, c0);
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- producer: the K-loop stages of every tile of this CTA
+      int gs = 0;
+      bool ok = true;
+      for (int lt = 0; lt < ntl && ok; ++lt) {
+        const int tile = (int)blockIdx.x + lt * (int)gridDim.x;
+        const int r0 = (tile / a.nct) * kUpM, c0 = (tile % a.nct) * N;
+        for (int kt = 0; kt < KT; ++kt, ++gs) {
+          const int s = gs % nst;
+          if (!mbar_wait(&empty[s], ((uint32_t)(gs / nst) & 1u) ^ 1u, a.err)) { ok = false; break; }
+          unsigned char* sb = base + s * STAGE;
+          mbar_arrive_expect_tx(&full[s], tx_bytes);
+          const int k0 = kt * kUpK;
+          tma_load_2d(sb + oRaw, &mapX, &full[s], r0, k0);
+          tma_load_2d(sb + oB1h, &mapMh, &full[s], k0, c0);
+          tma_load_2d(sb + oB2h, &mapEh, &full[s], k0, c0);
+          if (split) tma_load_2d(sb + oB1l, &mapMl, &full[s], k0, c0);
+          flags[2] = gs + 1;
+        }
       }
-      counters[0] = kt + 1;
     }
-  } else if (warp == 1 && lane == 0) {
-    const uint32_t idesc = idesc_tf32(kUpM, N);
-    for (int kt = 0; kt < KT; ++kt) {
-      const int seg = split ? kt : 0;
-      const bool first = split || kt == 0;
-      if (split && seg >= 1) {   // the accumulator warps have added the previous segment
-        if (!mbar_wait(acc_empty, (uint32_t)(seg - 1) & 1u, a.err)) break;
-        tc_fence_after();
-      }
-      const int s = kt % nst;
-      const uint32_t ph = (uint32_t)(kt / nst) & 1u;
-      if (!mbar_wait(&conv[s], ph, a.err)) break;
-      tc_fence_after();
-      const uint32_t sb = smem_addr(base + s * STAGE);
-      const uint64_t ah = sdesc_k_sw128(sb + oAh), al = sdesc_k_sw128(sb + oAl);
-      const uint64_t m1h = sdesc_k_sw128(sb + oB1h), m2h = sdesc_k_sw128(sb + oB2h);
-      const uint64_t m1l = sdesc_k_sw128(sb + oB1l), m2l = sdesc_k_sw128(sb + oB2l);
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer
+      const uint32_t idesc = idesc_tf32(kUpM, N);
+      int gs = 0;
+      bool ok = true;
+      for (int lt = 0; lt < ntl && ok; ++lt) {
+        const int b = lt & 1;
+        if (lt >= 2) {
+          if (!mbar_wait(&tempty[b], (uint32_t)((lt >> 1) - 1) & 1u, a.err)) break;
+          tc_fence_after();
+        }
+        const uint32_t d1 = tmem + (uint32_t)(b * 2 * N), d2 = d1 + (uint32_t)N;
+        for (int kt = 0; kt < KT; ++kt, ++gs) {
+          const int s = gs % nst;
+          if (!mbar_wait(&conv[s], (uint32_t)(gs / nst) & 1u, a.err)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sb = smem_addr(base + s * STAGE);
+          const uint64_t ah = sdesc_k_sw128(sb + oAh), al = sdesc_k_sw128(sb + oAl);
+          const uint64_t mh = sdesc_k_sw128(sb + oB1h), eh = sdesc_k_sw128(sb + oB2h);
+          const uint64_t ml = sdesc_k_sw128(sb + oB1l);
 #pragma unroll
-      for (int k = 0; k < kUpK / 8; ++k) {
-        const uint32_t acc = (first && k == 0) ? 0u : 1u;
-        mma_tf32(tmem + cAcc1, ah + 2 * k, m1h + 2 * k, idesc, acc);
-        mma_tf32(tmem + cAcc2, ah + 2 * k, m2h + 2 * k, idesc, acc);
-        if (split) {
-          mma_tf32(tmem + cAcc1, ah + 2 * k, m1l + 2 * k, idesc, 1);
-          mma_tf32(tmem + cAcc1, al + 2 * k, m1h + 2 * k, idesc, 1);
-          mma_tf32(tmem + cAcc2, ah + 2 * k, m2l + 2 * k, idesc, 1);
-          mma_tf32(tmem + cAcc2, al + 2 * k, m2h + 2 * k, idesc, 1);
+          for (int k = 0; k < kUpK / 8; ++k) {
+            const uint32_t acc = (kt | k) != 0 ? 1u : 0u;
+            mma_tf32(d1, ah + 2 * k, mh + 2 * k, idesc, acc);
+            mma_tf32(d2, ah + 2 * k, eh + 2 * k, idesc, acc);
+            if (split) {
+              mma_tf32(d1, ah + 2 * k, ml + 2 * k, idesc, 1);
+              mma_tf32(d1, al + 2 * k, mh + 2 * k, idesc, 1);
+            }
+          }
+          mma_commit(&empty[s]);
         }
+        if (ok) mma_commit(&tfull[b]);
       }
-      mma_commit(&empty[s]);
-      if (split || kt == KT - 1) mma_commit(acc_full);
-      counters[1] = kt + 1;
+      mma_commit(done);
     }
-    mma_commit(done);
-  } else if (warp == 2 || warp == 3) {
-    // converters: X slice [32 columns][128 rows] -> K-major SW128 [128 rows][32 columns]
-    const int tid = threadIdx.x - 64;
-    for (int kt = 0; kt < KT; ++kt) {
-      const int s = kt % nst;
-      const uint32_t ph = (uint32_t)(kt / nst) & 1u;
-      if (!mbar_wait(&full[s], ph, a.err)) break;
-      unsigned char* sb = base + s * STAGE;
-      const float* xr = reinterpret_cast<const float*>(sb);
-      for (int it = tid; it < kUpM * (kUpK / 4); it += kUpConvThreads) {
-        const int m = it & (kUpM - 1), j = it >> 7;   // row, 16-byte chunk of 4 columns
-        const float x0 = xr[(4 * j + 0) * kUpM + m], x1 = xr[(4 * j + 1) * kUpM + m];
-        const float x2 = xr[(4 * j + 2) * kUpM + m], x3 = xr[(4 * j + 3) * kUpM + m];
-        float4 h;
-        h.x = __uint_as_float(tf32_rna(x0));
-        h.y = __uint_as_float(tf32_rna(x1));
-        h.z = __uint_as_float(tf32_rna(x2));
-        h.w = __uint_as_float(tf32_rna(x3));
-        const uint32_t off = (uint32_t)(m >> 3) * 1024u + (uint32_t)(m & 7) * 128u +
-                             (uint32_t)((j ^ (m & 7)) * 16);
-        *reinterpret_cast<float4*>(sb + oAh + off) = h;
-        if (split) {
-          float4 l;
-          l.x = __uint_as_float(tf32_rna(x0 - h.x));
-          l.y = __uint_as_float(tf32_rna(x1 - h.y));
-          l.z = __uint_as_float(tf32_rna(x2 - h.z));
-          l.w = __uint_as_float(tf32_rna(x3 - h.w));
-          *reinterpret_cast<float4*>(sb + oAl + off) = l;
+  } else if (warp == 2 || warp == 3 || warp >= 8) {
+    // ---- converters: landed X slice [32 columns][128 rows] -> K-major SW128 rows
+    const int ct = conv_tid(warp, lane);
+    int gs = 0;
+    for (int lt = 0; lt < ntl; ++lt) {
+      bool abort = false;
+      for (int kt = 0; kt < KT; ++kt, ++gs) {
+        const int s = gs % nst;
+        if (!mbar_wait(&full[s], (uint32_t)(gs / nst) & 1u, a.err)) flags[1] = 1;
+        named_bar(2, kUpConvThreads);
+        if (*(volatile int*)&flags[1] != 0) { abort = true; break; }
+        unsigned char* sb = base + s * STAGE;
+        const float* xr = reinterpret_cast<const float*>(sb + oRaw);
+        float4 v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int it = ct + kUpConvThreads * i;
+          const int m = it & (kUpM - 1), j = it >> 7;   // row, 16-byte chunk of 4 columns
+          v[i].x = xr[(4 * j + 0) * kUpM + m];
+          v[i].y = xr[(4 * j + 1) * kUpM + m];
+          v[i].z = xr[(4 * j + 2) * kUpM + m];
+          v[i].w = xr[(4 * j + 3) * kUpM + m];
         }
+        named_bar(2, kUpConvThreads);   // the landed slice is read before it is overwritten
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int it = ct + kUpConvThreads * i;
+          const int m = it & (kUpM - 1), j = it >> 7;
+          const uint32_t off = (uint32_t)(m >> 3) * 1024u + (uint32_t)(m & 7) * 128u +
+                               (uint32_t)((j ^ (m & 7)) * 16);
+          float4 h;
+          h.x = __uint_as_float(tf32_rna(v[i].x));
+          h.y = __uint_as_float(tf32_rna(v[i].y));
+          h.z = __uint_as_float(tf32_rna(v[i].z));
+          h.w = __uint_as_float(tf32_rna(v[i].w));
+          *reinterpret_cast<float4*>(sb + oAh + off) = h;
+          if (split) {
+            float4 l;
+            l.x = __uint_as_float(tf32_rna(v[i].x - h.x));
+            l.y = __uint_as_float(tf32_rna(v[i].y - h.y));
+            l.z = __uint_as_float(tf32_rna(v[i].z - h.z));
+            l.w = __uint_as_float(tf32_rna(v[i].w - h.w));
+            *reinterpret_cast<float4*>(sb + oAl + off) = l;
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&conv[s]))
+                     : "memory");
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&conv[s]))
-                   : "memory");
+      if (abort) break;
     }
-  } else if (warp >= 4) {
+  } else {
+    // ---- epilogue warps 4-7
     const int q = warp - 4;
+    const int et = threadIdx.x - 128;          // 0 .. 127 = TMEM lane = row in the tile
+    const bool leader = et == 0;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    const int64_t r = r0 + q * 32 + lane;
-    const bool row_ok = r < a.n;
-    bool ok = true;
-    for (int seg = 0; seg < nseg - 1; ++seg) {   // compensated mode: add the segment into the totals
-      if (!mbar_wait_warp(acc_full, (uint32_t)seg & 1u, a.err)) { ok = false; break; }
+    const int nch = N / kUpChunk;
+    float* R = (kst & 1) ? a.R1 : a.R0;
+    const CUtensorMap* mapRp = (kst & 1) ? &mapR0e : &mapR1e;
+    const float* cprev = a.coef + (size_t)((kst + 1) & 1) * (2 * a.p + 1);
+    const float inv_etap = kst > 0 ? cprev[0] : 0.f;
+    const uint32_t ep_bytes = (kst > 0 ? 3u : 2u) * EPC;
+    int gc = 0;
+    auto issue_chunk = [&](int g, int r0, int cc) {
+      unsigned char* sl = ring + (g & 1) * 3 * EPC;
+      mbar_arrive_expect_tx(&epfull[g & 1], ep_bytes);
+      tma_load_2d(sl, &mapXe, &epfull[g & 1], r0, cc);
+      tma_load_2d(sl + EPC, &mapGe, &epfull[g & 1], r0, cc);
+      if (kst > 0) tma_load_2d(sl + 2 * EPC, mapRp, &epfull[g & 1], r0, cc);
+      flags[3] = g + 1;
+    };
+    for (int lt = 0; lt < ntl; ++lt) {
+      const int tile = (int)blockIdx.x + lt * (int)gridDim.x;
+      const int rb = tile / a.nct, ctl = tile % a.nct;
+      const int r0 = rb * kUpM, c0 = ctl * N;
+      const int b = lt & 1;
+      if (leader)
+        for (int j = 0; j < nch && j < 2; ++j) issue_chunk(gc + j, r0, c0 + j * kUpChunk);
+      if (!mbar_wait_warp(&tfull[b], (uint32_t)(lt >> 1) & 1u, a.err) && lane == 0) flags[0] = 1;
+      named_bar(1, 128);
+      if (*(volatile int*)&flags[0] != 0) break;
       tc_fence_after();
-      for (int j0 = 0; j0 < N; j0 += 16) {
-        uint32_t v1[16], t1[16], v2[16], t2[16];
-        tmem_ld16_nw(tmem + lane_off + cAcc1 + j0, v1);
-        tmem_ld16_nw(tmem + lane_off + cAcc2 + j0, v2);
-        if (seg > 0) {
-          tmem_ld16_nw(tmem + lane_off + cTot1 + j0, t1);
-          tmem_ld16_nw(tmem + lane_off + cTot2 + j0, t2);
-        }
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (seg > 0) {
-#pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            v1[c] = __float_as_uint(__fadd_rn(__uint_as_float(t1[c]), __uint_as_float(v1[c])));
-            v2[c] = __float_as_uint(__fadd_rn(__uint_as_float(t2[c]), __uint_as_float(v2[c])));
-          }
-        }
-        tmem_st16(tmem + lane_off + cTot1 + j0, v1);
-        tmem_st16(tmem + lane_off + cTot2 + j0, v2);
-      }
-      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-      tc_fence_before();
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(acc_empty))
-                   : "memory");
-    }
-    // every accumulator warp reaches the named barrier below exactly once
-    int* bad = reinterpret_cast<int*>(counters + 2);
-    if (threadIdx.x == 128) *bad = 0;
-    asm volatile("bar.sync 1, 128;" ::: "memory");
-    ok = ok && mbar_wait_warp(acc_full, (uint32_t)(nseg - 1) & 1u, a.err);
-    if (!ok && lane == 0) *bad = 1;
-    {
-      tc_fence_after();
-      // epilogue; the stage buffers are idle now and hold the cross-warp sums
-      float* colred = reinterpret_cast<float*>(base);              // [4][3][N]
-      float* wsum = colred + 4 * 3 * N;                            // [4][6]
-      const int k = a.st->k;
-      float* R = (k & 1) ? a.R1 : a.R0;
-      const float* Rp = (k & 1) ? a.R0 : a.R1;
-      const float* cprev = a.coef + (size_t)((k + 1) & 1) * (2 * a.p + 1);
-      const float inv_etap = k > 0 ? cprev[0] : 0.f;
+      const int64_t r = (int64_t)r0 + et;
+      const bool row_ok = r < a.n;
+      const uint32_t t1 = tmem + lane_off + (uint32_t)(b * 2 * N), t2 = t1 + (uint32_t)N;
       float ss = 0.f, sy = 0.f, yy = 0.f, kk = 0.f, gg = 0.f, xg = 0.f;
-      for (int j0 = 0; ok && j0 < N; j0 += 16) {
-        uint32_t v1[16], t1[16], v2[16], t2[16];
-        tmem_ld16_nw(tmem + lane_off + cAcc1 + j0, v1);
-        tmem_ld16_nw(tmem + lane_off + cAcc2 + j0, v2);
-        if (nseg > 1) {
-          tmem_ld16_nw(tmem + lane_off + cTot1 + j0, t1);
-          tmem_ld16_nw(tmem + lane_off + cTot2 + j0, t2);
-        }
-        // all global loads of the chunk in flight together (one CTA per SM: the
-        // epilogue hides latency by independent loads, not by other warps)
-        float xv[16], gv[16], rpv[16], om[16];
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int col = c0 + j0 + c;
-          const bool v = row_ok && col < a.p;
-          xv[c] = v ? __ldg(a.X + r + (int64_t)col * a.ldx) : 0.f;
-          gv[c] = v ? __ldg(a.G + r + (int64_t)col * a.ldg) : 0.f;
-        }
-        if (k > 0) {
-#pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const int col = c0 + j0 + c;
-            const bool v = row_ok && col < a.p;
-            rpv[c] = v ? __ldg(Rp + r + (int64_t)col * a.ldr) : 0.f;
-            om[c] = col < a.p ? __ldg(cprev + 1 + a.p + col) : 0.f;
-          }
-        } else {
-#pragma unroll
-          for (int c = 0; c < 16; ++c) { rpv[c] = 0.f; om[c] = 0.f; }
-        }
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      bool abort = false;
+      for (int j = 0; j < nch; ++j, ++gc) {
+        const int slot = gc & 1;
+        if (!mbar_wait_warp(&epfull[slot], (uint32_t)(gc >> 1) & 1u, a.err) && lane == 0)
+          flags[0] = 1;
+        named_bar(1, 128);
+        if (*(volatile int*)&flags[0] != 0) { abort = true; break; }
+        const int j0 = j * kUpChunk;
+        uint32_t v1[16], v2[16];
+        tmem_ld16_nw(t1 + (uint32_t)j0, v1);
+        tmem_ld16_nw(t2 + (uint32_t)j0, v2);
+        const float* Xs = reinterpret_cast<const float*>(ring + slot * 3 * EPC);
+        const float* Gs = Xs + kUpM * kUpChunk;
+        const float* Rs = Gs + kUpM * kUpChunk;
         float dv[48];
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-          float d1 = __uint_as_float(v1[c]), d2 = __uint_as_float(v2[c]);
-          if (nseg > 1) {
-            d1 = __fadd_rn(__uint_as_float(t1[c]), d1);
-            d2 = __fadd_rn(__uint_as_float(t2[c]), d2);
-          }
           const int col = c0 + j0 + c;
           float xx = 0.f, xrv = 0.f, rr = 0.f;
           if (row_ok && col < a.p) {
-            const float x = xv[c], g = gv[c];
-            const float rv = g - d1;
-            const float kv = g - d2;
+            const float x = Xs[c * kUpM + et], g = Gs[c * kUpM + et];
+            const float rv = g - __uint_as_float(v1[c]);
+            const float kv = rv - __uint_as_float(v2[c]);
             R[r + (int64_t)col * a.ldr] = rv;
             xx = x * x;
             xrv = x * rv;
@@ -351,9 +361,9 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
             kk = fmaf(kv, kv, kk);
             gg = fmaf(g, g, gg);
             xg = fmaf(x, g, xg);
-            if (k > 0) {
-              const float rp = rpv[c];
-              const float sv = om[c] * x - rp * inv_etap;
+            if (kst > 0) {
+              const float rp = Rs[c * kUpM + et];
+              const float sv = __ldg(cprev + 1 + a.p + col) * x - rp * inv_etap;
               const float yv = rv - rp;
               ss = fmaf(sv, sv, ss);
               sy = fmaf(sv, yv, sy);
@@ -366,55 +376,66 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         }
         warp_sum48(dv, lane);
         if ((lane & 1) == 0) {
-          const int b = 24 * ((lane >> 4) & 1) + 12 * ((lane >> 3) & 1) + 6 * ((lane >> 2) & 1) +
-                        3 * ((lane >> 1) & 1);
+          const int bb = 24 * ((lane >> 4) & 1) + 12 * ((lane >> 3) & 1) + 6 * ((lane >> 2) & 1) +
+                         3 * ((lane >> 1) & 1);
 #pragma unroll
           for (int e = 0; e < 3; ++e) {
-            const int idx = b + e, d = idx >> 4, c = idx & 15;
+            const int idx = bb + e, d = idx >> 4, c = idx & 15;
             colred[(q * 3 + d) * N + j0 + c] = dv[e];
           }
         }
+        named_bar(1, 128);   // every warp is done with the slot
+        if (leader && j + 2 < nch) issue_chunk(gc + 2, r0, c0 + (j + 2) * kUpChunk);
       }
+      if (abort) break;
+      // the accumulators of buffer b are read: the MMA may reuse them
+      tc_fence_before();
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&tempty[b]))
+                   : "memory");
       float tot[kTotDots] = {ss, sy, yy, kk, gg, xg};
 #pragma unroll
       for (int d = 0; d < kTotDots; ++d) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) tot[d] += __shfl_xor_sync(0xffffffffu, tot[d], o);
       }
-      if (ok && lane == 0) {
+      if (lane == 0) {
 #pragma unroll
         for (int d = 0; d < kTotDots; ++d) wsum[q * kTotDots + d] = tot[d];
       }
-      asm volatile("bar.sync 1, 128;" ::: "memory");   // the four accumulator warps
-      const int t = threadIdx.x - 128;
-      const bool all_ok = *(volatile int*)bad == 0;
-      for (int j = t; all_ok && j < N; j += 128) {
-        const int col = c0 + j;
+      named_bar(1, 128);
+      for (int jj = et; jj < N; jj += 128) {
+        const int col = c0 + jj;
         if (col < a.p) {
           float* cp = a.colpart + (size_t)rb * kColDots * a.p;
 #pragma unroll
           for (int d = 0; d < 3; ++d)
-            cp[(size_t)d * a.p + col] = ((colred[(0 * 3 + d) * N + j] + colred[(1 * 3 + d) * N + j]) +
-                                         colred[(2 * 3 + d) * N + j]) + colred[(3 * 3 + d) * N + j];
+            cp[(size_t)d * a.p + col] = ((colred[(0 * 3 + d) * N + jj] + colred[(1 * 3 + d) * N + jj]) +
+                                         colred[(2 * 3 + d) * N + jj]) + colred[(3 * 3 + d) * N + jj];
         }
       }
-      if (all_ok && t < kTotDots)
-        a.totpart[((size_t)rb * a.nct + ct) * kTotDots + t] =
-            ((wsum[t] + wsum[kTotDots + t]) + wsum[2 * kTotDots + t]) + wsum[3 * kTotDots + t];
+      if (et < kTotDots)
+        a.totpart[((size_t)rb * a.nct + ctl) * kTotDots + et] =
+            ((wsum[et] + wsum[kTotDots + et]) + wsum[2 * kTotDots + et]) + wsum[3 * kTotDots + et];
+      named_bar(1, 128);   // colred / wsum are free for the next tile
     }
   }
   __syncwarp();
   tc_fence_before();
   __syncthreads();
   if (threadIdx.x == 0) {
+    // every issued MMA has completed and every issued copy has landed (bounded waits)
     for (long long i = 0; i < kTcSpin && !mbar_try_wait(done, 0); ++i) {
     }
-    for (int kt = counters[1]; kt < counters[0]; ++kt) {
-      const int s = kt % nst;
-      const uint32_t ph = (uint32_t)(kt / nst) & 1u;
-      for (long long i = 0; i < kTcSpin && !mbar_try_wait(&full[s], ph); ++i) {
+    const int gs_issued = flags[2];
+    for (int g = gs_issued > nst ? gs_issued - nst : 0; g < gs_issued; ++g)
+      for (long long i = 0; i < kTcSpin && !mbar_try_wait(&full[g % nst], (uint32_t)(g / nst) & 1u);
+           ++i) {
       }
-    }
+    const int gc_issued = flags[3];
+    for (int g = gc_issued > 2 ? gc_issued - 2 : 0; g < gc_issued; ++g)
+      for (long long i = 0; i < kTcSpin && !mbar_try_wait(&epfull[g & 1], (uint32_t)(g >> 1) & 1u);
+           ++i) {
+      }
   }
   __syncthreads();
   if (warp == 2) {
@@ -424,48 +445,44 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   }
 }
 
-// Rounded TF32 parts of M and Psi(C) (p x p, column-major, leading dimension
-// p in the solver's buffers) into hi / lo arrays with leading dimension ldm:
-// hi = RN_tf32(v), lo = RN_tf32(v - hi).
+// TF32 parts of M and of E = Psi(C) - M (p x p, column-major, leading
+// dimension p in the solver's buffers) into three planes of leading dimension
+// ldm: M hi = RN_tf32(M), M lo = RN_tf32(M - M hi), E hi = RN_tf32(E).
 __global__ void tc_split_m_kernel(int p, const float* __restrict__ Mt, const float* __restrict__ L0t,
                                   int ldm, float* __restrict__ out, const DevState* __restrict__ st) {
   if (st != nullptr && st->stop != kRunning) return;
   const size_t plane = (size_t)ldm * p;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p * p; i += gridDim.x * blockDim.x) {
     const int r = i % p, c = i / p;
-    const float m = Mt[i], l = L0t[i];
-    const float mh = __uint_as_float(tf32_rna(m)), lh = __uint_as_float(tf32_rna(l));
+    const float m = Mt[i];
+    const float mh = __uint_as_float(tf32_rna(m));
     const size_t o = (size_t)c * ldm + r;
     out[o] = mh;
     out[plane + o] = __uint_as_float(tf32_rna(m - mh));
-    out[2 * plane + o] = lh;
-    out[3 * plane + o] = __uint_as_float(tf32_rna(l - lh));
+    out[2 * plane + o] = __uint_as_float(tf32_rna(L0t[i] - m));
   }
 }
 
 // ---------------------------------------------------------------- host side
-
-static uint32_t up_stage_bytes_host(int N, bool split) {
-  const uint32_t XR = kUpM * kUpK * 4, A = kUpM * kUpK * 4, BT = (uint32_t)N * kUpK * 4;
-  return split ? XR + 2 * A + 4 * BT : XR + A + 2 * BT;
-}
 
 void tc_update_plan(int64_t n, int p, TcUpdatePlan* pl) {
   pl->N = p >= 128 ? 128 : ((p + 15) / 16) * 16;
   pl->nct = (p + pl->N - 1) / pl->N;
   pl->nrt = (int)((n + kUpM - 1) / kUpM);
   pl->ldm = ((p + 31) / 32) * 32;
-  // stages: as many as fit (at most 4), with at least two in compensated mode
-  const size_t limit = 232448 - 1024 - kUpAux;
-  const uint32_t s3 = up_stage_bytes_host(pl->N, true);
-  size_t pipe = 2 * (size_t)s3;
-  const uint32_t s1 = up_stage_bytes_host(pl->N, false);
-  size_t plain = (size_t)s1 * (limit / s1 < (size_t)kUpMaxStages ? limit / s1 : kUpMaxStages);
-  if (plain > pipe) pipe = plain;
-  size_t split4 = (size_t)s3 * (limit / s3 < (size_t)kUpMaxStages ? limit / s3 : kUpMaxStages);
-  if (split4 > pipe) pipe = split4;
+  // stage buffers: what is left after the epilogue ring and the reduction scratch,
+  // at most four stages of either mode
+  const size_t fixed = 1024 + up_ring_bytes() + up_red_bytes(pl->N) + kUpAux;
+  const size_t avail = 232448 - fixed;
+  size_t pipe = 0;
+  for (int split = 0; split < 2; ++split) {
+    const size_t st = up_stage_bytes(pl->N, split != 0);
+    size_t k = avail / st;
+    if (k > (size_t)kUpMaxStages) k = kUpMaxStages;
+    if (k * st > pipe) pipe = k * st;
+  }
   pl->pipe_bytes = (uint32_t)pipe;
-  pl->smem = 1024 + pipe + kUpAux;
+  pl->smem = fixed + pipe;
 }
 
 bool tc_update_supported(const void* X, int64_t ldx) {
@@ -486,22 +503,27 @@ cudaError_t launch_tc_update(int64_t n, int p, const float* X, int64_t ldx, cons
     if (e != cudaSuccess) return e;
   }
   const size_t plane = (size_t)pl.ldm * p;
-  CUtensorMap mX, mMh, mMl, mLh, mLl;
+  CUtensorMap mX, mMh, mMl, mEh, mXe, mGe, mR0e, mR1e;
   if (!encode_map_f32(&mX, X, (uint64_t)n, (uint64_t)p, (uint64_t)ldx, kUpM, kUpK, false) ||
       !encode_map_f32(&mMh, msplit, p, p, pl.ldm, kUpK, pl.N, true) ||
       !encode_map_f32(&mMl, msplit + plane, p, p, pl.ldm, kUpK, pl.N, true) ||
-      !encode_map_f32(&mLh, msplit + 2 * plane, p, p, pl.ldm, kUpK, pl.N, true) ||
-      !encode_map_f32(&mLl, msplit + 3 * plane, p, p, pl.ldm, kUpK, pl.N, true))
+      !encode_map_f32(&mEh, msplit + 2 * plane, p, p, pl.ldm, kUpK, pl.N, true) ||
+      !encode_map_f32(&mXe, X, (uint64_t)n, (uint64_t)p, (uint64_t)ldx, kUpM, kUpChunk, false) ||
+      !encode_map_f32(&mGe, G, (uint64_t)n, (uint64_t)p, (uint64_t)ldg, kUpM, kUpChunk, false) ||
+      !encode_map_f32(&mR0e, R0, (uint64_t)n, (uint64_t)p, (uint64_t)ldr, kUpM, kUpChunk, false) ||
+      !encode_map_f32(&mR1e, R1, (uint64_t)n, (uint64_t)p, (uint64_t)ldr, kUpM, kUpChunk, false))
     return cudaErrorInvalidValue;
   TcUpdateArgs a;
-  a.n = n; a.p = p; a.N = pl.N; a.nct = pl.nct;
-  a.X = X; a.ldx = ldx; a.G = G; a.ldg = ldg; a.R0 = R0; a.R1 = R1; a.ldr = ldr;
+  a.n = n; a.p = p; a.N = pl.N; a.nct = pl.nct; a.ntiles = pl.nrt * pl.nct;
+  a.R0 = R0; a.R1 = R1; a.ldr = ldr;
   a.coef = coef; a.st = st; a.colpart = colpart; a.totpart = totpart; a.err = err;
   a.pipe_bytes = pl.pipe_bytes; a.refine_switch = refine_switch; a.force3 = force3;
   cudaError_t e = cudaFuncSetAttribute(tc_update_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
   if (e != cudaSuccess) return e;
-  tc_update_kernel<<<pl.nrt * pl.nct, kUpThreads, pl.smem, s>>>(mX, mMh, mMl, mLh, mLl, a);
+  int grid = device_sm_count();
+  if (grid > a.ntiles) grid = a.ntiles;
+  tc_update_kernel<<<grid, kUpThreads, pl.smem, s>>>(mX, mMh, mMl, mEh, mXe, mGe, mR0e, mR1e, a);
   return cudaGetLastError();
 }
 

@@ -171,6 +171,7 @@ cudaError_t launch_tc_gram(int64_t n, int p, const float* X, int64_t ldx, const 
                            const DevState* st, double refine_switch, int force3, cudaStream_t s);
 cudaError_t preload_tc_kernels();
 bool tma_encoder_available();
+int device_sm_count();   // SMs of the current device
 
 // Tensor-core update GEMM (FP32 storage): R = G - X M and the KKT residual,
 // with the column and tile dots of launch_update (nrt x 3 x p and

@@ -46,7 +46,8 @@ def test_grams_match_definition(precision, n, p):
         X = X.astype(np.float32).astype(np.float64)
         G = G.astype(np.float32).astype(np.float64)
     w = workload_hartree1d(n=n, p=p) if 2 * p <= n else None
-    s = gpu_solver(w, precision)
+    # the CUDA-core Grams (FP32 products); the tensor-core Grams have their own tests
+    s = gpu_solver(w, precision, tensor_cores="off")
     Xd, Gd = to_dev(X, s), to_dev(G, s)
     B, Cm = s.grams(Xd, Gd)
     Bref, Cref = ok.grams(X, G)

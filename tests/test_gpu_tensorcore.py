@@ -155,9 +155,9 @@ def _dense_case(n, p, seed):
 def test_tensor_core_update_three_iterations(n, p, variant, tc, tol):
     """Three FP32 iterations with the tcgen05 update GEMM R = G - X M (eq. S1) and its epilogue
     dots (column norms for PCAL's closed form, the Barzilai-Borwein sums of Section 5.1, the KKT
-    residual of Section 3.3) against the FP64 oracle: the steps X^3 - X^0, the step sizes eta^0..2
-    and the relative KKT values agree to the accuracy of the operand rounding (TF32: 2^-11;
-    compensated 3xTF32: FP32 level).  Row blocks of 128 with a ragged tail, column tiles of 128
+    residual of Section 3.3) against the FP64 oracle: the steps X^3 - X^0 and the step sizes
+    eta^0..2 agree to the accuracy of the operand rounding (TF32: 2^-11; compensated 3xTF32: FP32
+    level), the relative KKT values to TF32 level (its correction term X E is plain TF32).  Row blocks of 128 with a ragged tail, column tiles of 128
     with a ragged tail (p = 130), a single column (p = 1)."""
     from oracle import objectives as oo
     from oracle import plam as op
@@ -177,7 +177,7 @@ def test_tensor_core_update_three_iterations(n, p, variant, tc, tol):
     eta_ref = np.array([h.eta for h in ref.history[:3]])
     kkt_ref = np.array([h.kkt for h in ref.history])
     np.testing.assert_allclose(hist[:3, 4], eta_ref, rtol=5 * tol)
-    np.testing.assert_allclose(hist[:, 2], kkt_ref, rtol=5 * tol)
+    np.testing.assert_allclose(hist[:, 2], kkt_ref, rtol=max(5 * tol, 1e-3))
     s.close()
 
 
@@ -195,3 +195,36 @@ def test_tensor_core_update_replaces_the_cuda_core_update():
         counts[tc] = s.kernel_launches()
         s.close()
     assert counts["tf32"] == counts["off"] + 1
+
+
+@pytest.mark.parametrize("m,p", [(30, 256), (34, 130)])
+@pytest.mark.parametrize("tc,tol", [("3xtf32", 2e-5), ("tf32", 4e-3)])
+def test_tensor_core_update_persistent_tiles(m, p, tc, tol):
+    """The persistent update kernel walks several 128 x 128 tiles per CTA (27000 or 39304 rows:
+    hundreds of tiles on 152 SMs), alternating its two tensor-memory accumulator buffers and the
+    two-slot epilogue ring; three PCAL iterations on the 3D stencil against the FP64 oracle."""
+    from oracle import objectives as oo
+    from oracle import plam as op
+    from tests.gpu_helpers import gpu_solver, rel_err, to_host
+    from workloads import workload_stencil3d
+    w = workload_stencil3d(m=m, p=p)
+    obj = oo.Stencil3DObjective(w.m, w.V.astype(np.float32).astype(np.float64))
+    X0 = w.X0 + 0.02 * np.random.default_rng(5).standard_normal(w.X0.shape)
+    ref = op.solve(obj, X0, variant="pcal", beta=1.0, tol=0.0, maxit=3)
+    s = gpu_solver(w, "fp32", variant="pcal", beta=1.0, tol=0.0, maxit=3, final_orth=0,
+                   tensor_cores=tc, refine_switch=0.0, engine="graph")
+    n = w.n
+    Xd = to_dev(X0, s, ld=(n + 31) // 32 * 32)
+    st, info = s.solve(Xd)
+    hist = s.history()
+    X3 = to_host(Xd, n)
+    X0f = X0.astype(np.float32).astype(np.float64)
+    assert rel_err(X3 - X0f, ref.X - X0) <= 5 * tol
+    # eta^2 = <Y,Y>/|<S,Y>| (BB2) divides differences of residuals, Y = R^2 - R^1: the TF32 error
+    # of R is amplified by |R| / |Y| (up to ~10% here), so plain TF32 is held to eta^0, eta^1
+    ne = 3 if tc == "3xtf32" else 2
+    np.testing.assert_allclose(hist[:ne, 4], [h.eta for h in ref.history[:ne]], rtol=5 * tol)
+    # K = R - X E with E = Psi(C) - M in plain TF32 (2^-12 relative to X E, which is not small
+    # at an infeasible start): the KKT value carries that error in both modes
+    np.testing.assert_allclose(hist[:, 2], [h.kkt for h in ref.history], rtol=max(5 * tol, 1e-3))
+    s.close()
