@@ -76,8 +76,23 @@ enum { PLAM_PREC_FP64 = 0, PLAM_PREC_FP32 = 1 };
  *              rho = diag(X X^T), L = tridiag(-1,2,-1) Dirichlet
  *   STENCIL3D  f = 1/2 tr(X^T (L3 + Diag(V)) X), L3 the 7-point Dirichlet
  *              Laplacian on nx*ny*nz points, index i = x + nx*(y + ny*z);
- *              nx*ny*nz must equal n and stay below 2^31. */
-enum { PLAM_OBJ_DENSE = 0, PLAM_OBJ_HARTREE1D = 1, PLAM_OBJ_STENCIL3D = 2 };
+ *              nx*ny*nz must equal n and stay below 2^31.
+ * and a user objective (the problem statement of Section 2 admits any f with
+ * a gradient):
+ *   CALLBACK   f and grad f from plam_objective_t.grad, called on the host
+ *              once per gradient evaluation (see plam_grad_fn).  plam_solve
+ *              then launches each iteration directly (no CUDA graph; the
+ *              resident engine does not apply). */
+enum { PLAM_OBJ_DENSE = 0, PLAM_OBJ_HARTREE1D = 1, PLAM_OBJ_STENCIL3D = 2, PLAM_OBJ_CALLBACK = 3 };
+
+/* User gradient of PLAM_OBJ_CALLBACK: reads X (device, storage type, n x p,
+ * leading dimension ldx), writes G = grad f(X) (device, storage type, leading
+ * dimension ldg) and the value f(X) into *f (a device double), all as work
+ * ordered on `stream` (the handle's cudaStream_t); it may return before that
+ * work completes.  Returns 0 on success; any other value stops the calling
+ * entry point with PLAM_ERR_CUDA and the message "objective callback failed". */
+typedef int (*plam_grad_fn)(void* ctx, const void* X, int64_t ldx, void* G, int64_t ldg, double* f,
+                            void* stream);
 /* How plam_solve runs the loop.  GRAPH: the kernel sequence of one iteration,
  * replayed from a captured CUDA graph (any size).  RESIDENT: one cooperative
  * persistent launch for the whole solve, each SM keeping its rows of X, G/R
@@ -115,6 +130,8 @@ typedef struct {
   double quad_scale;    /* HARTREE1D: q, the coefficient of tr(X^T L X) (1/4 Kohn-Sham, 1/2 Problem 1) */
   int nx, ny, nz;       /* STENCIL3D: grid, nx*ny*nz == n */
   const void* V;        /* STENCIL3D: device n-vector potential, storage type (may be NULL: V = 0) */
+  plam_grad_fn grad;    /* CALLBACK: the user gradient (required) */
+  void* grad_ctx;       /* CALLBACK: passed to grad unchanged */
 } plam_objective_t;
 
 typedef struct {
@@ -195,6 +212,17 @@ plam_status_t plam_orthonormalize(plam_handle_t h, const void* X, int64_t ldx, d
  * "cost" rows "evaluate function").  Used by the autograd wrapper and tests. */
 plam_status_t plam_energy_grad(plam_handle_t h, const void* X, int64_t ldx, void* G, int64_t ldg,
                                double* f);
+
+/* The energy as a forward / backward pair (Section 5.2 objectives), for an
+ * automatic-differentiation wrapper.  No call synchronises the stream.
+ *   plam_energy          *f_dev = f(X), f_dev a device double.
+ *   plam_energy_backward G = s grad f(X), s = *scale_dev (a device double) or
+ *                        1 when scale_dev is NULL; G: device, storage type,
+ *                        leading dimension ldg (rows >= n are not written).
+ * Both use the handle's workspace: calls on one handle must not overlap. */
+plam_status_t plam_energy(plam_handle_t h, const void* X, int64_t ldx, double* f_dev);
+plam_status_t plam_energy_backward(plam_handle_t h, const void* X, int64_t ldx,
+                                   const double* scale_dev, void* G, int64_t ldg);
 
 /* The split-K tall-skinny Grams of one iteration (Table "cost": X^T X and
  * grad f^T X): B = X^T X and C = X^T G as FP64 p x p column-major device

@@ -11,12 +11,12 @@ import numpy as np
 
 from . import _lib
 from ._lib import (PLAM_ETA_ABB, PLAM_ETA_BB1, PLAM_ETA_BB2, PLAM_ETA_CONST, PLAM_ETA_DIFF,  # noqa: F401
-                   PLAM_LAMBDA1, PLAM_LAMBDA2, PLAM_OBJ_DENSE, PLAM_OBJ_HARTREE1D,
-                   PLAM_OBJ_STENCIL3D, PLAM_PREC_FP32, PLAM_PREC_FP64, PLAM_VARIANT_PCAL,
-                   PLAM_VARIANT_PLAM, PlamError, check, pcal_step, plam_create,
-                   plam_default_params, plam_destroy, plam_energy_grad, plam_grams, plam_history,
-                   plam_kernel_launches, plam_orthonormalize, plam_reset, plam_solve, plam_step,
-                   plam_time_kernels)
+                   PLAM_LAMBDA1, PLAM_LAMBDA2, PLAM_OBJ_CALLBACK, PLAM_OBJ_DENSE,
+                   PLAM_OBJ_HARTREE1D, PLAM_OBJ_STENCIL3D, PLAM_PREC_FP32, PLAM_PREC_FP64,
+                   PLAM_VARIANT_PCAL, PLAM_VARIANT_PLAM, PlamError, check, pcal_step, plam_create,
+                   plam_default_params, plam_destroy, plam_energy, plam_energy_backward,
+                   plam_energy_grad, plam_grams, plam_history, plam_kernel_launches,
+                   plam_orthonormalize, plam_reset, plam_solve, plam_step, plam_time_kernels)
 
 _RULES = {"abb": PLAM_ETA_ABB, "bb1": PLAM_ETA_BB1, "bb2": PLAM_ETA_BB2, "const": PLAM_ETA_CONST,
           "diff": PLAM_ETA_DIFF}
@@ -45,6 +45,56 @@ def colmajor_to_device(M: np.ndarray, dtype, device="cuda", ld: int | None = Non
     return t
 
 
+class _DeviceBuffer:
+    """A raw device buffer exposed through __cuda_array_interface__ (zero copy)."""
+
+    def __init__(self, ptr: int, shape, strides, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "strides": tuple(strides),
+                                         "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3}
+
+
+def _colmajor_view(ptr: int, n: int, p: int, ld: int, dtype):
+    """The n x p column-major matrix at device address ptr as an (n, p) tensor view."""
+    torch = _torch()
+    esz = 8 if dtype == torch.float64 else 4
+    buf = _DeviceBuffer(ptr, (n, p), (esz, ld * esz), "<f8" if esz == 8 else "<f4")
+    return torch.as_tensor(buf, device="cuda")
+
+
+def _energy_function():
+    """torch.autograd.Function over a Solver's built-in objective: the forward kernels give
+    f(X) on the device, the backward kernels grad_out * grad f(X) (plam_energy and
+    plam_energy_backward).  X is a (p, ld) tensor holding the column-major n x p matrix."""
+    torch = _torch()
+
+    class EnergyFn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, X, solver):
+            if X.dim() != 2 or X.stride(1) != 1 or X.shape[0] != solver.p or X.shape[1] < solver.n:
+                raise ValueError("X must be a (p, ld >= n) tensor with unit stride along ld")
+            f = torch.empty((1,), dtype=torch.float64, device=X.device)
+            check(plam_energy(solver.h, X.data_ptr(), X.stride(0), f.data_ptr()), "plam_energy")
+            ctx.save_for_backward(X)
+            ctx.solver = solver
+            return f[0]
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (X,) = ctx.saved_tensors
+            solver = ctx.solver
+            G = torch.zeros_like(X)
+            s = grad_out.detach().to(torch.float64).reshape(1).contiguous()
+            check(plam_energy_backward(solver.h, X.data_ptr(), X.stride(0), s.data_ptr(),
+                                       G.data_ptr(), G.stride(0)), "plam_energy_backward")
+            return G, None
+
+    return EnergyFn
+
+
+_ENERGY_FN = None
+
+
 def device_to_colmajor(t, n: int) -> np.ndarray:
     """Inverse of colmajor_to_device: an n x p float64 host array (Fortran order)."""
     return np.asfortranarray(t[:, :n].double().cpu().numpy().T)
@@ -61,7 +111,7 @@ class Solver:
                  variant="pcal", lambda_rule="lambda2", beta=1.0, eta_rule="abb", eta0=0.0,
                  eta_gamma=0.0, tol=1e-8, maxit=3000, precision="fp64", final_orth=1,
                  graph_iters=16, engine="auto", tensor_cores="auto", refine_switch=1e-3,
-                 stream=None):
+                 energy=None, stream=None):
         torch = _torch()
         self.n, self.p = int(n), int(p)
         self.precision = precision
@@ -97,11 +147,48 @@ class Solver:
                 Vt = V if isinstance(V, torch.Tensor) else colmajor_to_device(V, self.dtype)
                 self._keep.append(Vt)
                 obj.V = Vt.data_ptr()
+        elif kind == "callback":
+            if energy is None:
+                raise ValueError("kind='callback' needs energy=callable(X) -> scalar tensor")
+            self._cb_error = None
+            self._cb = _lib.plam_grad_fn(self._make_callback(energy))
+            obj.kind, obj.grad = PLAM_OBJ_CALLBACK, self._cb
         else:
             raise ValueError(kind)
         self.objective = obj
         self.stream = stream if stream is not None else torch.cuda.current_stream().cuda_stream
         self.h = plam_create(self.n, self.p, obj, prm, self.stream)
+
+    def _make_callback(self, energy):
+        """The C gradient callback of a user energy: f = energy(X) on an (n, p) view of X,
+        grad f by torch.autograd, both written as stream-ordered device work."""
+        torch = _torch()
+        n, p, dtype = self.n, self.p, self.dtype
+
+        def cb(ctx, Xp, ldx, Gp, ldg, fp, stream):
+            try:
+                s = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream()
+                with torch.cuda.stream(s):
+                    X = _colmajor_view(Xp, n, p, ldx, dtype).detach().requires_grad_(True)
+                    with torch.enable_grad():
+                        f = energy(X)
+                        (g,) = torch.autograd.grad(f, X)
+                    _colmajor_view(Gp, n, p, ldg, dtype).copy_(g)
+                    fo = torch.as_tensor(_DeviceBuffer(fp, (1,), (8,), "<f8"), device="cuda")
+                    fo.copy_(f.detach().to(torch.float64).reshape(1))
+                return 0
+            except Exception as e:       # reported by the C entry point as PLAM_ERR_CUDA
+                self._cb_error = e
+                return 1
+
+        return cb
+
+    def energy(self, X):
+        """f(X) as a differentiable 0-dim tensor (built-in objectives; backward = grad f)."""
+        global _ENERGY_FN
+        if _ENERGY_FN is None:
+            _ENERGY_FN = _energy_function()
+        return _ENERGY_FN.apply(X, self)
 
     def close(self):
         if getattr(self, "h", None) is not None:

@@ -30,7 +30,7 @@ PLAM_VARIANT_PLAM, PLAM_VARIANT_PCAL = 0, 1
 PLAM_LAMBDA1, PLAM_LAMBDA2 = 0, 1
 PLAM_ETA_ABB, PLAM_ETA_BB1, PLAM_ETA_BB2, PLAM_ETA_CONST, PLAM_ETA_DIFF = 0, 1, 2, 3, 4
 PLAM_PREC_FP64, PLAM_PREC_FP32 = 0, 1
-PLAM_OBJ_DENSE, PLAM_OBJ_HARTREE1D, PLAM_OBJ_STENCIL3D = 0, 1, 2
+PLAM_OBJ_DENSE, PLAM_OBJ_HARTREE1D, PLAM_OBJ_STENCIL3D, PLAM_OBJ_CALLBACK = 0, 1, 2, 3
 PLAM_ENGINE_AUTO, PLAM_ENGINE_GRAPH, PLAM_ENGINE_RESIDENT = 0, 1, 2
 
 
@@ -42,10 +42,15 @@ class plam_params_t(C.Structure):
                 ("tensor_cores", C.c_int), ("refine_switch", C.c_double)]
 
 
+# int grad(void* ctx, const void* X, int64_t ldx, void* G, int64_t ldg, double* f, void* stream)
+plam_grad_fn = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                           C.c_void_p, C.c_void_p)
+
+
 class plam_objective_t(C.Structure):
     _fields_ = [("kind", C.c_int), ("A", C.c_void_p), ("lda", C.c_int64), ("alpha", C.c_double),
                 ("quad_scale", C.c_double), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
-                ("V", C.c_void_p)]
+                ("V", C.c_void_p), ("grad", plam_grad_fn), ("grad_ctx", C.c_void_p)]
 
 
 class plam_info_t(C.Structure):
@@ -72,6 +77,9 @@ SIGNATURES = {
                                       C.c_int, C.POINTER(C.c_double)]),
     "plam_energy_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                    C.POINTER(C.c_double)]),
+    "plam_energy": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "plam_energy_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                       C.c_int64]),
     "plam_grams": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                              C.c_void_p, C.c_void_p]),
     "plam_grams_noalloc": (C.c_int, [C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_int64,
@@ -166,6 +174,16 @@ def plam_orthonormalize(h, X: int, ldx: int, Xout: int, ldo: int, passes: int = 
     st = load().plam_orthonormalize(h, C.c_void_p(X), ldx, C.c_void_p(Xout), ldo, passes,
                                     C.byref(feas) if want_feas else None)
     return st, feas.value
+
+
+def plam_energy(h, X: int, ldx: int, f_dev: int):
+    return load().plam_energy(h, C.c_void_p(X), ldx, C.c_void_p(f_dev))
+
+
+def plam_energy_backward(h, X: int, ldx: int, scale_dev, G: int, ldg: int):
+    return load().plam_energy_backward(h, C.c_void_p(X), ldx,
+                                       C.c_void_p(scale_dev) if scale_dev else None,
+                                       C.c_void_p(G), ldg)
 
 
 def plam_energy_grad(h, X: int, ldx: int, G: int, ldg: int, want_f=True):

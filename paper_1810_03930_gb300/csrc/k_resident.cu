@@ -549,7 +549,7 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_solve_kernel(Resident
           eta = eta0;
         }
         const double kkt = (K0 > 0.0) ? sqrt(kkd) / K0 : 0.0;
-        const double f = 0.5 * xgd - 0.25 * prm.hartree_alpha * tot[6];
+        const double f = prm.f_xg * xgd + prm.f_part * tot[6];
         const double feas = sqrt(feas2);
         last_kkt = kkt; last_feas = feas; last_f = f; last_ss = ssd; last_sy = syd; last_yy = yyd;
         if (b == 0 && nrec < prm.hist_cap) {

@@ -252,7 +252,7 @@ step_size_kernel(int nrt, int nct, const T* __restrict__ colpart, const T* __res
     const double K0 = st->K0;
     const double kkt = (K0 > 0.0) ? sqrt(kk) / K0 : 0.0;
     const double feas = sqrt(feas2);
-    const double f = 0.5 * xg - 0.25 * prm.hartree_alpha * hartree;
+    const double f = prm.f_xg * xg + prm.f_part * hartree;
     st->kkt = kkt;
     st->feas = feas;
     st->f = f;

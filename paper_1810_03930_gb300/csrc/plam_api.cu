@@ -35,6 +35,11 @@ plam_status_t cuda_fail(cudaError_t e, const char* what) {
   return PLAM_ERR_CUDA;
 }
 
+plam_status_t objective_fail() {
+  snprintf(g_err, sizeof(g_err), "objective callback failed: the user gradient returned non-zero");
+  return PLAM_ERR_CUDA;
+}
+
 }  // namespace
 
 void plam::set_last_error(const char* what, const char* detail) {
@@ -171,6 +176,17 @@ plam_status_t validate_params(const plam_params_t* prm) {
 
 bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 
+// f = f_xg <X, grad f> + f_part (sum of the objective's f partials): 1/2 <X, A X>
+// for the quadratic objectives; the Hartree term enters through its partials
+// rho^T L^{-1} rho; a user objective supplies f itself.
+void f_coefficients(const plam_handle_s* h, double* f_xg, double* f_part) {
+  switch (h->obj.kind) {
+    case PLAM_OBJ_HARTREE1D: *f_xg = 0.5; *f_part = -0.25 * h->obj.alpha; break;
+    case PLAM_OBJ_CALLBACK: *f_xg = 0.0; *f_part = 1.0; break;
+    default: *f_xg = 0.5; *f_part = 0.0; break;
+  }
+}
+
 template <typename T>
 IterParams iter_params(const plam_handle_s* h, int variant, int lambda2) {
   IterParams ip{};
@@ -186,6 +202,7 @@ IterParams iter_params(const plam_handle_s* h, int variant, int lambda2) {
   ip.gamma = h->prm.eta_gamma;
   ip.tol = h->prm.tol;
   ip.hartree_alpha = (h->obj.kind == PLAM_OBJ_HARTREE1D) ? h->obj.alpha : 0.0;
+  f_coefficients(h, &ip.f_xg, &ip.f_part);
   return ip;
 }
 
@@ -206,6 +223,13 @@ int launch_objective(plam_handle_s* h, const T* X, int64_t ldx, T* G, int64_t ld
       *err = launch_stencil_grad<T>(h->obj.nx, h->obj.ny, h->obj.nz, p, (const T*)h->obj.V, X, ldx,
                                     G, ldg, st, s);
       return 1;
+    case PLAM_OBJ_CALLBACK:
+      if (h->obj.grad(h->obj.grad_ctx, X, ldx, G, ldg, h->fpart, (void*)s) != 0) {
+        *err = cudaSuccess;
+        return -2;   // the message is set by objective_fail
+      }
+      *err = cudaGetLastError();
+      return 0;
   }
   *err = cudaErrorInvalidValue;
   return -1;
@@ -223,6 +247,7 @@ plam_status_t launch_iteration(plam_handle_s* h, T* X, int64_t ldx, int variant,
   cudaError_t e;
   if (ev) CK(cudaEventRecord(ev[0], s));
   int k = launch_objective<T>(h, X, ldx, G, h->ldw, h->st, s, &e);
+  if (k == -2) return objective_fail();
   if (k < 0 || e != cudaSuccess) return cuda_fail(e, "objective gradient");
   if (ev) CK(cudaEventRecord(ev[1], s));
   int nch = h->nchunks;
@@ -255,7 +280,7 @@ plam_status_t launch_iteration(plam_handle_s* h, T* X, int64_t ldx, int variant,
   }
   if (ev) CK(cudaEventRecord(ev[4], s));
   CK(launch_step_size<T>(nrt, nct, (const T*)h->colpart, (const T*)h->totpart, h->feas_row,
-                         h->fpart, h->obj.kind == PLAM_OBJ_HARTREE1D ? h->nfpart : 0, h->sums,
+                         h->fpart, h->nfpart, h->sums,
                          h->ticket, h->st, h->nubuf, (T*)h->coef, h->hist, ip, s));
   if (ev) CK(cudaEventRecord(ev[5], s));
   CK(launch_primal_update<T>(h->n, p, X, ldx, (const T*)h->R[0], (const T*)h->R[1], h->ldw,
@@ -393,6 +418,7 @@ template <typename T>
 plam_status_t energy_impl(plam_handle_s* h, const T* X, int64_t ldx, T* G, int64_t ldg, double* f) {
   cudaError_t e;
   const int k = launch_objective<T>(h, X, ldx, G, ldg, nullptr, h->stream, &e);
+  if (k == -2) return objective_fail();
   if (k < 0 || e != cudaSuccess) return cuda_fail(e, "objective gradient");
   h->launches += k;
   if (f) {
@@ -400,7 +426,7 @@ plam_status_t energy_impl(plam_handle_s* h, const T* X, int64_t ldx, T* G, int64
                                                               h->dotpart);
     CK(cudaGetLastError());
     h->launches += 1;
-    const int nf = h->obj.kind == PLAM_OBJ_HARTREE1D ? h->nfpart : 0;
+    const int nf = h->nfpart;
     CK(cudaMemcpyAsync(h->scal_host, h->dotpart, kDotBlocks * sizeof(double), cudaMemcpyDeviceToHost,
                        h->stream));
     if (nf > 0)
@@ -410,7 +436,73 @@ plam_status_t energy_impl(plam_handle_s* h, const T* X, int64_t ldx, T* G, int64
     double xg = 0.0, hy = 0.0;
     for (int i = 0; i < kDotBlocks; ++i) xg += h->scal_host[i];
     for (int i = 0; i < nf; ++i) hy += h->scal_host[kDotBlocks + i];
-    *f = 0.5 * xg - 0.25 * (h->obj.kind == PLAM_OBJ_HARTREE1D ? h->obj.alpha : 0.0) * hy;
+    double cx = 0.0, cf = 0.0;
+    f_coefficients(h, &cx, &cf);
+    *f = cx * xg + cf * hy;
+  }
+  return PLAM_OK;
+}
+
+// f(X) into device memory without a host synchronisation: the gradient goes
+// to the handle's G buffer, f = f_xg <X, G> + f_part (sum of the f partials).
+__global__ void energy_finalize_kernel(const double* __restrict__ dotpart, int ndot,
+                                       const double* __restrict__ fpart, int nf, double f_xg,
+                                       double f_part, double* __restrict__ f) {
+  if (threadIdx.x == 0) {
+    double xg = 0.0, hy = 0.0;
+    for (int i = 0; i < ndot; ++i) xg += dotpart[i];
+    for (int i = 0; i < nf; ++i) hy += fpart[i];
+    *f = f_xg * xg + f_part * hy;
+  }
+}
+
+template <typename T>
+__global__ void scale_columns_kernel(int64_t n, int p, const double* __restrict__ s, T* G,
+                                     int64_t ldg) {
+  const T sc = (T)*s;
+  const int c = blockIdx.y;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x)
+    G[r + (int64_t)c * ldg] *= sc;
+}
+
+template <typename T>
+plam_status_t energy_device_impl(plam_handle_s* h, const T* X, int64_t ldx, double* f) {
+  cudaError_t e;
+  T* G = (T*)h->G;
+  const int k = launch_objective<T>(h, X, ldx, G, h->ldw, nullptr, h->stream, &e);
+  if (k == -2) return objective_fail();
+  if (k < 0 || e != cudaSuccess) return cuda_fail(e, "objective gradient");
+  double cx = 0.0, cf = 0.0;
+  f_coefficients(h, &cx, &cf);
+  int ndot = 0;
+  if (cx != 0.0) {
+    dot_partial_kernel<T><<<kDotBlocks, 256, 0, h->stream>>>(h->n, (int)h->p, X, ldx, G, h->ldw,
+                                                              h->dotpart);
+    CK(cudaGetLastError());
+    ndot = kDotBlocks;
+  }
+  energy_finalize_kernel<<<1, 32, 0, h->stream>>>(h->dotpart, ndot, h->fpart, h->nfpart, cx, cf, f);
+  CK(cudaGetLastError());
+  h->launches += k + (ndot > 0 ? 2 : 1);
+  return PLAM_OK;
+}
+
+template <typename T>
+plam_status_t energy_backward_impl(plam_handle_s* h, const T* X, int64_t ldx, const double* s,
+                                   T* G, int64_t ldg) {
+  cudaError_t e;
+  const int k = launch_objective<T>(h, X, ldx, G, ldg, nullptr, h->stream, &e);
+  if (k == -2) return objective_fail();
+  if (k < 0 || e != cudaSuccess) return cuda_fail(e, "objective gradient");
+  h->launches += k;
+  if (s) {
+    int64_t bx = (h->n + 255) / 256;
+    if (bx > 64) bx = 64;
+    scale_columns_kernel<T><<<dim3((unsigned)bx, (unsigned)h->p), 256, 0, h->stream>>>(
+        h->n, (int)h->p, s, G, ldg);
+    CK(cudaGetLastError());
+    h->launches += 1;
   }
   return PLAM_OK;
 }
@@ -458,6 +550,10 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
           (int64_t)obj->nx * obj->ny * obj->nz != n || n > 2147483647 ||
           (obj->V && !aligned(obj->V, esz)))
         return PLAM_ERR_INVALID;
+      break;
+    case PLAM_OBJ_CALLBACK:
+      if (!obj->grad) return PLAM_ERR_INVALID;
+      if (prm->engine == PLAM_ENGINE_RESIDENT) return PLAM_ERR_UNSUPPORTED;
       break;
     default:
       return PLAM_ERR_INVALID;
@@ -522,6 +618,10 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
     ok = alloc((void**)&h->rho, n * sizeof(double)) && alloc((void**)&h->y, n * sizeof(double)) &&
          alloc((void**)&h->blk, 2 * (size_t)h->nfpart * sizeof(double)) &&
          alloc((void**)&h->fpart, (size_t)h->nfpart * sizeof(double));
+  }
+  if (ok && obj->kind == PLAM_OBJ_CALLBACK) {
+    h->nfpart = 1;
+    ok = alloc((void**)&h->fpart, sizeof(double));
   }
   if (ok && prm->final_orth == 2) ok = alloc((void**)&h->Qtmp, (size_t)h->ldw * p * sizeof(double));
   if (ok && prm->engine != PLAM_ENGINE_GRAPH && prm->precision == PLAM_PREC_FP32 &&
@@ -628,7 +728,8 @@ plam_status_t plam_solve(plam_handle_t h, void* X, int64_t ldx, double* Xout, in
   const int lambda2 = (variant == PLAM_VARIANT_PCAL && h->prm.lambda_rule == PLAM_LAMBDA2);
   plam_status_t st = reset_state(h);
   if (st != PLAM_OK) return st;
-  const int gi = h->prm.graph_iters;
+  // a user gradient runs on the host between the kernels: no graph capture
+  const int gi = h->obj.kind == PLAM_OBJ_CALLBACK ? 0 : h->prm.graph_iters;
   int stop = kRunning;
   if (h->r_nblk > 0) {
     // resident engine: the whole loop in one cooperative launch
@@ -721,6 +822,23 @@ plam_status_t plam_solve(plam_handle_t h, void* X, int64_t ldx, double* Xout, in
     inf->feas_orth = feas;
   }
   return stop == kConverged ? PLAM_OK : PLAM_ERR_NOT_CONVERGED;
+}
+
+plam_status_t plam_energy(plam_handle_t h, const void* X, int64_t ldx, double* f_dev) {
+  if (!h || !X || !f_dev || ldx < h->n || !aligned(X, h->esz)) return PLAM_ERR_INVALID;
+  plam_status_t st = h->prec == PLAM_PREC_FP64
+                         ? energy_device_impl<double>(h, (const double*)X, ldx, f_dev)
+                         : energy_device_impl<float>(h, (const float*)X, ldx, f_dev);
+  return st;
+}
+
+plam_status_t plam_energy_backward(plam_handle_t h, const void* X, int64_t ldx,
+                                   const double* scale_dev, void* G, int64_t ldg) {
+  if (!h || !X || !G || ldx < h->n || ldg < h->n) return PLAM_ERR_INVALID;
+  if (!aligned(X, h->esz) || !aligned(G, h->esz)) return PLAM_ERR_INVALID;
+  return h->prec == PLAM_PREC_FP64
+             ? energy_backward_impl<double>(h, (const double*)X, ldx, scale_dev, (double*)G, ldg)
+             : energy_backward_impl<float>(h, (const float*)X, ldx, scale_dev, (float*)G, ldg);
 }
 
 plam_status_t plam_energy_grad(plam_handle_t h, const void* X, int64_t ldx, void* G, int64_t ldg,

@@ -50,6 +50,7 @@ struct IterParams {
   double gamma;     // constant rule
   double tol;
   double hartree_alpha;  // f correction term for the Hartree objective (0 otherwise)
+  double f_xg, f_part;   // f = f_xg <X, G> + f_part (sum of the objective's f partials)
 };
 
 // Number of per-column dot products written by the update kernel and the
