@@ -145,8 +145,10 @@ typedef struct {
   double eta;           /* last eta used for an update */
   double K0;            /* ||G^0 - X^0 Psi(G^0^T X^0)||_F */
   double eta0;          /* eta at k = 0 */
-  double f_orth;        /* after the final orthonormalisation (NaN if not run) */
-  double kkt_orth;      /* relative KKT after the final orthonormalisation */
+  double f_orth;        /* f after the final orthonormalisation (NaN if not run; evaluated in the
+                           storage precision: FP32 mode rounds the FP64 output to float first) */
+  double kkt_orth;      /* relative KKT after the final orthonormalisation (likewise; NaN when
+                           p x 16 storage-type values exceed 227 KB of shared memory) */
   double feas_orth;     /* ||Q^T Q - I||_F of the orthonormalised output */
 } plam_info_t;
 

@@ -20,6 +20,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "../../include/plam.h"
 #include "plam_common.cuh"
@@ -128,6 +129,8 @@ struct plam_handle_s {
   // tensor-core update GEMM (FP32 mode)
   TcUpdatePlan tcu{};
   float* msplit = nullptr;
+  // KKT residual after the final orthonormalisation: per-CTA partial sums
+  double* kkt_part = nullptr;
 };
 
 namespace {
@@ -355,7 +358,7 @@ void free_handle(plam_handle_s* h) {
                  h->hist,
                  h->rho, h->blk, h->y, h->fpart, h->W, h->Z, h->info, h->feas_dev, h->Qtmp,
                  h->dotpart, h->r_halo, h->r_blk, h->r_part, h->r_red, h->r_dots, h->r_dred,
-                 h->r_bar, h->r_err, h->tc_err, h->msplit};
+                 h->r_bar, h->r_err, h->tc_err, h->msplit, h->kkt_part};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (h->st_host) cudaFreeHost(h->st_host);
@@ -440,6 +443,98 @@ plam_status_t energy_impl(plam_handle_s* h, const T* X, int64_t ldx, T* G, int64
     f_coefficients(h, &cx, &cf);
     *f = cx * xg + cf * hy;
   }
+  return PLAM_OK;
+}
+
+// ||G - Q Psi(Q^T G)||_F^2 after the final orthonormalisation (Section 3.3's
+// KKT measure; C = Q^T G in FP64 column-major): each CTA owns 128 rows of a
+// kKktCols-column block, keeps Psi(C) for the block in shared memory and forms
+// the residual elementwise; per-CTA partial sums in a fixed order.
+constexpr int kKktCols = 16;
+constexpr int kKktBlocksX = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(128)
+kkt_norm_kernel(int64_t n, int p, const T* __restrict__ Q, int64_t ldq, const T* __restrict__ G,
+                int64_t ldg, const double* __restrict__ C, double* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char kkt_smem[];
+  T* L = reinterpret_cast<T*>(kkt_smem);           // [p][kKktCols]
+  const int c0 = blockIdx.y * kKktCols;
+  for (int i = threadIdx.x; i < p * kKktCols; i += blockDim.x) {
+    const int j = i / kKktCols, c = c0 + i % kKktCols;
+    L[i] = c < p ? (T)(0.5 * (C[j + (size_t)c * p] + C[c + (size_t)j * p])) : T(0);
+  }
+  __syncthreads();
+  double s = 0.0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    T acc[kKktCols];
+#pragma unroll
+    for (int c = 0; c < kKktCols; ++c) acc[c] = T(0);
+    for (int j = 0; j < p; ++j) {
+      const T q = Q[r + (int64_t)j * ldq];
+#pragma unroll
+      for (int c = 0; c < kKktCols; ++c) acc[c] = fma(q, L[j * kKktCols + c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < kKktCols; ++c) {
+      if (c0 + c < p) {
+        const double k = (double)(G[r + (int64_t)(c0 + c) * ldg] - acc[c]);
+        s += k * k;
+      }
+    }
+  }
+  __shared__ double red[4];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    part[blockIdx.y * gridDim.x + blockIdx.x] = ((red[0] + red[1]) + red[2]) + red[3];
+}
+
+__global__ void round_to_float_kernel(int64_t n, int p, const double* __restrict__ X, int64_t ldx,
+                                      float* __restrict__ Y, int64_t ldy) {
+  const int c = blockIdx.y;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x)
+    Y[r + (int64_t)c * ldy] = (float)X[r + (int64_t)c * ldx];
+}
+
+// f and the relative KKT value of the orthonormalised output Q (storage type
+// T: the FP64 output itself, or its rounding to FP32 in FP32 mode).
+template <typename T>
+plam_status_t post_orth_metrics(plam_handle_s* h, const T* Q, int64_t ldq, double* f,
+                                double* kkt_rel) {
+  const int p = (int)h->p;
+  T* G = (T*)h->G;
+  plam_status_t st = energy_impl<T>(h, Q, ldq, G, h->ldw, f);
+  if (st != PLAM_OK) return st;
+  CK((launch_gram_partial<T, T>(h->n, p, Q, ldq, G, h->ldw, h->rows_per_chunk, h->nchunks,
+                                 (T*)h->part, nullptr, h->stream)));
+  CK(launch_gram_reduce<T>(p, h->nchunks, 1, (const T*)h->part, h->W, h->C, h->stream));
+  const int gy = (p + kKktCols - 1) / kKktCols;
+  int64_t gx = (h->n + 127) / 128;
+  if (gx > kKktBlocksX) gx = kKktBlocksX;
+  const size_t smem = (size_t)p * kKktCols * sizeof(T);
+  if (smem > 232448) {   // Psi(C) block does not fit in shared memory: not evaluated
+    *kkt_rel = NAN;
+    return PLAM_OK;
+  }
+  CK(cudaFuncSetAttribute(kkt_norm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)smem));
+  kkt_norm_kernel<T><<<dim3((unsigned)gx, (unsigned)gy), 128, smem, h->stream>>>(
+      h->n, p, Q, ldq, G, h->ldw, h->C, h->kkt_part);
+  CK(cudaGetLastError());
+  h->launches += 3;
+  const size_t np = (size_t)gx * gy;
+  std::vector<double> hp(np);
+  CK(cudaMemcpyAsync(hp.data(), h->kkt_part, np * sizeof(double), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  double s = 0.0;
+  for (size_t i = 0; i < np; ++i) s += hp[i];
+  const double K0 = h->st_host->K0;
+  *kkt_rel = K0 > 0 ? std::sqrt(s) / K0 : 0.0;
   return PLAM_OK;
 }
 
@@ -612,7 +707,9 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
             alloc((void**)&h->hist, (size_t)h->hist_cap * 5 * sizeof(double)) &&
             alloc((void**)&h->W, pp * sizeof(double)) && alloc((void**)&h->Z, pp * sizeof(double)) &&
             alloc((void**)&h->info, sizeof(int)) && alloc((void**)&h->feas_dev, sizeof(double)) &&
-            alloc((void**)&h->dotpart, kDotBlocks * sizeof(double));
+            alloc((void**)&h->dotpart, kDotBlocks * sizeof(double)) &&
+            alloc((void**)&h->kkt_part, (size_t)kKktBlocksX * ((p + kKktCols - 1) / kKktCols) *
+                                            sizeof(double));
   if (ok && obj->kind == PLAM_OBJ_HARTREE1D) {
     h->nfpart = hartree_blocks(n);
     ok = alloc((void**)&h->rho, n * sizeof(double)) && alloc((void**)&h->y, n * sizeof(double)) &&
@@ -820,6 +917,20 @@ plam_status_t plam_solve(plam_handle_t h, void* X, int64_t ldx, double* Xout, in
     st = plam_orthonormalize(h, X, ldx, Xout, ldo, h->prm.final_orth, &feas);
     if (st != PLAM_OK) return st;
     inf->feas_orth = feas;
+    // Table "orth step": f and KKT of the orthonormalised output
+    if (h->prec == PLAM_PREC_FP64) {
+      st = post_orth_metrics<double>(h, Xout, ldo, &inf->f_orth, &inf->kkt_orth);
+    } else {
+      float* Qf = (float*)h->R[0];
+      int64_t bx = (h->n + 255) / 256;
+      if (bx > 64) bx = 64;
+      round_to_float_kernel<<<dim3((unsigned)bx, (unsigned)h->p), 256, 0, h->stream>>>(
+          h->n, (int)h->p, Xout, ldo, Qf, h->ldw);
+      CK(cudaGetLastError());
+      h->launches += 1;
+      st = post_orth_metrics<float>(h, Qf, h->ldw, &inf->f_orth, &inf->kkt_orth);
+    }
+    if (st != PLAM_OK) return st;
   }
   return stop == kConverged ? PLAM_OK : PLAM_ERR_NOT_CONVERGED;
 }

@@ -4,8 +4,12 @@
                                       alpha = 1, q = 1/4, seeded orthonormal start): the
                                       oracle's PCAL (beta = 1e3) run to relative KKT 1e-9,
                                       then orthonormalised (Householder QR).
+  stencil3d_n262144_p256_optimum.json f* of the 3D workload (7-point Dirichlet Laplacian on
+                                      64^3 plus the seeded potential V iid U[0,1], p = 256):
+                                      half the sum of the 256 smallest eigenvalues (Ky Fan),
+                                      oracle.objectives.trace_min_optimum (about 40 minutes).
 
-Run from the repository root:  python tests/golden/make_golden.py
+Run from the repository root:  python tests/golden/make_golden.py [hartree1d] [stencil3d]
 """
 import json
 import os
@@ -18,7 +22,7 @@ sys.path.insert(0, ROOT)
 
 from oracle import objectives as oo  # noqa: E402
 from oracle import plam as op  # noqa: E402
-from workloads import workload_hartree1d  # noqa: E402
+from workloads import workload_hartree1d, workload_stencil3d  # noqa: E402
 
 
 def hartree_optimum():
@@ -34,8 +38,26 @@ def hartree_optimum():
             "source": "oracle/plam.py solve() run by tests/golden/make_golden.py"}
 
 
+def stencil_optimum():
+    w = workload_stencil3d(m=64, p=256)
+    obj = oo.Stencil3DObjective(w.m, w.V)
+    t0 = time.time()
+    f, ev = oo.trace_min_optimum(obj.H, w.p)
+    return {"workload": w.name, "n": w.n, "p": w.p, "m": w.m, "f_star": f,
+            "lambda_1": float(ev[0]), "lambda_p": float(ev[-1]),
+            "oracle_seconds": round(time.time() - t0, 1),
+            "source": "oracle/objectives.py trace_min_optimum() run by tests/golden/make_golden.py"}
+
+
 if __name__ == "__main__":
-    d = hartree_optimum()
-    with open(os.path.join(HERE, "hartree1d_n20000_p50_optimum.json"), "w") as fh:
-        json.dump(d, fh, indent=1)
-    print(d)
+    which = sys.argv[1:] or ["hartree1d"]
+    if "hartree1d" in which:
+        d = hartree_optimum()
+        with open(os.path.join(HERE, "hartree1d_n20000_p50_optimum.json"), "w") as fh:
+            json.dump(d, fh, indent=1)
+        print(d)
+    if "stencil3d" in which:
+        d = stencil_optimum()
+        with open(os.path.join(HERE, "stencil3d_n262144_p256_optimum.json"), "w") as fh:
+            json.dump(d, fh, indent=1)
+        print(d)

@@ -198,6 +198,12 @@ def test_dense_trace_solve_fp64(variant):
     assert abs(obj.value(Q) - fstar) <= 1e-10 * abs(fstar)
     assert info.feas_orth <= 1e-12
     assert op.feasibility(Q) <= 1e-12
+    # Table "orth step": f and the relative KKT value after the orthonormalisation, evaluated on
+    # the device, against the same quantities of the returned Q on the host
+    assert abs(info.f_orth - obj.value(Q)) <= 1e-12 * abs(fstar)
+    Gq = obj.grad(Q)
+    kq = np.linalg.norm(Gq - Q @ op.psi(Q.T @ Gq)) / info.K0
+    assert abs(info.kkt_orth - kq) <= 1e-6 * kq + 1e-14
     # subspaces: each is within ||KKT|| / gap of the exact eigenspace (Davis-Kahan)
     Qr = ref.X_orth
     gap = ev[20] - ev[19]
@@ -258,8 +264,13 @@ def test_hartree_full_size(precision, tol, ftol):
     assert abs(obj.value(Q) - g["f_star"]) <= ftol * abs(g["f_star"])
     assert op.feasibility(Q) <= 1e-12
     G = obj.grad(Q)
-    assert np.linalg.norm(op.kkt_residual(G, Q)) / g["K0"] <= 2.0 * tol
+    kq = np.linalg.norm(op.kkt_residual(G, Q)) / g["K0"]
+    assert kq <= 2.0 * tol
     assert abs(info.K0 - g["K0"]) <= 1e-5 * g["K0"]
+    # the device's own f and KKT of Q (FP32 mode: Q rounded to float, float arithmetic)
+    frel = 1e-12 if precision == "fp64" else 1e-6
+    assert abs(info.f_orth - obj.value(Q)) <= frel * abs(g["f_star"])
+    assert abs(info.kkt_orth - kq) <= (1e-6 if precision == "fp64" else 0.05) * kq + 1e-12
     s.close()
 
 
