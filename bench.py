@@ -55,6 +55,10 @@ def parse_args():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--kernel-iters", type=int, default=0,
+                    help="only time the kernel groups of this many iterations (graph engine's "
+                         "kernels launched one by one) and print them; a short, profiler-sized run")
+    ap.add_argument("--tensor-cores", choices=["auto", "off", "tf32", "3xtf32"], default="auto")
     return ap.parse_args()
 
 
@@ -207,7 +211,8 @@ def golden_fstar(name):
 def make_solver(wl, precision, torch, engine="auto", final_orth=1, maxit=3000):
     from paper_1810_03930_gb300 import Solver
     kw = dict(variant="pcal", lambda_rule="lambda2", beta=wl["beta"], tol=wl["tol"], maxit=maxit,
-              precision=precision, final_orth=final_orth, graph_iters=16, engine=engine)
+              precision=precision, final_orth=final_orth, graph_iters=16, engine=engine,
+              tensor_cores=wl.get("tensor_cores", "auto"))
     if wl["kind"] == "stencil3d":
         m = wl["m"]
         return Solver(wl["n"], wl["p"], "stencil3d", grid=(m, m, m), V=wl["V"], **kw)
@@ -476,9 +481,27 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def run_kernel_iters(args):
+    """Per-kernel-group milliseconds of the first --kernel-iters iterations (mixed path)."""
+    import torch
+    wl = dict(WORKLOADS[args.workload], tensor_cores=args.tensor_cores)
+    w = load_inputs(wl)
+    from paper_1810_03930_gb300 import colmajor_to_device
+    sol = make_solver(wl, "fp32", torch, engine="graph")
+    X = colmajor_to_device(w.X0, torch.float32)
+    kms, done = sol.time_kernels(X, args.kernel_iters)
+    sol.close()
+    print(json.dumps({"workload": wl["name"], "tensor_cores": args.tensor_cores, "iterations": done,
+                      "kernels_ms_per_launch": kms}), flush=True)
+
+
 def main():
     args = parse_args()
     rank, world, local = dist_env()
+    if args.kernel_iters > 0:
+        if rank == 0:
+            run_kernel_iters(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
