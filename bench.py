@@ -87,14 +87,14 @@ def barrier(world):
     torch.cuda.synchronize()
 
 
-def reduce_max_sum(world, tmax, tsum):
-    """(max over ranks of tmax, sum over ranks of tsum)."""
+def reduce_max_sum(world, tmax, tsum, device="cuda"):
+    """(max over ranks of tmax, sum over ranks of tsum); device "cpu" for a gloo group."""
     if world == 1:
         return tmax, tsum
     import torch
     import torch.distributed as dist
-    a = torch.tensor([tmax], dtype=torch.float64, device="cuda")
-    b = torch.tensor([tsum], dtype=torch.float64, device="cuda")
+    a = torch.tensor([tmax], dtype=torch.float64, device=device)
+    b = torch.tensor([tsum], dtype=torch.float64, device=device)
     dist.all_reduce(a, op=dist.ReduceOp.MAX)
     dist.all_reduce(b, op=dist.ReduceOp.SUM)
     return float(a.item()), float(b.item())

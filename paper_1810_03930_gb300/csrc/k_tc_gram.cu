@@ -366,8 +366,18 @@ void tc_gram_plan(int64_t n, int p, int with_g, TcGramPlan* pl) {
   for (int mb = 0; mb < pl->nmb; ++mb) nbt += pl->nnb - (mb * kTcM) / pl->N;
   pl->nbt = nbt;
   pl->ntiles = nbt + (with_g ? pl->nmb * pl->nnb : 0);
-  // one wave of one CTA per SM: chunks x tiles <= SMs (a second, partial wave doubles the time)
-  int64_t nch = device_sm_count() / pl->ntiles;
+  // chunks per tile: the fewest that fill at least 94% of whole waves of one CTA per SM (a
+  // last, partial wave costs as much as a full one; every chunk adds 2 p^2 partial sums)
+  const int sms = device_sm_count();
+  int64_t nch = 1;
+  double best = 0.0;
+  for (int64_t c = 1; c <= 4 * (int64_t)sms / pl->ntiles + 1 && c <= 1024; ++c) {
+    const int64_t ctas = c * pl->ntiles;
+    const int64_t waves = (ctas + sms - 1) / sms;
+    const double eff = (double)ctas / (double)(waves * sms);
+    if (eff > best + 1e-3) { best = eff; nch = c; }
+    if (eff >= 0.94) break;
+  }
   const int64_t max_ch = (n + kTcK - 1) / kTcK;
   if (nch > max_ch) nch = max_ch;
   if (nch < 1) nch = 1;
