@@ -226,6 +226,45 @@ plam_status_t plam_energy(plam_handle_t h, const void* X, int64_t ldx, double* f
 plam_status_t plam_energy_backward(plam_handle_t h, const void* X, int64_t ldx,
                                    const double* scale_dev, void* G, int64_t ldg);
 
+/* ---- Batched solves: many independent dense trace problems
+ * f_b = 1/2 tr(X_b^T A_b X_b) (Problem 3, Section 5.2) of uneven sizes in ONE
+ * persistent launch.  Each CTA takes problems from a device work queue (largest
+ * n^2 p first) and runs the whole PLAM / PCAL loop of one problem with
+ * block-level synchronisation; FP32 storage and products, FP64 p x p algebra,
+ * and the FP64 Cholesky-QR of each final iterate.  The launch, the queue reset
+ * and the copy of the results are captured once in a CUDA graph and replayed. */
+typedef struct {
+  int64_t n, p;         /* 1 <= p <= 64, 2p <= n */
+  const void* A;        /* device float, n x n symmetric, column-major */
+  int64_t lda;          /* >= n */
+  void* X;              /* device float, n x p: the start on entry, the last iterate on return */
+  int64_t ldx;          /* >= n */
+  double* Q;            /* device FP64 n x p: orthonormalised output (NULL: not formed) */
+  int64_t ldq;          /* >= n when Q is given */
+} plam_batch_problem_t;
+
+typedef struct plam_batch_s* plam_batch_t;
+
+/* prm: precision must be PLAM_PREC_FP32; variant, lambda_rule, beta, eta rule,
+ * tol and maxit apply to every problem.  The problem array is copied; A, X and
+ * Q stay owned by the caller and must outlive the batch.  The workspace (three
+ * n x p float buffers per problem) is allocated here. */
+plam_status_t plam_batch_create(plam_batch_t* b, const plam_batch_problem_t* probs, int count,
+                                const plam_params_t* prm, void* stream);
+/* Solves every problem; infos (host, count entries, may be NULL) receives each
+ * problem's result in the layout of plam_info_t (status PLAM_OK when it
+ * converged; f_orth and kkt_orth are NaN).  Returns PLAM_OK unless a CUDA call
+ * failed. */
+plam_status_t plam_batch_solve(plam_batch_t b, plam_info_t* infos);
+/* The autotuner: times `iters` iterations of every problem for each row-block
+ * height of the kernel's tiles (64, 128, 256) from the current X (restored
+ * after each trial) and keeps the fastest; *tile_rows and *ms (may be NULL)
+ * receive the choice and its time. */
+plam_status_t plam_batch_autotune(plam_batch_t b, int iters, int* tile_rows, double* ms);
+/* Fixes the row-block height (64, 128 or 256; default 128). */
+plam_status_t plam_batch_set_tile(plam_batch_t b, int tile_rows);
+plam_status_t plam_batch_destroy(plam_batch_t b);
+
 /* The split-K tall-skinny Grams of one iteration (Table "cost": X^T X and
  * grad f^T X): B = X^T X and C = X^T G as FP64 p x p column-major device
  * matrices with leading dimension p.  Partial sums over row chunks go through

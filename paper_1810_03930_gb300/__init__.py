@@ -255,3 +255,59 @@ class Solver:
 
     def kernel_launches(self):
         return plam_kernel_launches(self.h)
+
+
+class BatchSolver:
+    """Many independent dense trace problems f_b = 1/2 tr(X_b^T A_b X_b) (p_b <= 64) solved in one
+    persistent launch (plam_batch_*).  As, X0s: sequences of n_b x n_b and n_b x p_b host arrays
+    (or (p, ld) device tensors from colmajor_to_device).  FP32 storage; FP64 outputs Q_b."""
+
+    def __init__(self, As, X0s, *, variant="pcal", lambda_rule="lambda2", beta=1.0, eta_rule="abb",
+                 eta0=0.0, eta_gamma=0.0, tol=1e-6, maxit=3000, orthonormalize=True, stream=None):
+        torch = _torch()
+        prm = plam_default_params()
+        prm.variant = PLAM_VARIANT_PCAL if variant == "pcal" else PLAM_VARIANT_PLAM
+        prm.lambda_rule = PLAM_LAMBDA2 if lambda_rule == "lambda2" else PLAM_LAMBDA1
+        prm.beta, prm.eta_rule = float(beta), _RULES[eta_rule]
+        prm.eta0, prm.eta_gamma = float(eta0), float(eta_gamma)
+        prm.tol, prm.maxit = float(tol), int(maxit)
+        prm.precision = PLAM_PREC_FP32
+        self.A, self.X, self.Q, probs = [], [], [], []
+        for A, X0 in zip(As, X0s):
+            At = A if isinstance(A, torch.Tensor) else colmajor_to_device(A, torch.float32)
+            Xt = X0 if isinstance(X0, torch.Tensor) else colmajor_to_device(X0, torch.float32)
+            p, n = Xt.shape[0], (X0.shape[0] if not isinstance(X0, torch.Tensor) else At.shape[0])
+            Qt = torch.zeros((p, n), dtype=torch.float64, device="cuda") if orthonormalize else None
+            self.A.append(At)
+            self.X.append(Xt)
+            self.Q.append(Qt)
+            probs.append(_lib.plam_batch_problem_t(n, p, At.data_ptr(), At.stride(0), Xt.data_ptr(),
+                                                   Xt.stride(0), Qt.data_ptr() if Qt is not None else None,
+                                                   Qt.stride(0) if Qt is not None else 0))
+        self.count = len(probs)
+        self.stream = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        self.h = _lib.plam_batch_create(probs, prm, self.stream)
+
+    def solve(self):
+        st, infos = _lib.plam_batch_solve(self.h, self.count)
+        check(st, "plam_batch_solve")
+        return infos
+
+    def autotune(self, iters=20):
+        st, tile, ms = _lib.plam_batch_autotune(self.h, int(iters))
+        check(st, "plam_batch_autotune")
+        return tile, ms
+
+    def set_tile(self, tile_rows):
+        check(_lib.plam_batch_set_tile(self.h, int(tile_rows)), "plam_batch_set_tile")
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            _lib.plam_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

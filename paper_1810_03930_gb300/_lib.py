@@ -53,6 +53,11 @@ class plam_objective_t(C.Structure):
                 ("V", C.c_void_p), ("grad", plam_grad_fn), ("grad_ctx", C.c_void_p)]
 
 
+class plam_batch_problem_t(C.Structure):
+    _fields_ = [("n", C.c_int64), ("p", C.c_int64), ("A", C.c_void_p), ("lda", C.c_int64),
+                ("X", C.c_void_p), ("ldx", C.c_int64), ("Q", C.c_void_p), ("ldq", C.c_int64)]
+
+
 class plam_info_t(C.Structure):
     _fields_ = [("iters", C.c_int), ("status", C.c_int), ("converged", C.c_int), ("pad_", C.c_int),
                 ("f", C.c_double), ("kkt_rel", C.c_double), ("feas", C.c_double),
@@ -88,6 +93,13 @@ SIGNATURES = {
                                     C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "plam_history": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]),
     "plam_kernel_launches": (C.c_int64, [C.c_void_p]),
+    "plam_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(plam_batch_problem_t), C.c_int,
+                                    C.POINTER(plam_params_t), C.c_void_p]),
+    "plam_batch_solve": (C.c_int, [C.c_void_p, C.POINTER(plam_info_t)]),
+    "plam_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int),
+                                      C.POINTER(C.c_double)]),
+    "plam_batch_set_tile": (C.c_int, [C.c_void_p, C.c_int]),
+    "plam_batch_destroy": (C.c_int, [C.c_void_p]),
     "plam_last_error": (C.c_char_p, []),
     "plam_version": (C.c_int, []),
 }
@@ -228,3 +240,32 @@ def plam_kernel_launches(h) -> int:
 
 def plam_version() -> int:
     return int(load().plam_version())
+
+
+def plam_batch_create(problems, params, stream):
+    arr = (plam_batch_problem_t * len(problems))(*problems)
+    h = C.c_void_p()
+    check(load().plam_batch_create(C.byref(h), arr, len(problems), C.byref(params),
+                                   C.c_void_p(stream)), "plam_batch_create")
+    return h
+
+
+def plam_batch_solve(h, count: int):
+    infos = (plam_info_t * count)()
+    st = load().plam_batch_solve(h, infos)
+    return st, list(infos)
+
+
+def plam_batch_autotune(h, iters: int):
+    tile = C.c_int()
+    ms = C.c_double()
+    st = load().plam_batch_autotune(h, iters, C.byref(tile), C.byref(ms))
+    return st, tile.value, ms.value
+
+
+def plam_batch_set_tile(h, tile_rows: int):
+    return load().plam_batch_set_tile(h, tile_rows)
+
+
+def plam_batch_destroy(h):
+    return load().plam_batch_destroy(h)

@@ -20,6 +20,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/plam.h"
@@ -1053,5 +1054,230 @@ int64_t plam_kernel_launches(plam_handle_t h) { return h ? h->launches : -1; }
 const char* plam_last_error(void) { return g_err; }
 
 int plam_version(void) { return 100; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- batched solves
+
+struct plam_batch_s {
+  int count = 0;
+  cudaStream_t stream = nullptr;
+  plam::BatchParams prm{};
+  int tile = 128;
+  int grid = 1;
+  plam::BatchDesc* desc = nullptr;        // device
+  int* order = nullptr;                   // device
+  int* next = nullptr;                    // device
+  plam_info_t* info = nullptr;            // device
+  plam_info_t* info_host = nullptr;       // pinned
+  float* work = nullptr;                  // device: G, R0, R1 of every problem
+  std::vector<plam::BatchDesc> hdesc;
+  cudaGraphExec_t graph = nullptr;
+  int graph_tile = 0;
+};
+
+namespace {
+
+void free_batch(plam_batch_s* b) {
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  void* dev[] = {b->desc, b->order, b->next, b->info, b->work};
+  for (void* p : dev)
+    if (p) cudaFree(p);
+  if (b->info_host) cudaFreeHost(b->info_host);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+plam_status_t plam_batch_create(plam_batch_t* out, const plam_batch_problem_t* probs, int count,
+                                const plam_params_t* prm, void* stream) {
+  using namespace plam;
+  if (!out) return PLAM_ERR_INVALID;
+  *out = nullptr;
+  if (!probs || count < 1 || !prm || validate_params(prm) != PLAM_OK) return PLAM_ERR_INVALID;
+  if (prm->precision != PLAM_PREC_FP32) {
+    snprintf(g_err, sizeof(g_err), "plam_batch_create: FP32 mode only");
+    return PLAM_ERR_UNSUPPORTED;
+  }
+  size_t work = 0;
+  for (int i = 0; i < count; ++i) {
+    const plam_batch_problem_t& q = probs[i];
+    if (q.p < 1 || q.p > 64 || q.n < 2 * q.p || !q.A || !q.X || q.lda < q.n || q.ldx < q.n ||
+        !aligned(q.A, 4) || !aligned(q.X, 4) || (q.Q && (q.ldq < q.n || !aligned(q.Q, 8))))
+      return PLAM_ERR_INVALID;
+    work += 3 * (size_t)round_up(q.n, 32) * (size_t)q.p;
+  }
+  plam_batch_s* b = new (std::nothrow) plam_batch_s();
+  if (!b) return PLAM_ERR_NOMEM;
+  b->count = count;
+  b->stream = (cudaStream_t)stream;
+  b->prm.variant = prm->variant;
+  b->prm.lambda2 = prm->variant == PLAM_VARIANT_PCAL && prm->lambda_rule == PLAM_LAMBDA2;
+  b->prm.eta_rule = prm->eta_rule;
+  b->prm.maxit = prm->maxit;
+  b->prm.beta = prm->beta;
+  b->prm.eta0_user = prm->eta0;
+  b->prm.gamma = prm->eta_gamma;
+  b->prm.tol = prm->tol;
+  int dev = 0, sms = 1;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  b->grid = count < sms ? count : sms;
+  bool ok = cudaMalloc((void**)&b->desc, count * sizeof(BatchDesc)) == cudaSuccess &&
+            cudaMalloc((void**)&b->order, count * sizeof(int)) == cudaSuccess &&
+            cudaMalloc((void**)&b->next, sizeof(int)) == cudaSuccess &&
+            cudaMalloc((void**)&b->info, count * sizeof(plam_info_t)) == cudaSuccess &&
+            cudaMalloc((void**)&b->work, work * sizeof(float)) == cudaSuccess &&
+            cudaMallocHost((void**)&b->info_host, count * sizeof(plam_info_t)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_batch(b);
+    return PLAM_ERR_NOMEM;
+  }
+  b->hdesc.resize(count);
+  float* w = b->work;
+  for (int i = 0; i < count; ++i) {
+    const plam_batch_problem_t& q = probs[i];
+    BatchDesc& d = b->hdesc[i];
+    d.n = q.n; d.p = (int)q.p; d.pad_ = 0;
+    d.A = (const float*)q.A; d.lda = q.lda; d.X = (float*)q.X; d.ldx = q.ldx;
+    d.ldw = round_up(q.n, 32);
+    d.G = w; w += d.ldw * q.p;
+    d.R0 = w; w += d.ldw * q.p;
+    d.R1 = w; w += d.ldw * q.p;
+    d.Q = q.Q; d.ldq = q.ldq;
+  }
+  // the queue: largest n^2 p first, so that the longest problems start first
+  std::vector<int> ord(count);
+  for (int i = 0; i < count; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+    const double cx = (double)probs[x].n * probs[x].n * probs[x].p;
+    const double cy = (double)probs[y].n * probs[y].n * probs[y].p;
+    return cx > cy;
+  });
+  ok = cudaMemcpy(b->desc, b->hdesc.data(), count * sizeof(BatchDesc), cudaMemcpyHostToDevice) ==
+           cudaSuccess &&
+       cudaMemcpy(b->order, ord.data(), count * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
+       preload_batched_kernels() == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_batch(b);
+    return PLAM_ERR_CUDA;
+  }
+  *out = b;
+  return PLAM_OK;
+}
+
+plam_status_t plam_batch_set_tile(plam_batch_t b, int tile_rows) {
+  if (!b || (tile_rows != 64 && tile_rows != 128 && tile_rows != 256)) return PLAM_ERR_INVALID;
+  b->tile = tile_rows;
+  return PLAM_OK;
+}
+
+plam_status_t plam_batch_solve(plam_batch_t b, plam_info_t* infos) {
+  using namespace plam;
+  if (!b) return PLAM_ERR_INVALID;
+  if (!b->graph || b->graph_tile != b->tile) {
+    if (b->graph) {
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+    cudaStream_t cs = nullptr;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(b->next, 0, sizeof(int), cs);
+    if (ce == cudaSuccess)
+      ce = launch_batched(b->tile, b->desc, b->order, b->count, b->next, b->info, b->prm, b->grid,
+                          cs);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(b->info_host, b->info, b->count * sizeof(plam_info_t),
+                           cudaMemcpyDeviceToHost, cs);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (ce == cudaSuccess) ce = ee;
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return cuda_fail(ce, "batched solve graph");
+    b->graph_tile = b->tile;
+  }
+  CK(cudaGraphLaunch(b->graph, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  if (infos) memcpy(infos, b->info_host, b->count * sizeof(plam_info_t));
+  return PLAM_OK;
+}
+
+plam_status_t plam_batch_autotune(plam_batch_t b, int iters, int* tile_rows, double* ms) {
+  using namespace plam;
+  if (!b || iters < 1) return PLAM_ERR_INVALID;
+  // back up every start, time each tile height from the same starts, restore
+  size_t tot = 0;
+  for (const BatchDesc& d : b->hdesc) tot += (size_t)d.n * d.p;
+  float* bak = nullptr;
+  if (cudaMalloc((void**)&bak, tot * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return PLAM_ERR_NOMEM;
+  }
+  auto copy_all = [&](bool save) -> cudaError_t {
+    size_t off = 0;
+    for (const BatchDesc& d : b->hdesc) {
+      cudaError_t e = save ? cudaMemcpy2DAsync(bak + off, d.n * sizeof(float), d.X,
+                                               d.ldx * sizeof(float), d.n * sizeof(float), d.p,
+                                               cudaMemcpyDeviceToDevice, b->stream)
+                           : cudaMemcpy2DAsync(d.X, d.ldx * sizeof(float), bak + off,
+                                               d.n * sizeof(float), d.n * sizeof(float), d.p,
+                                               cudaMemcpyDeviceToDevice, b->stream);
+      if (e != cudaSuccess) return e;
+      off += (size_t)d.n * d.p;
+    }
+    return cudaSuccess;
+  };
+  BatchParams tp = b->prm;
+  tp.maxit = iters;
+  tp.tol = 0.0;
+  const int tiles[3] = {64, 128, 256};
+  int best = b->tile;
+  double best_ms = INFINITY;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaError_t ce = copy_all(true);
+  for (int i = 0; i < 3 && ce == cudaSuccess; ++i) {
+    for (int rep = 0; rep < 2 && ce == cudaSuccess; ++rep) {   // first run warms up
+      ce = cudaMemsetAsync(b->next, 0, sizeof(int), b->stream);
+      if (ce == cudaSuccess) ce = cudaEventRecord(e0, b->stream);
+      if (ce == cudaSuccess)
+        ce = launch_batched(tiles[i], b->desc, b->order, b->count, b->next, b->info, tp, b->grid,
+                            b->stream);
+      if (ce == cudaSuccess) ce = cudaEventRecord(e1, b->stream);
+      if (ce == cudaSuccess) ce = copy_all(false);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->stream);
+      float t = 0.f;
+      if (ce == cudaSuccess && rep == 1 && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess &&
+          t < best_ms) {
+        best_ms = t;
+        best = tiles[i];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(bak);
+  if (ce != cudaSuccess) return cuda_fail(ce, "batched autotune");
+  b->tile = best;
+  if (tile_rows) *tile_rows = best;
+  if (ms) *ms = best_ms;
+  return PLAM_OK;
+}
+
+plam_status_t plam_batch_destroy(plam_batch_t b) {
+  if (!b) return PLAM_ERR_INVALID;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  free_batch(b);
+  return PLAM_OK;
+}
 
 }  // extern "C"

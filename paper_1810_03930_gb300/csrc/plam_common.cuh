@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/plam.h"
+
 namespace plam {
 
 constexpr int kThreads = 256;     // threads of the tiled kernels (16 x 16 micro-tile grid)
@@ -192,6 +194,33 @@ cudaError_t launch_tc_update(int64_t n, int p, const float* X, int64_t ldx, cons
                              float* totpart, int* err, double refine_switch, int force3,
                              cudaStream_t s);
 cudaError_t preload_tc_update_kernels();
+
+// Batched dense trace problems (p <= 64), one persistent launch: each CTA takes
+// problems from the queue `next` in the host's order and runs the whole loop.
+struct BatchDesc {
+  int64_t n;
+  int p, pad_;
+  const float* A;
+  int64_t lda;
+  float* X;
+  int64_t ldx;
+  float* G;
+  float* R0;
+  float* R1;
+  int64_t ldw;
+  double* Q;        // FP64 output of the final orthonormalisation (may be null)
+  int64_t ldq;
+};
+
+struct BatchParams {
+  int variant, lambda2, eta_rule, maxit;
+  double beta, eta0_user, gamma, tol;
+};
+
+size_t batch_smem_bytes(int rb);
+cudaError_t launch_batched(int rb, const BatchDesc* desc, const int* order, int count, int* next,
+                           plam_info_t* info, BatchParams prm, int grid, cudaStream_t s);
+cudaError_t preload_batched_kernels();
 
 // Force the module load of every kernel (lazy loading must not happen inside
 // a stream capture).
