@@ -40,6 +40,10 @@ WORKLOADS = {
     # 1e-6 of the optimum.  The FP64 path is timed over its first 30 iterations only.
     "stencil3d": dict(kind="stencil3d", m=64, n=262144, p=256, beta=1.0, tol=1e-5,
                       name="stencil3d_n262144_p256", fp64_maxit=30),
+    # 512 independent dense trace problems, n uniform in [64, 2048], p uniform in
+    # [4, min(64, n/2)], beta = 1, PCAL to relative KKT 1e-6 in one persistent launch.
+    "batched": dict(kind="batched", count=512, n_lo=64, n_hi=2048, beta=1.0, tol=1e-6,
+                    name="batched_512_dense_trace_n64-2048_p4-64", fp64_sample=6),
 }
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
@@ -453,7 +457,13 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     wl = dict(WORKLOADS[args.workload])
-    w = load_inputs(wl)
+    if wl["kind"] == "batched":        # the oracle on the batch's first problem per step
+        from workloads import batched_shapes, workload_batched_problem
+        n, p = batched_shapes(count=wl["count"], n_lo=wl["n_lo"], n_hi=wl["n_hi"])[0]
+        w = workload_batched_problem(0, n, p)
+        wl.update(kind="dense", n=n, p=p, A=w.A)
+    else:
+        w = load_inputs(wl)
     from oracle import objectives as oo
     from oracle import plam as op
     obj = oo.objective_for(w)
@@ -495,9 +505,174 @@ def run_kernel_iters(args):
                       "kernels_ms_per_launch": kms}), flush=True)
 
 
+def run_batched(args, rank, world, local):
+    """The batched configuration: one step = one persistent launch solving every problem."""
+    import numpy as np
+    import torch
+    dist_init(world, local)
+    wl = dict(WORKLOADS["batched"])
+    from paper_1810_03930_gb300 import BatchSolver, colmajor_to_device
+    from workloads import batched_shapes, workload_batched_problem
+    shapes = batched_shapes(count=wl["count"], n_lo=wl["n_lo"], n_hi=wl["n_hi"])
+    ws = [workload_batched_problem(i, n, p) for i, (n, p) in enumerate(shapes)]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    bs = BatchSolver([w.A for w in ws], [w.X0 for w in ws], beta=wl["beta"], tol=wl["tol"],
+                     maxit=3000)
+    X0s = [x.clone() for x in bs.X]
+    tile, tune_ms = bs.autotune(iters=20)
+
+    def restore():
+        for x, x0 in zip(bs.X, X0s):
+            x.copy_(x0)
+
+    def step(host=None):
+        flush.zero_()
+        if host is None:
+            restore()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        if host is not None:
+            for x, h in zip(bs.X, host[0]):
+                x.copy_(h, non_blocking=True)
+        infos = bs.solve()
+        if host is not None:
+            for q, h in zip(bs.Q, host[1]):
+                h.copy_(q, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), infos
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    clk = ClockSampler(local)
+    barrier(world)
+    clk.start()
+    ms, its, conv = [], [], []
+    for _ in range(args.steps):
+        t, infos = step()
+        ms.append(t)
+        its.append(sum(i.iters for i in infos))
+        conv.append(sum(1 for i in infos if i.converged))
+    barrier(world)
+    clocks = clk.stop()
+    t_max, it_all = reduce_max_sum(world, sum(ms) / 1e3, float(sum(its)))
+    value = it_all / t_max
+    ms_per_step = 1e3 * t_max / args.steps
+    # parity: the objective of every orthonormalised result against Ky Fan's optimum
+    from oracle import objectives as oo
+    errs = []
+    for w, q in zip(ws[:64], bs.Q[:64]):
+        Q = np.asfortranarray(q[:, : w.n].double().cpu().numpy().T)
+        fstar = 0.5 * np.linalg.eigvalsh(w.A)[: w.p].sum()
+        errs.append(abs(oo.TraceObjective(w.A).value(Q) - fstar) / abs(fstar))
+    parity = {"checked": len(errs), "max_obj_rel_err": float(max(errs)),
+              "converged": conv[-1], "count": len(ws),
+              "max_feas_orth": float(max(i.feas_orth for i in infos))}
+    # roofline: the kernel is bound by its FP32 arithmetic (A stays in L2 while a CTA works on it)
+    flops = sum(i.iters * (2.0 * w.n * w.n * w.p + 8.0 * w.n * w.p * w.p) for w, i in zip(ws, infos))
+    clock_mhz = clocks.get("sm_mhz") or 2070.0
+    peak = 152 * 128 * 2 * clock_mhz * 1e6 / 1e12
+    achieved = flops / (ms_per_step * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "batched_solve_kernel", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x median SM clock "
+                               f"{clock_mhz:.0f} MHz",
+                "alg_flops_per_launch": flops, "launch_ms": ms_per_step}
+    # FP64 comparator: sequential single-problem FP64 solves of a sample, scaled by cost
+    from paper_1810_03930_gb300 import Solver
+    idx = np.linspace(0, len(ws) - 1, wl["fp64_sample"]).astype(int)
+    t64, cost64 = 0.0, 0.0
+    for i in idx:
+        w = ws[i]
+        s = Solver(w.n, w.p, "dense", A=w.A, variant="pcal", beta=wl["beta"], tol=wl["tol"],
+                   maxit=3000, precision="fp64", final_orth=1)
+        Xd = colmajor_to_device(w.X0, torch.float64)
+        Q = s.new_matrix(dtype=torch.float64)
+        s.solve(Xd.clone(), Q)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st, inf = s.solve(Xd, Q)
+        e1.record()
+        torch.cuda.synchronize()
+        t64 += e0.elapsed_time(e1) / 1e3
+        cost64 += w.n * w.n * w.p
+        s.close()
+    cost_all = float(sum(w.n * w.n * w.p for w in ws))
+    fp64 = {"time_to_kkt_s": t64 * cost_all / cost64, "sampled_problems": len(idx),
+            "time_to_kkt_note": "512 sequential FP64 single-problem solves, extrapolated from "
+                                f"{len(idx)} timed ones by the sum of n^2 p"}
+    # end to end: starts from pinned host memory, orthonormalised results back to the host
+    hx = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in bs.X]
+    hq = [torch.empty(q.shape, dtype=q.dtype, pin_memory=True) for q in bs.Q]
+    for h, x0 in zip(hx, X0s):
+        h.copy_(x0.cpu())
+    te, ite = [], 0
+    for _ in range(max(1, args.steps)):
+        t, infos_e = step(host=(hx, hq))
+        te.append(t)
+        ite += sum(i.iters for i in infos_e)
+    t_e, it_e = reduce_max_sum(world, sum(te) / 1e3, float(ite))
+    e2e = {"value": it_e / t_e, "unit": "iters/s", "time_to_kkt_s": t_e / len(te),
+           "h2d_bytes_per_step": int(sum(h.numel() * h.element_size() for h in hx)),
+           "d2h_bytes_per_step": int(sum(h.numel() * h.element_size() for h in hq))}
+    out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": wl["name"], "problems": len(ws),
+                      "objective": "1/2 tr(X_b^T A_b X_b), A_b = (B+B^T)/2, B iid N(0,1)",
+                      "solver": "PCAL eq.(lambda2), ABB, one persistent launch (CUDA graph)",
+                      "beta": wl["beta"], "tol_kkt_rel": wl["tol"], "tile_rows": tile,
+                      "autotune_ms": tune_ms, "final_orth": "FP64 Cholesky-QR per problem",
+                      "l2": "flushed before every step (256 MB write)",
+                      "parallelism": "replicas" if world > 1 else "single GPU"},
+           "time_to_kkt_s": ms_per_step / 1e3, "iters_per_step": statistics.mean(its),
+           "fp64": fp64, "mixed_speedup_vs_fp64": fp64["time_to_kkt_s"] / (ms_per_step / 1e3),
+           "parity": parity, "engine": "batched", "roofline": roofline, "e2e": e2e,
+           "gpu_launches": args.steps, "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_batched(ws, wl, args.cpu_seconds, ms_per_step / 1e3)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    bs.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline_batched(ws, wl, seconds, gpu_s):
+    """The oracle on the host cores: sequential solves of the batch's problems until about
+    `seconds` have passed, extrapolated to the whole batch by the sum of n^2 p."""
+    from oracle import objectives as oo
+    from oracle import plam as op
+    t0 = time.perf_counter()
+    cost_done, done, its = 0.0, 0, 0
+    for w in ws[::-1]:                       # smallest problems last in the list: take a mix
+        r = op.solve(oo.TraceObjective(w.A), w.X0, variant="pcal", beta=wl["beta"], tol=wl["tol"],
+                     maxit=3000, record=False)
+        cost_done += w.n * w.n * w.p
+        done += 1
+        its += r.iters
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    cost_all = float(sum(w.n * w.n * w.p for w in ws))
+    est = dt * cost_all / cost_done
+    return {"value": its / dt, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"FP64 NumPy oracle PCAL, {done} of the {len(ws)} problems solved to KKT "
+                       f"{wl['tol']} in {dt:.1f} s; whole batch extrapolated by the sum of n^2 p: "
+                       f"{est:.0f} s"),
+            "time_to_kkt_s_est": est}
+
+
 def main():
     args = parse_args()
     rank, world, local = dist_env()
+    if args.workload == "batched" and args.impl == "ours" and args.kernel_iters == 0:
+        run_batched(args, rank, world, local)
+        return
     if args.kernel_iters > 0:
         if rank == 0:
             run_kernel_iters(args)

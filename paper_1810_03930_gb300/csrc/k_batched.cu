@@ -9,7 +9,7 @@
 // Per iteration of problem b (FP32 storage and products, FP64 p x p algebra
 // and scalars, as the single-problem FP32 mode):
 //   1. G = A X                      RB x 64 output tiles, 32-deep stages of A and X
-//   2. B = X^T X, C = X^T G          FP32 partial sums flushed into FP64 every 256 rows
+//   2. B = X^T X, C = X^T G          FP32 sums over 32-row stages, added up in FP64
 //   3. Psi(C), d (eq. lambda2), M, ||B - I||, f = 1/2 tr(C)
 //   4. R = G - X M, K = G - X Psi(C) with the column dots and the BB sums
 //   5. eta (Section 5.1 rules), stop test, PCAL column norms nu
@@ -43,72 +43,110 @@ struct BatchSmem {
   int problem;
 };
 
+// one stage buffer: a 32 x RB tile of A and a 32 x 64 tile of X (two buffers per CTA)
 __host__ __device__ inline size_t batch_stage_floats(int rb) { return (size_t)kBK * rb + (size_t)kBK * kBMaxP; }
 
 // ---------------------------------------------------------------- step 1: G = A X
 // The sum over n runs in float within each 32-deep stage and is carried across
 // stages in a compensated (Kahan) pair, so that the FP32 rounding of G grows
-// with the stage depth, not with n.
+// with the stage depth, not with n.  Lane tx owns RB/32 consecutive rows
+// (vector loads from shared memory), warp ty the columns 4ty .. 4ty + 3 (a
+// broadcast float4); the next stage is fetched into registers while the
+// current one is multiplied (two shared-memory buffers, one barrier a stage).
 template <int RB>
-__device__ void batch_ax(const BatchDesc& q, float* stA, float* stX) {
-  constexpr int U = RB / 32;
+__device__ void batch_ax(const BatchDesc& q, float* st0, float* st1) {
+  constexpr int R4 = RB / 32;
+  constexpr int NA = kBK * RB / kBThreads;
+  constexpr int NX = kBK * kBMaxP / kBThreads;
   const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
   const int64_t n = q.n;
-  const int p = q.p, V = (p + 15) / 16;
+  const int p = q.p;
+  const bool active = 4 * ty < p;            // warp-uniform: this warp has columns
+  float pa[NA], px[NX];
   for (int64_t r0 = 0; r0 < n; r0 += RB) {
-    float sum[U][4], comp[U][4];
+    float sum[R4][4], comp[R4][4];
 #pragma unroll
-    for (int u = 0; u < U; ++u)
+    for (int i = 0; i < R4; ++i)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) sum[u][v] = comp[u][v] = 0.f;
-    for (int64_t k0 = 0; k0 < n; k0 += kBK) {
-      for (int e = t; e < kBK * RB; e += kBThreads) {
-        const int i = e % RB, kk = e / RB;
+      for (int v = 0; v < 4; ++v) sum[i][v] = comp[i][v] = 0.f;
+    auto fetch = [&](int64_t k0) {
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        const int e = t + j * kBThreads, i = e % RB, kk = e / RB;
         const int64_t r = r0 + i, kc = k0 + kk;
-        stA[kk * RB + i] = (r < n && kc < n) ? q.A[r + kc * q.lda] : 0.f;
+        pa[j] = (r < n && kc < n) ? q.A[r + kc * q.lda] : 0.f;
       }
-      for (int e = t; e < kBK * kBMaxP; e += kBThreads) {
-        const int kk = e % kBK, c = e / kBK;
+#pragma unroll
+      for (int j = 0; j < NX; ++j) {
+        const int e = t + j * kBThreads, kk = e % kBK, c = e / kBK;
         const int64_t kr = k0 + kk;
-        stX[kk * kBMaxP + c] = (kr < n && c < p) ? q.X[kr + (int64_t)c * q.ldx] : 0.f;
+        px[j] = (kr < n && c < p) ? q.X[kr + (int64_t)c * q.ldx] : 0.f;
       }
+    };
+    auto stash = [&](float* st) {
+#pragma unroll
+      for (int j = 0; j < NA; ++j) st[t + j * kBThreads] = pa[j];
+#pragma unroll
+      for (int j = 0; j < NX; ++j) {
+        const int e = t + j * kBThreads;
+        st[kBK * RB + (e % kBK) * kBMaxP + e / kBK] = px[j];
+      }
+    };
+    fetch(0);
+    stash(st0);
+    __syncthreads();
+    int buf = 0;
+    for (int64_t k0 = 0; k0 < n; k0 += kBK) {
+      const bool more = k0 + kBK < n;
+      if (more) fetch(k0 + kBK);
+      const float* st = buf ? st1 : st0;
+      if (active) {
+        float acc[R4][4];
+#pragma unroll
+        for (int i = 0; i < R4; ++i)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[i][v] = 0.f;
+#pragma unroll 4
+        for (int kk = 0; kk < kBK; ++kk) {
+          float a[R4];
+#pragma unroll
+          for (int i4 = 0; i4 < R4; i4 += 2) {
+            const float2 a2 = *reinterpret_cast<const float2*>(st + kk * RB + tx * R4 + i4);
+            a[i4] = a2.x;
+            a[i4 + 1] = a2.y;
+          }
+          const float4 b = *reinterpret_cast<const float4*>(st + kBK * RB + kk * kBMaxP + 4 * ty);
+#pragma unroll
+          for (int i = 0; i < R4; ++i) {
+            acc[i][0] = fmaf(a[i], b.x, acc[i][0]);
+            acc[i][1] = fmaf(a[i], b.y, acc[i][1]);
+            acc[i][2] = fmaf(a[i], b.z, acc[i][2]);
+            acc[i][3] = fmaf(a[i], b.w, acc[i][3]);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < R4; ++i)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const float y = acc[i][v] - comp[i][v];
+            const float s2 = sum[i][v] + y;
+            comp[i][v] = (s2 - sum[i][v]) - y;
+            sum[i][v] = s2;
+          }
+      }
+      if (more) stash(buf ? st0 : st1);
       __syncthreads();
-      float acc[U][4];
+      buf ^= 1;
+    }
+    if (active) {
 #pragma unroll
-      for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
-#pragma unroll 8
-      for (int kk = 0; kk < kBK; ++kk) {
-        float a[U], b[4];
-#pragma unroll
-        for (int u = 0; u < U; ++u) a[u] = stA[kk * RB + tx + 32 * u];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) b[v] = stX[kk * kBMaxP + ty + 16 * v];
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-          for (int v = 0; v < 4; ++v)
-            if (v < V) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u)
+      for (int i = 0; i < R4; ++i) {
+        const int64_t r = r0 + tx * R4 + i;
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          const float y = acc[u][v] - comp[u][v];
-          const float s2 = sum[u][v] + y;
-          comp[u][v] = (s2 - sum[u][v]) - y;
-          sum[u][v] = s2;
+          const int c = 4 * ty + v;
+          if (r < n && c < p) q.G[r + (int64_t)c * q.ldw] = sum[i][v];
         }
-      __syncthreads();
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t r = r0 + tx + 32 * u;
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const int c = ty + 16 * v;
-        if (r < n && c < p) q.G[r + (int64_t)c * q.ldw] = sum[u][v];
       }
     }
   }
@@ -161,7 +199,7 @@ __device__ void batch_grams(const BatchDesc& q, const float* Y, int64_t ldy, flo
         }
     }
     __syncthreads();
-    if (!exact && ((stage & 7) == 7 || r0 + kBK >= n)) {   // flush every 256 rows
+    if (!exact) {   // each 32-row stage's float sums into the FP64 totals
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -201,7 +239,7 @@ __device__ void batch_solve_one(const BatchDesc& q, const BatchParams& prm, plam
     float* R = (k & 1) ? q.R1 : q.R0;
     const float* Rp = (k & 1) ? q.R0 : q.R1;
     // 1-2. gradient and Grams
-    batch_ax<RB>(q, stA, stX);
+    batch_ax<RB>(q, stA, stX);   // stA, stX: the two stage buffers
     __syncthreads();
     batch_grams<false>(q, q.G, q.ldw, stA, stX, S.B, S.C);
     // 3. p x p algebra in FP64
@@ -456,7 +494,7 @@ batched_solve_kernel(const BatchDesc* __restrict__ desc, const int* __restrict__
   extern __shared__ __align__(16) unsigned char bsm[];
   BatchSmem& S = *reinterpret_cast<BatchSmem*>(bsm);
   float* stA = reinterpret_cast<float*>(bsm + ((sizeof(BatchSmem) + 15) & ~(size_t)15));
-  float* stX = stA + kBK * RB;
+  float* stX = stA + batch_stage_floats(RB);     // second stage buffer
   if (threadIdx.x == 0) S.flags[1] = 0;
   for (;;) {
     if (threadIdx.x == 0) S.problem = atomicAdd(next, 1);
@@ -472,7 +510,7 @@ batched_solve_kernel(const BatchDesc* __restrict__ desc, const int* __restrict__
 // ---------------------------------------------------------------- host side
 
 size_t batch_smem_bytes(int rb) {
-  return ((sizeof(BatchSmem) + 15) & ~(size_t)15) + batch_stage_floats(rb) * sizeof(float);
+  return ((sizeof(BatchSmem) + 15) & ~(size_t)15) + 2 * batch_stage_floats(rb) * sizeof(float);
 }
 
 cudaError_t launch_batched(int rb, const BatchDesc* desc, const int* order, int count, int* next,
