@@ -59,8 +59,11 @@ typedef enum {
 } plam_status_t;
 
 enum { PLAM_VARIANT_PLAM = 0, PLAM_VARIANT_PCAL = 1 };
-/* Multiplier rule: eq. (Lambda1), or eq. (lambda2) (PCAL only). */
-enum { PLAM_LAMBDA1 = 0, PLAM_LAMBDA2 = 1 };
+/* Multiplier rule: eq. (Lambda1), eq. (lambda2) (PCAL only), or the dual
+ * ascent step of Algorithm 1, Lambda^k = Lambda^{k-1} - beta ((X^k)^T X^k - I)
+ * from Lambda^0 = Psi(grad f(X^0)^T X^0) (PLAM-DA / PCAL-DA, Section 5.3's
+ * comparison; graph engine only). */
+enum { PLAM_LAMBDA1 = 0, PLAM_LAMBDA2 = 1, PLAM_LAMBDA_DA = 2 };
 /* Proximal parameter rules of Section 5.1: alternating BB (default), BB1, BB2,
  * constant gamma, differential ||Y||_F/||S||_F. */
 enum { PLAM_ETA_ABB = 0, PLAM_ETA_BB1 = 1, PLAM_ETA_BB2 = 2, PLAM_ETA_CONST = 3, PLAM_ETA_DIFF = 4 };
@@ -103,7 +106,8 @@ enum { PLAM_ENGINE_AUTO = 0, PLAM_ENGINE_GRAPH = 1, PLAM_ENGINE_RESIDENT = 2 };
 
 typedef struct {
   int variant;          /* PLAM_VARIANT_* used by plam_solve (plam_step/pcal_step choose their own) */
-  int lambda_rule;      /* PLAM_LAMBDA1 / PLAM_LAMBDA2; PCAL default LAMBDA2, PLAM always LAMBDA1 */
+  int lambda_rule;      /* PLAM_LAMBDA1 / PLAM_LAMBDA2 / PLAM_LAMBDA_DA; PCAL default LAMBDA2;
+                           PLAM uses LAMBDA1 unless DA is asked for */
   double beta;          /* penalty parameter beta > = 0 */
   int eta_rule;         /* PLAM_ETA_* */
   double eta0;          /* eta at k = 0; <= 0 selects ||G^0||_F/||X^0||_F + beta */

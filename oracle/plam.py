@@ -169,6 +169,7 @@ def solve(obj, X0, variant="pcal", beta=1.0, lambda_rule="lambda2", eta_rule="ab
     lo, hi = clamp[0] * eta0, clamp[1] * eta0
     hist = []
     X_prev = R_prev = None
+    Lam_prev = None
     eta = eta0
     converged = diverged = False
     k = 0
@@ -189,7 +190,12 @@ def solve(obj, X0, variant="pcal", beta=1.0, lambda_rule="lambda2", eta_rule="ab
             break
         if k >= maxit:
             break
-        if variant == "pcal" and lambda_rule == "lambda2":
+        if lambda_rule == "da":
+            # PLAM-DA / PCAL-DA (Section 5.3): Algorithm 1's dual ascent step,
+            # Lambda^k = Lambda^{k-1} - beta (X^k^T X^k - I), from Lambda^0 = Psi(G^0^T X^0)
+            Lam = L0 if Lam_prev is None else Lam_prev - beta * (B - I)
+            Lam_prev = Lam
+        elif variant == "pcal" and lambda_rule == "lambda2":
             Lam = multiplier_lambda2(G, X, B, beta)
         else:
             Lam = L0

@@ -118,7 +118,7 @@ class Solver:
         self.dtype = storage_dtype(precision)
         prm = plam_default_params()
         prm.variant = PLAM_VARIANT_PCAL if variant == "pcal" else PLAM_VARIANT_PLAM
-        prm.lambda_rule = PLAM_LAMBDA2 if lambda_rule == "lambda2" else PLAM_LAMBDA1
+        prm.lambda_rule = {"lambda1": PLAM_LAMBDA1, "lambda2": PLAM_LAMBDA2, "da": 2}[lambda_rule]
         prm.beta = float(beta)
         prm.eta_rule = _RULES[eta_rule]
         prm.eta0 = float(eta0)

@@ -26,6 +26,8 @@
 //     (since X^T (G - X Lambda0 + beta X (B - I)) = C - B Lambda0 + beta B (B - I)
 //      and B, Lambda0 are symmetric)
 //   M = Lambda0 + Diag(d) - beta (B - I)               eq. (S1): grad_X L_beta = G - X M
+//   or, for PLAM-DA / PCAL-DA (Section 5.3), the dual ascent step of Algorithm 1
+//   Lambda^k = Lambda^{k-1} - beta (B^k - I), Lambda^0 = Psi(C^0), M = Lambda^k - beta (B - I)
 //   feas_row_i = sum_j (B_ij - delta_ij)^2
 // M is symmetric, so column i of M is row i.
 #include "plam_device.cuh"
@@ -234,9 +236,17 @@ gram_finalize_kernel(int p, const double* __restrict__ red, double* __restrict__
   const double sf = block_sum(tf, scratch);
   const double beta = prm.beta;
   const double d = prm.lambda2 ? (cii - s1 + beta * (s2 - Brow[i])) : 0.0;
+  const bool da = prm.lambda_da && prm.lam != nullptr;
+  const bool da_first = da && (st == nullptr || st->k == 0);
   for (int j = threadIdx.x; j < p; j += blockDim.x) {
     const double delta = (j == i) ? 1.0 : 0.0;
-    const double m = Lrow[j] + delta * d - beta * (Brow[j] - delta);
+    double lam = Lrow[j] + delta * d;
+    if (da) {   // dual ascent (Algorithm 1's multiplier step) from Lambda^0 = Psi(C^0)
+      double* lp = prm.lam + j + (size_t)i * p;
+      lam = da_first ? Lrow[j] : *lp - beta * (Brow[j] - delta);
+      *lp = lam;
+    }
+    const double m = lam - beta * (Brow[j] - delta);
     Mt[j + (size_t)i * p] = (T)m;
     L0t[j + (size_t)i * p] = (T)Lrow[j];
     if (Bout) Bout[j + (size_t)i * p] = Brow[j];

@@ -132,6 +132,8 @@ struct plam_handle_s {
   float* msplit = nullptr;
   // KKT residual after the final orthonormalisation: per-CTA partial sums
   double* kkt_part = nullptr;
+  // dual-ascent multiplier (PLAM_LAMBDA_DA), p x p FP64
+  double* lam = nullptr;
 };
 
 namespace {
@@ -166,7 +168,7 @@ __global__ void dot_partial_kernel(int64_t n, int p, const T* __restrict__ X, in
 plam_status_t validate_params(const plam_params_t* prm) {
   if (!prm) return PLAM_ERR_INVALID;
   if (prm->variant != PLAM_VARIANT_PLAM && prm->variant != PLAM_VARIANT_PCAL) return PLAM_ERR_INVALID;
-  if (prm->lambda_rule != PLAM_LAMBDA1 && prm->lambda_rule != PLAM_LAMBDA2) return PLAM_ERR_INVALID;
+  if (prm->lambda_rule < PLAM_LAMBDA1 || prm->lambda_rule > PLAM_LAMBDA_DA) return PLAM_ERR_INVALID;
   if (prm->eta_rule < PLAM_ETA_ABB || prm->eta_rule > PLAM_ETA_DIFF) return PLAM_ERR_INVALID;
   if (prm->precision != PLAM_PREC_FP64 && prm->precision != PLAM_PREC_FP32) return PLAM_ERR_INVALID;
   if (!(prm->beta >= 0.0) || !std::isfinite(prm->beta)) return PLAM_ERR_INVALID;
@@ -207,6 +209,8 @@ IterParams iter_params(const plam_handle_s* h, int variant, int lambda2) {
   ip.tol = h->prm.tol;
   ip.hartree_alpha = (h->obj.kind == PLAM_OBJ_HARTREE1D) ? h->obj.alpha : 0.0;
   f_coefficients(h, &ip.f_xg, &ip.f_part);
+  ip.lambda_da = h->prm.lambda_rule == PLAM_LAMBDA_DA;
+  ip.lam = h->lam;
   return ip;
 }
 
@@ -359,7 +363,7 @@ void free_handle(plam_handle_s* h) {
                  h->hist,
                  h->rho, h->blk, h->y, h->fpart, h->W, h->Z, h->info, h->feas_dev, h->Qtmp,
                  h->dotpart, h->r_halo, h->r_blk, h->r_part, h->r_red, h->r_dots, h->r_dred,
-                 h->r_bar, h->r_err, h->tc_err, h->msplit, h->kkt_part};
+                 h->r_bar, h->r_err, h->tc_err, h->msplit, h->kkt_part, h->lam};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (h->st_host) cudaFreeHost(h->st_host);
@@ -717,12 +721,14 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
          alloc((void**)&h->blk, 2 * (size_t)h->nfpart * sizeof(double)) &&
          alloc((void**)&h->fpart, (size_t)h->nfpart * sizeof(double));
   }
+  if (ok && prm->lambda_rule == PLAM_LAMBDA_DA) ok = alloc((void**)&h->lam, pp * sizeof(double));
   if (ok && obj->kind == PLAM_OBJ_CALLBACK) {
     h->nfpart = 1;
     ok = alloc((void**)&h->fpart, sizeof(double));
   }
   if (ok && prm->final_orth == 2) ok = alloc((void**)&h->Qtmp, (size_t)h->ldw * p * sizeof(double));
   if (ok && prm->engine != PLAM_ENGINE_GRAPH && prm->precision == PLAM_PREC_FP32 &&
+      prm->lambda_rule != PLAM_LAMBDA_DA &&
       (obj->kind == PLAM_OBJ_HARTREE1D || obj->kind == PLAM_OBJ_DENSE)) {
     int dev = 0, sms = 0, optin = 0, coop = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
@@ -1098,8 +1104,8 @@ plam_status_t plam_batch_create(plam_batch_t* out, const plam_batch_problem_t* p
   if (!out) return PLAM_ERR_INVALID;
   *out = nullptr;
   if (!probs || count < 1 || !prm || validate_params(prm) != PLAM_OK) return PLAM_ERR_INVALID;
-  if (prm->precision != PLAM_PREC_FP32) {
-    snprintf(g_err, sizeof(g_err), "plam_batch_create: FP32 mode only");
+  if (prm->precision != PLAM_PREC_FP32 || prm->lambda_rule == PLAM_LAMBDA_DA) {
+    snprintf(g_err, sizeof(g_err), "plam_batch_create: FP32 mode with a closed-form multiplier only");
     return PLAM_ERR_UNSUPPORTED;
   }
   size_t work = 0;

@@ -53,6 +53,8 @@ struct IterParams {
   double tol;
   double hartree_alpha;  // f correction term for the Hartree objective (0 otherwise)
   double f_xg, f_part;   // f = f_xg <X, G> + f_part (sum of the objective's f partials)
+  int lambda_da;         // 1: dual ascent Lambda^k = Lambda^{k-1} - beta (B^k - I) (PLAM-DA, PCAL-DA)
+  double* lam;           // p x p FP64 multiplier carried across iterations (dual ascent only)
 };
 
 // Number of per-column dot products written by the update kernel and the

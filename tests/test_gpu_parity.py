@@ -568,3 +568,24 @@ def test_resident_barrier_timeout_is_reported(monkeypatch):
     assert st in (0, 2) and info.iters > 0
     torch.cuda.synchronize()
     s.close()
+
+
+@pytest.mark.parametrize("variant", ["plam", "pcal"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_dual_ascent_iterations_match_oracle(variant, precision):
+    """PLAM-DA / PCAL-DA (Section 5.3): twenty iterations with the dual ascent multiplier carried
+    on the device, against the oracle from the same start (dense trace problem)."""
+    w = workload_dense_trace(300, 6)
+    obj = oo.TraceObjective(w.A if precision == "fp64" else w.A.astype(np.float32).astype(np.float64))
+    X0 = w.X0 if precision == "fp64" else w.X0.astype(np.float32).astype(np.float64)
+    ref = op.solve(obj, X0, variant=variant, beta=1.5, lambda_rule="da", tol=0.0, maxit=20)
+    s = gpu_solver(w, precision, variant=variant, lambda_rule="da", beta=1.5, tol=0.0, maxit=20,
+                   final_orth=0, engine="graph")
+    Xd = to_dev(X0, s)
+    st, info = s.solve(Xd)
+    hist = s.history()
+    tol = 1e-9 if precision == "fp64" else 2e-4
+    np.testing.assert_allclose(hist[:20, 4], [h.eta for h in ref.history[:20]], rtol=tol)
+    np.testing.assert_allclose(hist[:, 2], [h.kkt for h in ref.history], rtol=tol)
+    assert rel_err(to_host(Xd, w.n), ref.X) <= tol
+    s.close()
