@@ -216,7 +216,7 @@ def make_solver(wl, precision, torch, engine="auto", final_orth=1, maxit=3000):
     from paper_1810_03930_gb300 import Solver
     kw = dict(variant="pcal", lambda_rule="lambda2", beta=wl["beta"], tol=wl["tol"], maxit=maxit,
               precision=precision, final_orth=final_orth, graph_iters=16, engine=engine,
-              tensor_cores=wl.get("tensor_cores", "auto"))
+              tensor_cores=wl.get("tensor_cores", "auto"), orth_metrics=False)
     if wl["kind"] == "stencil3d":
         m = wl["m"]
         return Solver(wl["n"], wl["p"], "stencil3d", grid=(m, m, m), V=wl["V"], **kw)
@@ -364,9 +364,8 @@ def run_ours(args, rank, world, local):
         fp64 = {"time_to_kkt_s": statistics.mean(ms64) / 1e3,
                 "iters_per_solve": statistics.mean(its64),
                 "iters_per_s": sum(its64) / (sum(ms64) / 1e3)}
-    # ---- which engine ran the metric: the resident engine is one launch per solve
-    launches_per_solve = launches / max(1, args.steps)
-    engine = "resident" if launches_per_solve <= 12 else "graph"
+    # ---- which engine ran the metric
+    engine = sol.engine()
     peak_hbm, peak_kind = measured_peaks()
     clock_mhz = clocks.get("sm_mhz") or 2070.0
     n, p = wl["n"], wl["p"]
@@ -492,8 +491,27 @@ def run_reference(args, rank, world):
 
 
 def run_kernel_iters(args):
-    """Per-kernel-group milliseconds of the first --kernel-iters iterations (mixed path)."""
+    """Per-kernel-group milliseconds of the first --kernel-iters iterations (mixed path); for the
+    batched workload, one launch capped at --kernel-iters iterations per problem."""
     import torch
+    if WORKLOADS[args.workload]["kind"] == "batched":
+        from paper_1810_03930_gb300 import BatchSolver
+        from workloads import batched_shapes, workload_batched_problem
+        wl = WORKLOADS["batched"]
+        shapes = batched_shapes(count=wl["count"], n_lo=wl["n_lo"], n_hi=wl["n_hi"])
+        ws = [workload_batched_problem(i, n, p) for i, (n, p) in enumerate(shapes)]
+        bs = BatchSolver([w.A for w in ws], [w.X0 for w in ws], beta=wl["beta"], tol=0.0,
+                         maxit=args.kernel_iters)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        infos = bs.solve()
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"workload": wl["name"], "iterations_per_problem": args.kernel_iters,
+                          "launch_ms": e0.elapsed_time(e1),
+                          "iterations": sum(i.iters for i in infos)}), flush=True)
+        bs.close()
+        return
     wl = dict(WORKLOADS[args.workload], tensor_cores=args.tensor_cores)
     w = load_inputs(wl)
     from paper_1810_03930_gb300 import colmajor_to_device

@@ -124,6 +124,8 @@ typedef struct {
                            (= 1 when p >= 128).  Needs 16-byte aligned X and G with leading dimensions
                            that are multiples of 4, otherwise the CUDA-core Grams run */
   double refine_switch; /* relative KKT value below which the tensor-core Grams are compensated */
+  int orth_metrics;     /* 1 (default): plam_solve also evaluates f and the relative KKT value of the
+                           orthonormalised output (plam_info_t.f_orth, kkt_orth); 0: skipped */
 } plam_params_t;
 
 typedef struct {
@@ -171,6 +173,10 @@ plam_status_t plam_default_params(plam_params_t* prm);
  * Errors: PLAM_ERR_INVALID, PLAM_ERR_NOMEM, PLAM_ERR_CUDA; *h is NULL then. */
 plam_status_t plam_create(plam_handle_t* h, int64_t n, int64_t p, const plam_objective_t* obj,
                           const plam_params_t* prm, void* stream);
+
+/* The engine plam_solve runs on this handle: PLAM_ENGINE_RESIDENT or
+ * PLAM_ENGINE_GRAPH (graph_iters > 0), or 0 for direct launches. */
+int plam_solve_engine(plam_handle_t h);
 
 /* Releases every resource of the handle (synchronises its stream first). */
 plam_status_t plam_destroy(plam_handle_t h);

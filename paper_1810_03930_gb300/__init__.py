@@ -111,7 +111,7 @@ class Solver:
                  variant="pcal", lambda_rule="lambda2", beta=1.0, eta_rule="abb", eta0=0.0,
                  eta_gamma=0.0, tol=1e-8, maxit=3000, precision="fp64", final_orth=1,
                  graph_iters=16, engine="auto", tensor_cores="auto", refine_switch=1e-3,
-                 energy=None, stream=None):
+                 energy=None, orth_metrics=True, stream=None):
         torch = _torch()
         self.n, self.p = int(n), int(p)
         self.precision = precision
@@ -131,6 +131,7 @@ class Solver:
         prm.engine = {"auto": 0, "graph": 1, "resident": 2}[engine]
         prm.tensor_cores = {"auto": -1, "off": 0, "on": 1, "tf32": 1, "3xtf32": 2}[tensor_cores]
         prm.refine_switch = float(refine_switch)
+        prm.orth_metrics = 1 if orth_metrics else 0
         self.params = prm
         obj = _lib.plam_objective_t()
         self._keep = []
@@ -252,6 +253,11 @@ class Solver:
 
     def reset(self):
         plam_reset(self.h)
+
+    def engine(self):
+        """'resident', 'graph' or 'direct': what solve() runs on this handle."""
+        e = _lib.load().plam_solve_engine(self.h)
+        return {2: "resident", 1: "graph"}.get(e, "direct")
 
     def kernel_launches(self):
         return plam_kernel_launches(self.h)

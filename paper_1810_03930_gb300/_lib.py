@@ -39,7 +39,7 @@ class plam_params_t(C.Structure):
                 ("eta_rule", C.c_int), ("eta0", C.c_double), ("eta_gamma", C.c_double),
                 ("tol", C.c_double), ("maxit", C.c_int), ("precision", C.c_int),
                 ("final_orth", C.c_int), ("graph_iters", C.c_int), ("engine", C.c_int),
-                ("tensor_cores", C.c_int), ("refine_switch", C.c_double)]
+                ("tensor_cores", C.c_int), ("refine_switch", C.c_double), ("orth_metrics", C.c_int)]
 
 
 # int grad(void* ctx, const void* X, int64_t ldx, void* G, int64_t ldg, double* f, void* stream)
@@ -93,6 +93,7 @@ SIGNATURES = {
                                     C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "plam_history": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]),
     "plam_kernel_launches": (C.c_int64, [C.c_void_p]),
+    "plam_solve_engine": (C.c_int, [C.c_void_p]),
     "plam_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(plam_batch_problem_t), C.c_int,
                                     C.POINTER(plam_params_t), C.c_void_p]),
     "plam_batch_solve": (C.c_int, [C.c_void_p, C.POINTER(plam_info_t)]),

@@ -49,10 +49,11 @@ __host__ __device__ inline size_t batch_stage_floats(int rb) { return (size_t)kB
 // ---------------------------------------------------------------- step 1: G = A X
 // The sum over n runs in float within each 32-deep stage and is carried across
 // stages in a compensated (Kahan) pair, so that the FP32 rounding of G grows
-// with the stage depth, not with n.  Lane tx owns RB/32 consecutive rows
-// (vector loads from shared memory), warp ty the columns 4ty .. 4ty + 3 (a
-// broadcast float4); the next stage is fetched into registers while the
-// current one is multiplied (two shared-memory buffers, one barrier a stage).
+// with the stage depth, not with n.  Lane tx owns RB/32 rows in groups of four
+// consecutive ones (conflict-free float4 loads from shared memory; pairs for
+// RB = 64), warp ty the columns 4ty .. 4ty + 3 (a broadcast float4); the next
+// stage is fetched into registers while the current one is multiplied (two
+// shared-memory buffers, one barrier a stage).
 template <int RB>
 __device__ void batch_ax(const BatchDesc& q, float* st0, float* st1) {
   constexpr int R4 = RB / 32;
@@ -109,11 +110,19 @@ __device__ void batch_ax(const BatchDesc& q, float* st0, float* st1) {
 #pragma unroll 4
         for (int kk = 0; kk < kBK; ++kk) {
           float a[R4];
+          if (R4 == 2) {
+            const float2 a2 = *reinterpret_cast<const float2*>(st + kk * RB + tx * 2);
+            a[0] = a2.x;
+            a[1] = a2.y;
+          } else {
 #pragma unroll
-          for (int i4 = 0; i4 < R4; i4 += 2) {
-            const float2 a2 = *reinterpret_cast<const float2*>(st + kk * RB + tx * R4 + i4);
-            a[i4] = a2.x;
-            a[i4 + 1] = a2.y;
+            for (int h = 0; h < R4 / 4; ++h) {   // conflict-free float4 rows 128 h + 4 tx .. + 3
+              const float4 a4 = *reinterpret_cast<const float4*>(st + kk * RB + h * 128 + tx * 4);
+              a[4 * h] = a4.x;
+              a[4 * h + 1] = a4.y;
+              a[4 * h + 2] = a4.z;
+              a[4 * h + 3] = a4.w;
+            }
           }
           const float4 b = *reinterpret_cast<const float4*>(st + kBK * RB + kk * kBMaxP + 4 * ty);
 #pragma unroll
@@ -141,7 +150,7 @@ __device__ void batch_ax(const BatchDesc& q, float* st0, float* st1) {
     if (active) {
 #pragma unroll
       for (int i = 0; i < R4; ++i) {
-        const int64_t r = r0 + tx * R4 + i;
+        const int64_t r = r0 + (R4 == 2 ? tx * 2 + i : (i / 4) * 128 + tx * 4 + (i % 4));
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const int c = 4 * ty + v;
@@ -453,15 +462,44 @@ __device__ void batch_solve_one(const BatchDesc& q, const BatchParams& prm, plam
         q.Q[r + (int64_t)c * q.ldq] = s;
       }
       __syncthreads();
-      double fe = 0.0;
-      for (int e = t; e < p * p; e += kBThreads) {
-        const int i = e % p, j = e / p;
-        double s = 0.0;
-        for (int64_t r = 0; r < n; ++r) s = fma(q.Q[r + (int64_t)i * q.ldq], q.Q[r + (int64_t)j * q.ldq], s);
-        s -= (i == j) ? 1.0 : 0.0;
-        fe += s * s;
+      // ||Q^T Q - I||_F: Q^T Q over 32-row stages of Q staged in shared memory (the stage
+      // buffers), thread (ti, tj) owning entries i = ti + 16a, j = tj + 32b
+      {
+        double* qs = reinterpret_cast<double*>(stA);      // [32][64] doubles
+        const int ti = t & 15, tj = t >> 4;
+        double acc[4][2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = 0.0;
+        for (int64_t r0 = 0; r0 < n; r0 += kBK) {
+          for (int e = t; e < kBK * kBMaxP; e += kBThreads) {
+            const int rr = e % kBK, c = e / kBK;
+            const int64_t r = r0 + rr;
+            qs[rr * kBMaxP + c] = (r < n && c < p) ? q.Q[r + (int64_t)c * q.ldq] : 0.0;
+          }
+          __syncthreads();
+          for (int rr = 0; rr < kBK; ++rr) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+              const double qi = qs[rr * kBMaxP + ti + 16 * a];
+              acc[a][0] = fma(qi, qs[rr * kBMaxP + tj], acc[a][0]);
+              acc[a][1] = fma(qi, qs[rr * kBMaxP + tj + 32], acc[a][1]);
+            }
+          }
+          __syncthreads();
+        }
+        double fe = 0.0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b2 = 0; b2 < 2; ++b2) {
+            const int i = ti + 16 * a, j = tj + 32 * b2;
+            if (i < p && j < p) {
+              const double e2 = acc[a][b2] - (i == j ? 1.0 : 0.0);
+              fe += e2 * e2;
+            }
+          }
+        feas_orth = sqrt(block_sum(fe, S.scratch));
       }
-      feas_orth = sqrt(block_sum(fe, S.scratch));
     }
   }
   if (t == 0) {

@@ -628,6 +628,7 @@ plam_status_t plam_default_params(plam_params_t* prm) {
   prm->engine = PLAM_ENGINE_AUTO;
   prm->tensor_cores = -1;
   prm->refine_switch = 1e-3;
+  prm->orth_metrics = 1;
   return PLAM_OK;
 }
 
@@ -925,7 +926,8 @@ plam_status_t plam_solve(plam_handle_t h, void* X, int64_t ldx, double* Xout, in
     if (st != PLAM_OK) return st;
     inf->feas_orth = feas;
     // Table "orth step": f and KKT of the orthonormalised output
-    if (h->prec == PLAM_PREC_FP64) {
+    if (!h->prm.orth_metrics) {
+    } else if (h->prec == PLAM_PREC_FP64) {
       st = post_orth_metrics<double>(h, Xout, ldo, &inf->f_orth, &inf->kkt_orth);
     } else {
       float* Qf = (float*)h->R[0];
@@ -940,6 +942,13 @@ plam_status_t plam_solve(plam_handle_t h, void* X, int64_t ldx, double* Xout, in
     if (st != PLAM_OK) return st;
   }
   return stop == kConverged ? PLAM_OK : PLAM_ERR_NOT_CONVERGED;
+}
+
+int plam_solve_engine(plam_handle_t h) {
+  if (!h) return -1;
+  if (h->r_nblk > 0) return PLAM_ENGINE_RESIDENT;
+  const int gi = h->obj.kind == PLAM_OBJ_CALLBACK ? 0 : h->prm.graph_iters;
+  return gi > 0 ? PLAM_ENGINE_GRAPH : 0;
 }
 
 plam_status_t plam_energy(plam_handle_t h, const void* X, int64_t ldx, double* f_dev) {
