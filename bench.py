@@ -180,24 +180,38 @@ def kernel_bytes(wl, w, nchunks_unused=None):
             "primal_update": 3 * npw}
 
 
-def csrc_hash():
+KERNEL_SOURCES = {
+    "resident": ["k_resident.cu"], "tc_update": ["k_tc_update.cu", "tc_ptx.cuh"],
+    "tc_gram": ["k_tc_gram.cu", "tc_ptx.cuh"], "stencil_grad": ["k_objective.cu"],
+    "hartree_grad": ["k_objective.cu"], "dense_grad": ["k_objective.cu"],
+    "update": ["k_update.cu"], "primal_update": ["k_update.cu"], "step_size": ["k_update.cu"],
+    "gram_partial": ["k_gram.cu"], "gram_finalize": ["k_gram.cu"],
+    "batched_solve": ["k_batched.cu"],
+}
+
+
+def csrc_hash(kernel=None):
+    """sha256 (16 hex digits) of a kernel's sources plus the shared headers (all of csrc/
+    when kernel is None)."""
     h = hashlib.sha256()
     cdir = os.path.join(ROOT, "paper_1810_03930_gb300", "csrc")
-    for fn in sorted(os.listdir(cdir)):
+    names = sorted(os.listdir(cdir)) if kernel is None else sorted(
+        KERNEL_SOURCES.get(kernel, []) + ["plam_common.cuh", "plam_device.cuh"])
+    for fn in names:
         h.update(open(os.path.join(cdir, fn), "rb").read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel, workload):
     """dram bytes per launch recorded by an ncu capture summarised under profiles/, if the
-    kernels have not changed since (the summary carries the source hash)."""
+    kernel's sources have not changed since (the summary carries their hash)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    hsh = re.search(r"csrc_sha256_16:\s*([0-9a-f]+)", text)
-    if not m or not hsh or hsh.group(1) != csrc_hash():
+    hsh = re.search(r"kernel_sources_sha256_16:\s*([0-9a-f]+)", text)
+    if not m or not hsh or hsh.group(1) != csrc_hash(kernel):
         return None
     return float(m.group(1))
 
