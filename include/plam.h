@@ -75,7 +75,8 @@ enum { PLAM_ETA_ABB = 0, PLAM_ETA_BB1 = 1, PLAM_ETA_BB2 = 2, PLAM_ETA_CONST = 3,
 enum { PLAM_PREC_FP64 = 0, PLAM_PREC_FP32 = 1 };
 /* Built-in objectives (Section 5.2):
  *   DENSE      f = 1/2 tr(X^T A X), A symmetric n x n              (Problem 3)
- *   HARTREE1D  f = q tr(X^T L X) + (alpha/4) rho^T L^{-1} rho,     (Problem 1, KS form eq. KS-energy)
+ *   HARTREE1D  f = q tr(X^T L X) + (alpha/4) rho^T L^{-1} rho     (Problem 1, KS form eq. KS-energy;
+ *                  - (3 xc / 4) sum rho^{4/3}                      with xc: Problem 6's exchange)
  *              rho = diag(X X^T), L = tridiag(-1,2,-1) Dirichlet
  *   STENCIL3D  f = 1/2 tr(X^T (L3 + Diag(V)) X), L3 the 7-point Dirichlet
  *              Laplacian on nx*ny*nz points, index i = x + nx*(y + ny*z);
@@ -138,6 +139,8 @@ typedef struct {
   const void* V;        /* STENCIL3D: device n-vector potential, storage type (may be NULL: V = 0) */
   plam_grad_fn grad;    /* CALLBACK: the user gradient (required) */
   void* grad_ctx;       /* CALLBACK: passed to grad unchanged */
+  double xc;            /* HARTREE1D: exchange coefficient gamma of Problem 6, adding
+                           -(3 gamma / 4) sum_i rho_i^{4/3} (0: none; the resident engine needs 0) */
 } plam_objective_t;
 
 typedef struct {

@@ -4,7 +4,8 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 
   TraceObjective     Problem 3 (Section 5.2, eq. RR): f = 1/2 tr(X^T A X), grad = A X.
   HartreeObjective   Problem 1 / Kohn-Sham form (Section 1.1 eq. KS-energy,
-                     Section 5.2 eq. nonlinear):
+                     Section 5.2 eq. nonlinear), optionally with Problem 6's
+                     exchange term -(3 gamma/4) sum rho^{4/3}:
                          f = q tr(X^T L X) + (alpha/4) rho^T L^{-1} rho,
                          rho = diag(X X^T),
                      L = tridiag(-1, 2, -1) with Dirichlet ends.  q = 1/4 follows
@@ -82,12 +83,16 @@ def laplacian_1d_apply(X: np.ndarray) -> np.ndarray:
 
 
 class HartreeObjective:
-    """f = q tr(X^T L X) + (alpha/4) rho^T L^{-1} rho with rho = diag(X X^T)."""
+    """f = q tr(X^T L X) + (alpha/4) rho^T L^{-1} rho - (3 xc/4) sum_i rho_i^{4/3}, rho = diag(X X^T).
 
-    def __init__(self, n: int, alpha: float = 1.0, quad_scale: float = 0.25):
+    The last term is Problem 6's exchange energy (Section 5.2, gamma = xc); its gradient
+    follows from d rho_i / d X_ij = 2 X_ij: -(3 xc/4)(4/3) rho_i^{1/3} 2 X_ij = -2 xc rho_i^{1/3} X_ij."""
+
+    def __init__(self, n: int, alpha: float = 1.0, quad_scale: float = 0.25, xc: float = 0.0):
         self.n = int(n)
         self.alpha = float(alpha)
         self.q = float(quad_scale)
+        self.xc = float(xc)
         self._ab = laplacian_1d_banded(self.n)
 
     def density(self, X):
@@ -100,12 +105,14 @@ class HartreeObjective:
     def value(self, X):
         rho = self.density(X)
         y = self.hartree_potential(rho)
-        return self.q * float(np.sum(X * laplacian_1d_apply(X))) + 0.25 * self.alpha * float(rho @ y)
+        return (self.q * float(np.sum(X * laplacian_1d_apply(X))) + 0.25 * self.alpha * float(rho @ y)
+                - 0.75 * self.xc * float(np.sum(np.cbrt(rho) * rho)))
 
     def grad(self, X):
         rho = self.density(X)
         y = self.hartree_potential(rho)
-        return 2.0 * self.q * laplacian_1d_apply(X) + self.alpha * (y[:, None] * X)
+        return (2.0 * self.q * laplacian_1d_apply(X) + self.alpha * (y[:, None] * X)
+                - 2.0 * self.xc * (np.cbrt(rho)[:, None] * X))
 
     def hess_norm_bound(self):
         """Upper bound of ||grad^2 f(0)||_2 = 2 q ||L||_2 <= 8 q (the Hartree part vanishes at 0)."""
@@ -167,7 +174,7 @@ def objective_for(w) -> object:
     if w.kind == "dense":
         return TraceObjective(w.A)
     if w.kind == "hartree1d":
-        return HartreeObjective(w.n, w.alpha, w.quad_scale)
+        return HartreeObjective(w.n, w.alpha, w.quad_scale, getattr(w, "xc", 0.0) or 0.0)
     if w.kind == "stencil3d":
         return Stencil3DObjective(w.m, w.V)
     raise ValueError(w.kind)

@@ -107,7 +107,7 @@ class Solver:
     n x p matrix (ld = leading dimension >= n).
     """
 
-    def __init__(self, n, p, kind, *, A=None, alpha=1.0, quad_scale=0.25, grid=None, V=None,
+    def __init__(self, n, p, kind, *, A=None, alpha=1.0, quad_scale=0.25, xc=0.0, grid=None, V=None,
                  variant="pcal", lambda_rule="lambda2", beta=1.0, eta_rule="abb", eta0=0.0,
                  eta_gamma=0.0, tol=1e-8, maxit=3000, precision="fp64", final_orth=1,
                  graph_iters=16, engine="auto", tensor_cores="auto", refine_switch=1e-3,
@@ -141,6 +141,7 @@ class Solver:
             obj.kind, obj.A, obj.lda = PLAM_OBJ_DENSE, At.data_ptr(), At.stride(0)
         elif kind == "hartree1d":
             obj.kind, obj.alpha, obj.quad_scale = PLAM_OBJ_HARTREE1D, float(alpha), float(quad_scale)
+            obj.xc = float(xc)
         elif kind == "stencil3d":
             nx, ny, nz = grid
             obj.kind, obj.nx, obj.ny, obj.nz = PLAM_OBJ_STENCIL3D, nx, ny, nz

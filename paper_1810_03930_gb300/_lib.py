@@ -50,7 +50,8 @@ plam_grad_fn = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_
 class plam_objective_t(C.Structure):
     _fields_ = [("kind", C.c_int), ("A", C.c_void_p), ("lda", C.c_int64), ("alpha", C.c_double),
                 ("quad_scale", C.c_double), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
-                ("V", C.c_void_p), ("grad", plam_grad_fn), ("grad_ctx", C.c_void_p)]
+                ("V", C.c_void_p), ("grad", plam_grad_fn), ("grad_ctx", C.c_void_p),
+                ("xc", C.c_double)]
 
 
 class plam_batch_problem_t(C.Structure):

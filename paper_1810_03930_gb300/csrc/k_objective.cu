@@ -3,7 +3,8 @@
 //
 // dense_grad_kernel     G = A X for f = 1/2 tr(X^T A X) (Problem 3), a tiled
 //                       64 x 64 GEMM over shared-memory stages of A and X.
-// hartree kernels       f = q tr(X^T L X) + (alpha/4) rho^T L^{-1} rho
+// hartree kernels       f = q tr(X^T L X) + (alpha/4) rho^T L^{-1} rho - (3 xc / 4) sum rho^{4/3}
+//                       (the last term: Problem 6's exchange, 0 unless xc is set)
 //                       (eq. KS-energy, Problem 1 with L = tridiag(-1,2,-1)),
 //                       G = 2 q L X + alpha Diag(y) X with y = L^{-1} rho.
 //   The Dirichlet Laplacian has the closed-form inverse (1-based indices)
@@ -125,8 +126,8 @@ hartree_density_kernel(int64_t n, int p, const T* __restrict__ X, int64_t ldx,
 
 template <typename T>
 __global__ void __launch_bounds__(kHB)
-hartree_grad_kernel(int64_t n, int p, double alpha, double q, double inv_np1, const T* __restrict__ X,
-                    int64_t ldx,
+hartree_grad_kernel(int64_t n, int p, double alpha, double q, double xc, double inv_np1,
+                    const T* __restrict__ X, int64_t ldx,
                     T* __restrict__ G, int64_t ldg, const double* __restrict__ rho,
                     const double* __restrict__ blk, double* __restrict__ yout,
                     double* __restrict__ fpart, const DevState* __restrict__ st) {
@@ -169,11 +170,14 @@ hartree_grad_kernel(int64_t n, int p, double alpha, double q, double inv_np1, co
   const double P = Pbefore + incl_a;
   const double Q = Qafter + (ctot - incl_c);   // strictly after i
   const double y = ((double)(n - r) * P + i1 * Q) * inv_np1;   // 1/(n+1) from the host
-  const double fy = block_sum((r < n) ? rv * y : 0.0, scratch);
+  // f partial of this block: f = 1/2 <X, G> - (alpha/4) rho^T y + (xc/4) sum rho^{4/3}
+  const double c3 = (xc != 0.0 && r < n) ? cbrt(rv) : 0.0;
+  const double fy = block_sum((r < n) ? -0.25 * alpha * rv * y + 0.25 * xc * rv * c3 : 0.0, scratch);
   if (threadIdx.x == 0 && fpart) fpart[b] = fy;
   if (r >= n) return;
   if (yout) yout[r] = y;
-  const T ty = (T)(alpha * y);
+  // row scale: alpha L^{-1} rho (Hartree) - 2 xc rho^{1/3} (exchange, Problem 6)
+  const T ty = (T)(alpha * y - 2.0 * xc * c3);
   const T q2 = (T)(2.0 * q);
   for (int cc = 0; cc < p; ++cc) {
     const T* xc = X + (int64_t)cc * ldx;
@@ -252,15 +256,15 @@ cudaError_t launch_dense_grad(int64_t n, int p, const T* A, int64_t lda, const T
 }
 
 template <typename T>
-cudaError_t launch_hartree_grad(int64_t n, int p, double alpha, double q, const T* X, int64_t ldx,
-                                T* G, int64_t ldg, double* rho, double* blk, double* y,
+cudaError_t launch_hartree_grad(int64_t n, int p, double alpha, double q, double xc, const T* X,
+                                int64_t ldx, T* G, int64_t ldg, double* rho, double* blk, double* y,
                                 double* fpart, const DevState* st, cudaStream_t s) {
   const int nb = hartree_blocks(n);
   hartree_density_kernel<T><<<nb, kHB, 0, s>>>(n, p, X, ldx, rho, blk, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  hartree_grad_kernel<T><<<nb, kHB, 0, s>>>(n, p, alpha, q, 1.0 / (double)(n + 1), X, ldx, G, ldg,
-                                             rho, blk, y, fpart, st);
+  hartree_grad_kernel<T><<<nb, kHB, 0, s>>>(n, p, alpha, q, xc, 1.0 / (double)(n + 1), X, ldx, G,
+                                             ldg, rho, blk, y, fpart, st);
   return cudaGetLastError();
 }
 
@@ -292,7 +296,7 @@ cudaError_t preload_objective_kernels() {
 #define PLAM_INST(T)                                                                              \
   template cudaError_t launch_dense_grad<T>(int64_t, int, const T*, int64_t, const T*, int64_t,   \
                                             T*, int64_t, const DevState*, cudaStream_t);          \
-  template cudaError_t launch_hartree_grad<T>(int64_t, int, double, double, const T*, int64_t,    \
+  template cudaError_t launch_hartree_grad<T>(int64_t, int, double, double, double, const T*, int64_t, \
                                               T*, int64_t, double*, double*, double*, double*,    \
                                               const DevState*, cudaStream_t);                     \
   template cudaError_t launch_stencil_grad<T>(int, int, int, int, const T*, const T*, int64_t, T*, \

@@ -187,7 +187,7 @@ bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 // rho^T L^{-1} rho; a user objective supplies f itself.
 void f_coefficients(const plam_handle_s* h, double* f_xg, double* f_part) {
   switch (h->obj.kind) {
-    case PLAM_OBJ_HARTREE1D: *f_xg = 0.5; *f_part = -0.25 * h->obj.alpha; break;
+    case PLAM_OBJ_HARTREE1D: *f_xg = 0.5; *f_part = 1.0; break;   // partials carry -alpha/4, xc/4
     case PLAM_OBJ_CALLBACK: *f_xg = 0.0; *f_part = 1.0; break;
     default: *f_xg = 0.5; *f_part = 0.0; break;
   }
@@ -224,7 +224,8 @@ int launch_objective(plam_handle_s* h, const T* X, int64_t ldx, T* G, int64_t ld
       *err = launch_dense_grad<T>(h->n, p, (const T*)h->obj.A, h->obj.lda, X, ldx, G, ldg, st, s);
       return 1;
     case PLAM_OBJ_HARTREE1D:
-      *err = launch_hartree_grad<T>(h->n, p, h->obj.alpha, h->obj.quad_scale, X, ldx, G, ldg, h->rho,
+      *err = launch_hartree_grad<T>(h->n, p, h->obj.alpha, h->obj.quad_scale, h->obj.xc, X, ldx, G,
+                                    ldg, h->rho,
                                     h->blk, h->y, h->fpart, st, s);
       return 2;
     case PLAM_OBJ_STENCIL3D:
@@ -644,7 +645,8 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
       if (!obj->A || obj->lda < n || !aligned(obj->A, esz)) return PLAM_ERR_INVALID;
       break;
     case PLAM_OBJ_HARTREE1D:
-      if (!std::isfinite(obj->alpha) || !std::isfinite(obj->quad_scale)) return PLAM_ERR_INVALID;
+      if (!std::isfinite(obj->alpha) || !std::isfinite(obj->quad_scale) || !std::isfinite(obj->xc))
+        return PLAM_ERR_INVALID;
       break;
     case PLAM_OBJ_STENCIL3D:
       if (obj->nx < 1 || obj->ny < 1 || obj->nz < 1 ||
@@ -730,7 +732,7 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
   if (ok && prm->final_orth == 2) ok = alloc((void**)&h->Qtmp, (size_t)h->ldw * p * sizeof(double));
   if (ok && prm->engine != PLAM_ENGINE_GRAPH && prm->precision == PLAM_PREC_FP32 &&
       prm->lambda_rule != PLAM_LAMBDA_DA &&
-      (obj->kind == PLAM_OBJ_HARTREE1D || obj->kind == PLAM_OBJ_DENSE)) {
+      ((obj->kind == PLAM_OBJ_HARTREE1D && obj->xc == 0.0) || obj->kind == PLAM_OBJ_DENSE)) {
     int dev = 0, sms = 0, optin = 0, coop = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
@@ -847,6 +849,7 @@ plam_status_t plam_solve(plam_handle_t h, void* X, int64_t ldx, double* Xout, in
     L.dred = h->r_dred; L.bar = h->r_bar; L.err = h->r_err; L.st = h->st; L.nubuf = h->nubuf;
     L.coef = (float*)h->coef; L.hist = h->hist;
     L.prm = iter_params<float>(h, variant, lambda2);
+    if (h->obj.kind == PLAM_OBJ_HARTREE1D) L.prm.f_part = -0.25 * h->obj.alpha;   // its own rho^T y sum
     // failure-detection test hook: extra expected arrivals that never come, so the
     // bounded barrier wait runs out (no fault; the kernel returns a status)
     const char* extra = getenv("PLAM_TEST_BARRIER_EXTRA");

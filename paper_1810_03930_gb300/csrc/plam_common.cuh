@@ -104,8 +104,8 @@ template <typename T>
 cudaError_t launch_dense_grad(int64_t n, int p, const T* A, int64_t lda, const T* X, int64_t ldx,
                               T* G, int64_t ldg, const DevState* st, cudaStream_t s);
 template <typename T>
-cudaError_t launch_hartree_grad(int64_t n, int p, double alpha, double q, const T* X, int64_t ldx,
-                                T* G, int64_t ldg, double* rho, double* blk, double* y,
+cudaError_t launch_hartree_grad(int64_t n, int p, double alpha, double q, double xc, const T* X,
+                                int64_t ldx, T* G, int64_t ldg, double* rho, double* blk, double* y,
                                 double* fpart, const DevState* st, cudaStream_t s);
 int hartree_blocks(int64_t n);
 template <typename T>

@@ -589,3 +589,35 @@ def test_dual_ascent_iterations_match_oracle(variant, precision):
     np.testing.assert_allclose(hist[:, 2], [h.kkt for h in ref.history], rtol=tol)
     assert rel_err(to_host(Xd, w.n), ref.X) <= tol
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_exchange_energy_and_solve_match_oracle(precision):
+    """Problem 6 (Kohn-Sham with the exchange term, Section 5.2: q = 1/2, alpha = 2,
+    gamma = 2 (3/pi)^{1/3}): gradient and energy kernels, then a PCAL solve, against the oracle."""
+    from workloads import workload_ks_exchange
+    w = workload_ks_exchange(2000, 10)
+    obj = oo.objective_for(w)
+    from paper_1810_03930_gb300 import Solver
+    kw = dict(alpha=w.alpha, quad_scale=w.quad_scale, xc=w.xc, precision=precision)
+    X = w.X0 + 0.01 * rng_for(12, 4).standard_normal(w.X0.shape)
+    if precision == "fp32":
+        X = X.astype(np.float32).astype(np.float64)
+    s = Solver(w.n, w.p, "hartree1d", **kw)
+    Gd = s.new_matrix()
+    f = s.energy_grad(to_dev(X, s), Gd)
+    tol = 1e-10 if precision == "fp64" else 2e-6
+    assert rel_err(to_host(Gd, w.n), obj.grad(X)) <= tol
+    assert abs(f - obj.value(X)) <= tol * abs(obj.value(X)) * 10
+    s.close()
+    ref = op.solve(obj, w.X0, variant="pcal", beta=100.0, tol=1e-9, maxit=20000, record=False)
+    stol = 1e-9 if precision == "fp64" else 1e-6
+    s = Solver(w.n, w.p, "hartree1d", variant="pcal", beta=100.0, tol=stol, maxit=20000,
+               final_orth=1, **kw)
+    Qd = s.new_matrix(dtype=torch.float64)
+    st, info = s.solve(to_dev(w.X0, s), Qd)
+    assert st == 0 and info.converged
+    Q = to_host(Qd, w.n)
+    assert abs(obj.value(Q) - ref.f_orth) <= (1e-10 if precision == "fp64" else 1e-6) * abs(ref.f_orth)
+    assert abs(info.f_orth - obj.value(Q)) <= (1e-12 if precision == "fp64" else 1e-6) * abs(ref.f_orth)
+    s.close()

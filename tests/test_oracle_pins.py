@@ -426,3 +426,32 @@ def test_dual_ascent_variants(variant):
         assert r.converged
         ev = np.linalg.eigvalsh(A)
         assert abs(r.f_orth - 0.5 * ev[:p].sum()) <= 1e-9 * abs(0.5 * ev[:p].sum())
+
+
+def test_exchange_term_pins():
+    """Problem 6's exchange term -(3 gamma/4) sum rho^{4/3} (Section 5.2): (i) with gamma = 0 the
+    objective is the Hartree one exactly; (ii) hand value on X = [e_1 .. e_p] placed on distinct
+    rows (rho = their indicator, so sum rho^{4/3} = p); (iii) the gradient -2 gamma rho^{1/3} X
+    against central differences."""
+    n, p = 40, 3
+    gamma = 2.0 * (3.0 / math.pi) ** (1.0 / 3.0)
+    rng = np.random.default_rng(12)
+    X = rng.standard_normal((n, p)) / math.sqrt(n)
+    h0 = oo.HartreeObjective(n, 2.0, 0.5)
+    h1 = oo.HartreeObjective(n, 2.0, 0.5, xc=0.0)
+    assert h1.value(X) == h0.value(X) and np.array_equal(h1.grad(X), h0.grad(X))
+    rows = [3, 17, 30]
+    E = np.zeros((n, p))
+    for c, r in enumerate(rows):
+        E[r, c] = 1.0
+    hx = oo.HartreeObjective(n, 2.0, 0.5, xc=gamma)
+    # L^{-1} by the Dirichlet Green's function min(i,j)(n+1-max(i,j))/(n+1), 1-based
+    ginv = lambda i, j: min(i, j) * (n + 1 - max(i, j)) / (n + 1)
+    rr = [r + 1 for r in rows]
+    hartree = sum(ginv(i, j) for i in rr for j in rr)
+    expect = 0.5 * 2.0 * p + 0.25 * 2.0 * hartree - 0.75 * gamma * p
+    assert abs(hx.value(E) - expect) <= 1e-12 * abs(expect)
+    D = rng.standard_normal((n, p))
+    hstep = 1e-5
+    dd = (hx.value(X + hstep * D) - hx.value(X - hstep * D)) / (2 * hstep)
+    assert abs(dd - np.sum(hx.grad(X) * D)) <= 1e-7 * max(1.0, abs(dd))

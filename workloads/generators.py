@@ -33,6 +33,7 @@ __all__ = [
     "gaussian_start", "uniform_potential", "paper_p3_operator", "paper_p2_linear", "Workload",
     "workload_dense_trace", "workload_hartree1d", "workload_stencil3d",
     "batched_shapes", "workload_batched_problem", "workload_by_config",
+    "workload_ks_exchange",
 ]
 
 
@@ -110,6 +111,7 @@ class Workload:
     m: int = 0                     # grid edge (kind == "stencil3d"), n = m^3
     alpha: float = 1.0             # Hartree coupling (kind == "hartree1d")
     quad_scale: float = 0.25       # coefficient of tr(X^T L X) (kind == "hartree1d")
+    xc: float = 0.0                # exchange coefficient gamma (kind == "hartree1d", Problem 6)
     params: dict = field(default_factory=dict)  # suggested solver parameters
 
 
@@ -131,6 +133,16 @@ def workload_hartree1d(n: int = 20000, p: int = 50, alpha: float = 1.0,
     return Workload(name=f"hartree1d_n{n}_p{p}", kind="hartree1d", n=n, p=p, X0=X0,
                     alpha=alpha, quad_scale=quad_scale,
                     params=dict(variant="pcal", beta=1000.0, tol=1e-6))
+
+
+def workload_ks_exchange(n: int = 2000, p: int = 10, config: int = 6) -> Workload:
+    """Problem 6 shape (Section 5.2): f = 1/2 tr(X^T L X) + 1/2 rho^T L^{-1} rho
+    - (3/4) gamma rho^T rho^{1/3}, gamma = 2 (3/pi)^{1/3}, L = tridiag(-1, 2, -1) Dirichlet
+    (q = 1/2, alpha = 2, xc = gamma), orthonormal Gaussian start."""
+    X0 = orthonormal_start(n, p, rng_for(config, 1))
+    gamma = 2.0 * (3.0 / np.pi) ** (1.0 / 3.0)
+    return Workload(name=f"ks_exchange_n{n}_p{p}", kind="hartree1d", n=n, p=p, X0=X0, alpha=2.0,
+                    quad_scale=0.5, xc=gamma, params=dict(variant="pcal", beta=100.0, tol=1e-8))
 
 
 def workload_stencil3d(m: int = 64, p: int = 256, config: int = 3,
