@@ -608,11 +608,22 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_solve_kernel(Resident
         a.coef[(size_t)(k & 1) * (2 * p + 1)] = (float)ie;
         if (nrec - 1 < prm.hist_cap) a.hist[(size_t)(nrec - 1) * 5 + 4] = e2;
       }
-      // X <- (X - R/eta) / nu  (PLAM: nu = 1)
+      // X <- (X - R/eta) / nu  (PLAM: nu = 1), four rows of one column per
+      // thread and step over all threads (rp is a multiple of 4; the padding
+      // rows of X and R are zero and stay zero)
       const float fie = (float)ie;
-      for (int r = t; r < nr; r += kResThreads)
-        for (int c = 0; c < p; ++c)
-          Xs[c * rp + r] = (Xs[c * rp + r] - gr[c * rp + r] * fie) * (prm.variant == 1 ? inu[c] : 1.f);
+      float4* X4 = reinterpret_cast<float4*>(Xs);
+      const float4* R4 = reinterpret_cast<const float4*>(gr);
+      for (int e4 = t; e4 < p * rp / 4; e4 += kResThreads) {
+        const float sc = prm.variant == 1 ? inu[(4 * e4) / rp] : 1.f;
+        float4 x = X4[e4];
+        const float4 g = R4[e4];
+        x.x = (x.x - g.x * fie) * sc;
+        x.y = (x.y - g.y * fie) * sc;
+        x.z = (x.z - g.z * fie) * sc;
+        x.w = (x.w - g.w * fie) * sc;
+        X4[e4] = x;
+      }
       eta_prev = eta;
       eta = e2;
       inv_etap = fie;

@@ -15,9 +15,10 @@
 // and R^{k-1} is read from the other one, so the same launch sequence serves
 // every iteration (and can be captured once in a CUDA graph).
 //
-// step_size_kernel: reduces the per-tile sums in a fixed order (one warp per
-// sum, lanes striding over tiles, fixed butterfly), and the last CTA to finish
-// (atomic ticket, no waiting) computes the KKT value, the stopping decision,
+// step_size_kernel: reduces the per-tile sums in a fixed order (CTAs over
+// groups of 32 dot slots x ranges of row tiles, coalesced loads, then the
+// ranges in order), and the last CTA to finish (atomic ticket, no waiting)
+// computes the KKT value, the stopping decision,
 // eta (rules of Section 5.1 with the safeguards of the design notes) and, for
 // PCAL, the column norms nu_c = ||X_c - R_c/eta|| from
 //     nu_c^2 = ||X_c||^2 - 2 <X_c,R_c> / eta + ||R_c||^2 / eta^2.
@@ -181,47 +182,85 @@ update_kernel(int64_t n, int p, const T* __restrict__ X, int64_t ldx, const T* _
   }
 }
 
-constexpr int kStepThreads = 512;
+constexpr int kStepThreads = 256;
+constexpr int kStepWarps = kStepThreads / 32;
 
-// Sum of `cnt` partials spaced `stride` apart, by one warp in a fixed order.
+// Phase 1 of the step-size kernel: CTA (g, t) sums, for the 32 dot slots of
+// group g (lane = slot, so every load of a warp is one coalesced 128-byte
+// line), the partials of the t-th range of row tiles.  Warp w takes the rows
+// w, w + 8, ... of the range, eight independent loads in flight per lane,
+// added in row order; the eight warps are then added in warp order.  The
+// last group holds the six whole-tile sums.
 template <typename T>
-__device__ inline double warp_fixed_sum(const T* __restrict__ src, int cnt, size_t stride) {
-  const int l = threadIdx.x & 31;
-  T s = 0;
-  for (int i = l; i < cnt; i += 32) s += __ldcg(src + (size_t)i * stride);
+__device__ inline void step_partial_sums(int nrt, int nct, int p, const T* __restrict__ colpart,
+                                         const T* __restrict__ totpart, T* __restrict__ dsum) {
+  const int ncg = (kColDots * p + 31) / 32;
+  const bool tot = (int)blockIdx.x == ncg;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int rows = tot ? nrt * nct : nrt;
+  const int width = tot ? kTotDots : kColDots * p;
+  const T* src = tot ? totpart : colpart;
+  const int col = tot ? lane : (int)blockIdx.x * 32 + lane;
+  const int per = (rows + (int)gridDim.y - 1) / (int)gridDim.y;
+  const int i0 = (int)blockIdx.y * per;
+  const int i1 = min(rows, i0 + per);
+  T s = T(0);
+  if (col < width) {
+    int i = i0 + w;
+    for (; i + 7 * kStepWarps < i1; i += 8 * kStepWarps) {
+      T v[8];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  return (double)s;
+      for (int u = 0; u < 8; ++u) v[u] = __ldcg(src + (size_t)(i + u * kStepWarps) * width + col);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; i < i1; i += kStepWarps) s += __ldcg(src + (size_t)i * width + col);
+  }
+  __shared__ T red[kStepWarps][32];
+  red[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && col < width) {
+    T t = red[0][lane];
+#pragma unroll
+    for (int u = 1; u < kStepWarps; ++u) t += red[u][lane];
+    dsum[(size_t)blockIdx.y * (kColDots * p + kTotDots) + (tot ? kColDots * p : 0) + col] = t;
+  }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kStepThreads)
 step_size_kernel(int nrt, int nct, const T* __restrict__ colpart, const T* __restrict__ totpart,
-                 const double* __restrict__ feas_row, const double* __restrict__ fpart, int nfpart,
-                 double* __restrict__ sums, unsigned int* __restrict__ ticket, DevState* st,
-                 double* __restrict__ nubuf, T* __restrict__ coef, double* __restrict__ hist,
-                 IterParams prm) {
+                 T* __restrict__ dsum, const double* __restrict__ feas_row,
+                 const double* __restrict__ fpart, int nfpart, double* __restrict__ sums,
+                 unsigned int* __restrict__ ticket, DevState* st, double* __restrict__ nubuf,
+                 T* __restrict__ coef, double* __restrict__ hist, IterParams prm) {
   if (st->stop != kRunning) return;
   const int p = prm.p;
   const int nslots = kColDots * p + kTotDots;
-  const int warps_total = gridDim.x * (blockDim.x >> 5);
-  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  for (int slot = gw; slot < nslots; slot += warps_total) {
-    double v;
-    if (slot < kColDots * p) {
-      v = warp_fixed_sum<T>(colpart + slot, nrt, (size_t)kColDots * p);
-    } else {
-      v = warp_fixed_sum<T>(totpart + (slot - kColDots * p), nrt * nct, (size_t)kTotDots);
-    }
-    if ((threadIdx.x & 31) == 0) sums[slot] = v;
-  }
+  step_partial_sums<T>(nrt, nct, p, colpart, totpart, dsum);
   __shared__ bool last;
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1);
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // the row ranges in order (all loads of a slot issued before the adds), in
+  // the storage type: this CTA runs alone, and GB300 adds doubles at 1/64 of
+  // the float rate, so ~25k double adds here would cost ~10 us
+  const int nranges = (int)gridDim.y;
+  for (int slot = threadIdx.x; slot < nslots; slot += blockDim.x) {
+    T buf[kStepRanges];
+#pragma unroll
+    for (int u = 0; u < kStepRanges; ++u)
+      buf[u] = (u < nranges) ? __ldcg(dsum + (size_t)u * nslots + slot) : T(0);
+    T v = buf[0];
+#pragma unroll
+    for (int u = 1; u < kStepRanges; ++u)
+      if (u < nranges) v += buf[u];
+    sums[slot] = (double)v;
+  }
+  __syncthreads();
 
   __shared__ double scratch[33];
   __shared__ double sc[8];
@@ -391,17 +430,17 @@ cudaError_t launch_update(int64_t n, int p, const T* X, int64_t ldx, const T* G,
 }
 
 template <typename T>
-cudaError_t launch_step_size(int nrt, int nct, const T* colpart, const T* totpart,
+cudaError_t launch_step_size(int nrt, int nct, const T* colpart, const T* totpart, T* dsum,
                              const double* feas_row, const double* fpart, int nfpart, double* sums,
                              unsigned int* ticket, DevState* st, double* nubuf, T* coef,
                              double* hist, IterParams prm, cudaStream_t s) {
-  // one warp per partial sum where possible (16 warps per CTA), at least 8 CTAs
-  const int nslots = kColDots * prm.p + kTotDots;
-  int blocks = (nslots + 15) / 16;
-  blocks = blocks < 8 ? 8 : (blocks > 304 ? 304 : blocks);
-  step_size_kernel<T><<<blocks, kStepThreads, 0, s>>>(nrt, nct, colpart, totpart, feas_row,
-                                                        fpart, nfpart, sums, ticket, st, nubuf,
-                                                        coef, hist, prm);
+  // 32 dot slots per CTA column, about 64 row tiles (8 per warp) per CTA row
+  const int groups = (kColDots * prm.p + 31) / 32 + 1;
+  int ranges = (nrt + 8 * kStepWarps - 1) / (8 * kStepWarps);
+  ranges = ranges < 1 ? 1 : (ranges > kStepRanges ? kStepRanges : ranges);
+  step_size_kernel<T><<<dim3(groups, ranges), kStepThreads, 0, s>>>(
+      nrt, nct, colpart, totpart, dsum, feas_row, fpart, nfpart, sums, ticket, st, nubuf, coef,
+      hist, prm);
   return cudaGetLastError();
 }
 
@@ -440,7 +479,7 @@ cudaError_t preload_update_kernels() {
   template cudaError_t launch_update<T>(int64_t, int, const T*, int64_t, const T*, int64_t, T*,    \
                                         T*, int64_t, const T*, const T*, const T*,                 \
                                         const DevState*, T*, T*, cudaStream_t);                    \
-  template cudaError_t launch_step_size<T>(int, int, const T*, const T*, const double*,            \
+  template cudaError_t launch_step_size<T>(int, int, const T*, const T*, T*, const double*,       \
                                            const double*, int, double*, unsigned int*, DevState*,  \
                                            double*, T*, double*, IterParams, cudaStream_t);        \
   template cudaError_t launch_primal_update<T>(int64_t, int, T*, int64_t, const T*, const T*,      \

@@ -86,6 +86,7 @@ struct plam_handle_s {
   void* totpart = nullptr;
   int nrt = 0, nct = 0;
   double* sums = nullptr;
+  void* dsum = nullptr;     // kStepRanges x (3p + 6) row-range sums of the dots
   unsigned int* ticket = nullptr;
   DevState* st = nullptr;
   double* nubuf = nullptr;
@@ -288,7 +289,8 @@ plam_status_t launch_iteration(plam_handle_s* h, T* X, int64_t ldx, int variant,
                         (T*)h->colpart, (T*)h->totpart, s));
   }
   if (ev) CK(cudaEventRecord(ev[4], s));
-  CK(launch_step_size<T>(nrt, nct, (const T*)h->colpart, (const T*)h->totpart, h->feas_row,
+  CK(launch_step_size<T>(nrt, nct, (const T*)h->colpart, (const T*)h->totpart, (T*)h->dsum,
+                         h->feas_row,
                          h->fpart, h->nfpart, h->sums,
                          h->ticket, h->st, h->nubuf, (T*)h->coef, h->hist, ip, s));
   if (ev) CK(cudaEventRecord(ev[5], s));
@@ -360,8 +362,8 @@ void free_handle(plam_handle_s* h) {
   if (!h) return;
   if (h->graph) cudaGraphExecDestroy(h->graph);
   void* dev[] = {h->G, h->R[0], h->R[1], h->part, h->part64, h->B, h->L0, h->C, h->red, h->Mt, h->L0t,
-                 h->feas_row, h->colpart, h->totpart, h->sums, h->ticket, h->st, h->nubuf, h->coef,
-                 h->hist,
+                 h->feas_row, h->colpart, h->totpart, h->sums, h->dsum, h->ticket, h->st, h->nubuf,
+                 h->coef, h->hist,
                  h->rho, h->blk, h->y, h->fpart, h->W, h->Z, h->info, h->feas_dev, h->Qtmp,
                  h->dotpart, h->r_halo, h->r_blk, h->r_part, h->r_red, h->r_dots, h->r_dred,
                  h->r_bar, h->r_err, h->tc_err, h->msplit, h->kkt_part, h->lam};
@@ -708,6 +710,7 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
             alloc(&h->colpart, (size_t)h->nrt * kColDots * p * esz) &&
             alloc(&h->totpart, (size_t)h->nrt * h->nct * kTotDots * esz) &&
             alloc((void**)&h->sums, (kColDots * p + kTotDots) * sizeof(double)) &&
+            alloc(&h->dsum, (size_t)kStepRanges * (kColDots * p + kTotDots) * esz) &&
             alloc((void**)&h->ticket, sizeof(unsigned int)) &&
             alloc((void**)&h->st, sizeof(DevState)) &&
             alloc((void**)&h->nubuf, 2 * p * sizeof(double)) &&

@@ -87,9 +87,11 @@ template <typename T>
 cudaError_t launch_update(int64_t n, int p, const T* X, int64_t ldx, const T* G, int64_t ldg,
                           T* R0, T* R1, int64_t ldr, const T* Mt, const T* L0t, const T* coef,
                           const DevState* st, T* colpart, T* totpart, cudaStream_t s);
+// dsum: kStepRanges x (3p + 6) partial sums of scratch in the storage type;
 // sums: 3p + 6 doubles of scratch; ticket: one zero-initialised counter.
+constexpr int kStepRanges = 32;
 template <typename T>
-cudaError_t launch_step_size(int nrt, int nct, const T* colpart, const T* totpart,
+cudaError_t launch_step_size(int nrt, int nct, const T* colpart, const T* totpart, T* dsum,
                              const double* feas_row, const double* fpart, int nfpart, double* sums,
                              unsigned int* ticket, DevState* st, double* nubuf, T* coef,
                              double* hist, IterParams prm, cudaStream_t s);

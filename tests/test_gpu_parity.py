@@ -95,11 +95,14 @@ def test_energy_grad_matches_oracle(precision, kind):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("grid", [(37, 9, 19), (64, 3, 2), (1, 1, 40), (33, 33, 17)])
+@pytest.mark.parametrize("grid", [(37, 9, 19), (64, 3, 2), (1, 1, 40), (33, 33, 17),
+                                  (256, 5, 3), (132, 4, 17), (8, 7, 18), (4, 300, 3)])
 def test_stencil_gradient_on_non_cubic_grids(precision, grid):
     """G = (L3 + Diag(V)) X on grids whose x extent is not a multiple of the 32-wide tile and
     whose z extent is not a multiple of the 16-plane march, against L3 assembled here as the
-    Kronecker sum of three Dirichlet second differences (x fastest)."""
+    Kronecker sum of three Dirichlet second differences (x fastest).  x extents that are
+    multiples of 4 take the 16-byte-vector kernel: rows of 64 vectors (two warps), of 33
+    vectors (warp edges inside rows), of 2 and of 1 vector (both x boundaries in one vector)."""
     import scipy.sparse as sp
     nx, ny, nz = grid
     n, p = nx * ny * nz, 3
