@@ -44,6 +44,11 @@ WORKLOADS = {
     # [4, min(64, n/2)], beta = 1, PCAL to relative KKT 1e-6 in one persistent launch.
     "batched": dict(kind="batched", count=512, n_lo=64, n_hi=2048, beta=1.0, tol=1e-6,
                     name="batched_512_dense_trace_n64-2048_p4-64", fp64_sample=6),
+    # 3D Laplacian plus potential on a 128^3 grid, p = 1024 (8.6 GB per n x p FP32 buffer):
+    # per-kernel timings only (--kernel-iters), from a Gaussian start generated on the device
+    # (a host FP64 start would take 17 GB).
+    "stencil3d_128": dict(kind="stencil3d", m=128, n=2097152, p=1024, beta=1.0, tol=1e-5,
+                          name="stencil3d_n2097152_p1024", kernel_only=True),
 }
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
@@ -526,11 +531,22 @@ def run_kernel_iters(args):
                           "iterations": sum(i.iters for i in infos)}), flush=True)
         bs.close()
         return
+    import numpy as np
     wl = dict(WORKLOADS[args.workload], tensor_cores=args.tensor_cores)
-    w = load_inputs(wl)
-    from paper_1810_03930_gb300 import colmajor_to_device
-    sol = make_solver(wl, "fp32", torch, engine="graph")
-    X = colmajor_to_device(w.X0, torch.float32)
+    if wl.get("kernel_only"):
+        from workloads import rng_for, uniform_potential
+        wl["V"] = uniform_potential(wl["n"], rng_for(5, 0))
+        sol = make_solver(wl, "fp32", torch, engine="graph")
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(1810039300 + 10 * 5 + 1)
+        # column-major n x p: a (p, n) row-major tensor; iid N(0, 1/n) entries
+        X = torch.randn((wl["p"], wl["n"]), generator=gen, device="cuda",
+                        dtype=torch.float32) / float(np.sqrt(wl["n"]))
+    else:
+        w = load_inputs(wl)
+        from paper_1810_03930_gb300 import colmajor_to_device
+        sol = make_solver(wl, "fp32", torch, engine="graph")
+        X = colmajor_to_device(w.X0, torch.float32)
     kms, done = sol.time_kernels(X, args.kernel_iters)
     sol.close()
     print(json.dumps({"workload": wl["name"], "tensor_cores": args.tensor_cores, "iterations": done,
@@ -709,6 +725,8 @@ def main():
         if rank == 0:
             run_kernel_iters(args)
         return
+    if WORKLOADS[args.workload].get("kernel_only"):
+        raise SystemExit(f"workload {args.workload}: per-kernel timings only (use --kernel-iters K)")
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

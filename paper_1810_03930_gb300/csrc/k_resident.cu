@@ -68,21 +68,32 @@ struct ResidentArgs {
 __device__ inline float ldcg_f(const float* p) { return __ldcg(p); }
 __device__ inline double ldcg_d(const double* p) { return __ldcg(p); }
 
+__device__ __forceinline__ void red_add_release_gpu(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // Grid-wide barrier with a bounded wait.  bar[0] counts arrivals over the
 // whole launch (zeroed before it); barrier number g releases when the count
-// reaches (g + 1) * expect, and every CTA polls the count directly.  Returns
-// false when the wait expired here or the error flag is already raised.
+// reaches (g + 1) * expect, and every CTA polls the count directly.  The CTA's
+// writes are ordered before thread 0's arrival by the block barrier and
+// published by the arrival's release semantics; the polling load acquires
+// the other CTAs' writes, and the closing block barrier passes them on to the
+// CTA's threads (no full fences).  Returns false when the wait expired here
+// or the error flag is already raised.
 __device__ bool grid_barrier(unsigned int* bar, unsigned int expect, unsigned int& gen, int* err) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
     const unsigned int target = (gen + 1u) * expect;
-    __threadfence();
-    atomicAdd(&bar[0], 1u);
+    red_add_release_gpu(&bar[0], 1u);
     long long spins = 0;
-    const volatile unsigned int* cnt = bar;
-    while (*cnt < target) {
+    while (ld_acquire_gpu(bar) < target) {
       if (++spins > kBarrierSpins) {
         atomicExch(err, 1);
         ok = 0;
@@ -91,7 +102,6 @@ __device__ bool grid_barrier(unsigned int* bar, unsigned int expect, unsigned in
       if (spins > 4096) __nanosleep(64);   // busy-poll first, then back off
     }
     gen = gen + 1u;
-    __threadfence();
     if (ok && *(volatile int*)err != 0) ok = 0;
   }
   __syncthreads();
@@ -272,19 +282,25 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_solve_kernel(Resident
       const float Q = Qafter + (tot_c - ic);
       const float y = ((float)(n - gi) * P + (float)(gi + 1) * Q) * (float)a.inv_np1;
       fy = block_sum_f((t < nr) ? rv * y : 0.f, fscr);
-      // neighbours' boundary rows, fetched once
+      // neighbours' boundary rows, fetched once; alpha y of each row for all threads
       if (t < p) halo_s[t] = (b > 0) ? ldcg_f(a.halo + (size_t)(b - 1) * 2 * p + p + t) : 0.f;
       else if (t < 2 * p) halo_s[t] = (r0 + nr < n) ? ldcg_f(a.halo + (size_t)(b + 1) * 2 * p + t - p) : 0.f;
+      if (t < nr) grp[t] = (float)a.alpha * y;
       __syncthreads();
-      if (t < nr) {
-        const float ty = (float)a.alpha * y;
-        const float q2 = (float)(2.0 * a.q);
-        const bool first = (t == 0), last = (t == nr - 1);
-        for (int c = 0; c < p; ++c) {
-          const float x = Xs[c * rp + t];
-          const float xm = first ? halo_s[c] : Xs[c * rp + t - 1];
-          const float xp = last ? halo_s[p + c] : Xs[c * rp + t + 1];
-          gr[c * rp + t] = fmaf(q2, (x + x) - xm - xp, ty * x);
+      {
+        // row r = t mod nr, columns g, g + ng, ... for the ng = 512 / nr groups of rows
+        const int ng = kResThreads / nr;
+        const int g = t / nr, r = t - g * nr;
+        if (g < ng) {
+          const float ty = grp[r];
+          const float q2 = (float)(2.0 * a.q);
+          const bool first = (r == 0), last = (r == nr - 1);
+          for (int c = g; c < p; c += ng) {
+            const float x = Xs[c * rp + r];
+            const float xm = first ? halo_s[c] : Xs[c * rp + r - 1];
+            const float xp = last ? halo_s[p + c] : Xs[c * rp + r + 1];
+            gr[c * rp + r] = fmaf(q2, (x + x) - xm - xp, ty * x);
+          }
         }
       }
     } else {
@@ -415,6 +431,7 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_solve_kernel(Resident
       feas2 = (double)block_sum_f(fr, fscr);
     }
     if (t < p) {
+      // d_i = C_ii - sum_k B_ik Psi_ki + beta (sum_k B_ik^2 - B_ii) (eq. lambda2)
       const int i = t;
       float s1f = 0.f, s2f = 0.f;
       for (int kk2 = 0; kk2 < p; ++kk2) {
@@ -459,24 +476,36 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_solve_kernel(Resident
               a2[u][v] = fmaf(xa[u], la[v], a2[u][v]);
             }
         }
+        // the tile's four rows of a column are one 16-byte vector (rp is a multiple
+        // of 4), so consecutive lanes touch consecutive vectors: no bank conflicts
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const int c = 4 * cb + v;
           if (c >= p) continue;
+          const int o = c * rp + 4 * rb;
+          const float4 g4 = *reinterpret_cast<const float4*>(gr + o);
+          const float4 x4 = *reinterpret_cast<const float4*>(Xs + o);
+          const float4 p4 = (k > 0) ? *reinterpret_cast<const float4*>(rpv + o)
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float ga[4] = {g4.x, g4.y, g4.z, g4.w};
+          const float xa2[4] = {x4.x, x4.y, x4.z, x4.w};
+          const float pa[4] = {p4.x, p4.y, p4.z, p4.w};
+          float rva[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int r = 4 * rb + u;
+            rva[u] = ga[u];
             if (r >= nr) continue;
-            const float g = gr[c * rp + r];
-            const float x = Xs[c * rp + r];
+            const float g = ga[u];
+            const float x = xa2[u];
             const float rv = g - a1[u][v];
             const float kv = g - a2[u][v];
-            gr[c * rp + r] = rv;
+            rva[u] = rv;
             kk = fmaf(kv, kv, kk);
             gg = fmaf(g, g, gg);
             xg = fmaf(x, g, xg);
             if (k > 0) {
-              const float rpe = rpv[c * rp + r];
+              const float rpe = pa[u];
               const float sv = omn[c] * x - rpe * inv_etap;
               const float yv = rv - rpe;
               ss = fmaf(sv, sv, ss);
@@ -484,6 +513,7 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_solve_kernel(Resident
               yy = fmaf(yv, yv, yy);
             }
           }
+          *reinterpret_cast<float4*>(gr + o) = make_float4(rva[0], rva[1], rva[2], rva[3]);
         }
       }
       __syncthreads();
@@ -492,7 +522,9 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_solve_kernel(Resident
       const int chunks = kResThreads / p;
       const int rpc = (nr + chunks - 1) / chunks;
       if (t < chunks * p) {
-        const int c = t % p, ch = t / p;
+        // chunk index fastest across the lanes: their rows are rpc apart, which
+        // spreads a warp's loads over the banks better than columns rp apart
+        const int c = t / chunks, ch = t % chunks;
         const int ra = ch * rpc, rb2 = min(nr, ra + rpc);
         float sx = 0.f, sxr = 0.f, sr = 0.f;
         for (int r = ra; r < rb2; ++r) {

@@ -24,9 +24,12 @@
 //                          canonical K-major 128-byte-swizzle layout, rounded
 //                          to nearest TF32 (and split into hi + lo when
 //                          compensated)
-//   warps 4-7            : epilogue (TMEM lane quarter = warp mod 4); one of
-//                          them streams the tile's X, G and R^{k-1} through a
-//                          two-slot ring of 16-column TMA copies
+//   warps 4-7, 10-13     : epilogue, two groups of four warps (TMEM lane
+//                          quarter = warp mod 4).  The tile's X, G and R^{k-1}
+//                          stream through a two-slot ring of 16-column TMA
+//                          copies; group e takes the chunks in slot e (every
+//                          other chunk), so two warps per scheduler share the
+//                          epilogue arithmetic
 // M, its TF32 remainder and E arrive from a small kernel that stores their
 // rounded TF32 parts once per iteration.
 //
@@ -40,7 +43,7 @@ namespace plam {
 
 constexpr int kUpM = 128;          // rows of X per tile (TMEM lanes)
 constexpr int kUpK = 32;           // inner indices per stage
-constexpr int kUpThreads = 320;    // 10 warps
+constexpr int kUpThreads = 448;    // 14 warps
 constexpr int kUpConvThreads = 128;
 constexpr int kUpMaxStages = 4;
 constexpr int kUpChunk = 16;       // epilogue columns per ring slot
@@ -105,7 +108,7 @@ __host__ __device__ inline uint32_t up_stage_bytes(int N, bool split) {
   return split ? 2 * A + 3 * BT : A + 2 * BT;
 }
 __host__ __device__ inline uint32_t up_ring_bytes() { return 2u * 3u * kUpM * kUpChunk * 4u; }
-__host__ __device__ inline uint32_t up_red_bytes(int N) { return (12u * N + 24u) * 4u; }
+__host__ __device__ inline uint32_t up_red_bytes(int N) { return (12u * N + 48u) * 4u; }
 
 __device__ __forceinline__ void named_bar(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
@@ -139,7 +142,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   unsigned char* ring = base + a.pipe_bytes;                        // [2 slots][X | G | R^{k-1}]
   const uint32_t EPC = kUpM * kUpChunk * 4;                          // one 128 x 16 operand chunk
   float* colred = reinterpret_cast<float*>(ring + up_ring_bytes());  // [4][3][N]
-  float* wsum = colred + 12 * N;                                     // [4][6]
+  float* wsum = colred + 12 * N;                                     // [8][6]
   uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(colred) +
                                                up_red_bytes(N));
   uint64_t* conv = full + kUpMaxStages;
@@ -150,7 +153,8 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   uint64_t* done = epfull + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   int* flags = reinterpret_cast<int*>(tmem_slot + 1);   // [epilogue abort, converter abort,
-                                                        //  stages issued, ring chunks issued]
+                                                        //  stages issued, chunks issued into
+                                                        //  ring slot 0, into slot 1]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int KT = (a.p + kUpK - 1) / kUpK;
   const int ntl = (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
@@ -165,11 +169,11 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 128);
+      mbar_init(&tempty[b], 256);
       mbar_init(&epfull[b], 1);
     }
     mbar_init(done, 1);
-    flags[0] = 0; flags[1] = 0; flags[2] = 0; flags[3] = 0;
+    flags[0] = 0; flags[1] = 0; flags[2] = 0; flags[3] = 0; flags[4] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 2) {
@@ -243,7 +247,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       }
       mma_commit(done);
     }
-  } else if (warp == 2 || warp == 3 || warp >= 8) {
+  } else if (warp == 2 || warp == 3 || warp == 8 || warp == 9) {
     // ---- converters: landed X slice [32 columns][128 rows] -> K-major SW128 rows
     const int ct = conv_tid(warp, lane);
     int gs = 0;
@@ -295,10 +299,17 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       if (abort) break;
     }
   } else {
-    // ---- epilogue warps 4-7
-    const int q = warp - 4;
-    const int et = threadIdx.x - 128;          // 0 .. 127 = TMEM lane = row in the tile
-    const bool leader = et == 0;
+    // ---- epilogue: group e = 0 (warps 4-7) and e = 1 (warps 10-13).  Every named
+    // barrier below is reached by every thread of its group (or of both groups)
+    // whatever happens; after an expired wait only the work is skipped, and both
+    // groups leave the tile loop together after an all-epilogue barrier.
+    const int e = warp >= 10 ? 1 : 0;
+    const int q = warp & 3;                    // TMEM lane quarter
+    const int et = q * 32 + lane;              // TMEM lane = row in the tile
+    const int el = (warp - (e ? 10 : 4)) * 32 + lane;   // 0 .. 127 within the group
+    const int ea = e * 128 + el;               // 0 .. 255 over both groups
+    const int gbar = e ? 3 : 1;                // named barrier of the group
+    const bool leader = el == 0;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     const int nch = N / kUpChunk;
     float* R = (kst & 1) ? a.R1 : a.R0;
@@ -306,88 +317,95 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     const float* cprev = a.coef + (size_t)((kst + 1) & 1) * (2 * a.p + 1);
     const float inv_etap = kst > 0 ? cprev[0] : 0.f;
     const uint32_t ep_bytes = (kst > 0 ? 3u : 2u) * EPC;
-    int gc = 0;
-    auto issue_chunk = [&](int g, int r0, int cc) {
+    // chunk g of this CTA's sequence (tiles in order, nch chunks each) into ring slot g & 1
+    auto issue_seq = [&](int g) {
+      const int lt2 = g / nch, jj = g - lt2 * nch;
+      if (lt2 >= ntl) return;
+      const int tile2 = (int)blockIdx.x + lt2 * (int)gridDim.x;
+      const int r0c = (tile2 / a.nct) * kUpM, cc = (tile2 % a.nct) * N + jj * kUpChunk;
       unsigned char* sl = ring + (g & 1) * 3 * EPC;
       mbar_arrive_expect_tx(&epfull[g & 1], ep_bytes);
-      tma_load_2d(sl, &mapXe, &epfull[g & 1], r0, cc);
-      tma_load_2d(sl + EPC, &mapGe, &epfull[g & 1], r0, cc);
-      if (kst > 0) tma_load_2d(sl + 2 * EPC, mapRp, &epfull[g & 1], r0, cc);
-      flags[3] = g + 1;
+      tma_load_2d(sl, &mapXe, &epfull[g & 1], r0c, cc);
+      tma_load_2d(sl + EPC, &mapGe, &epfull[g & 1], r0c, cc);
+      if (kst > 0) tma_load_2d(sl + 2 * EPC, mapRp, &epfull[g & 1], r0c, cc);
+      flags[3 + (g & 1)] = g + 1;
     };
+    if (leader) issue_seq(e);
+    bool aborted = false;
     for (int lt = 0; lt < ntl; ++lt) {
       const int tile = (int)blockIdx.x + lt * (int)gridDim.x;
       const int rb = tile / a.nct, ctl = tile % a.nct;
       const int r0 = rb * kUpM, c0 = ctl * N;
       const int b = lt & 1;
-      if (leader)
-        for (int j = 0; j < nch && j < 2; ++j) issue_chunk(gc + j, r0, c0 + j * kUpChunk);
       if (!mbar_wait_warp(&tfull[b], (uint32_t)(lt >> 1) & 1u, a.err) && lane == 0) flags[0] = 1;
-      named_bar(1, 128);
+      named_bar(4, 256);
       if (*(volatile int*)&flags[0] != 0) break;
       tc_fence_after();
       const int64_t r = (int64_t)r0 + et;
       const bool row_ok = r < a.n;
       const uint32_t t1 = tmem + lane_off + (uint32_t)(b * 2 * N), t2 = t1 + (uint32_t)N;
       float ss = 0.f, sy = 0.f, yy = 0.f, kk = 0.f, gg = 0.f, xg = 0.f;
-      bool abort = false;
-      for (int j = 0; j < nch; ++j, ++gc) {
-        const int slot = gc & 1;
-        if (!mbar_wait_warp(&epfull[slot], (uint32_t)(gc >> 1) & 1u, a.err) && lane == 0)
-          flags[0] = 1;
-        named_bar(1, 128);
-        if (*(volatile int*)&flags[0] != 0) { abort = true; break; }
-        const int j0 = j * kUpChunk;
-        uint32_t v1[16], v2[16];
-        tmem_ld16_nw(t1 + (uint32_t)j0, v1);
-        tmem_ld16_nw(t2 + (uint32_t)j0, v2);
-        const float* Xs = reinterpret_cast<const float*>(ring + slot * 3 * EPC);
-        const float* Gs = Xs + kUpM * kUpChunk;
-        const float* Rs = Gs + kUpM * kUpChunk;
-        float dv[48];
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      // the chunks of this tile whose sequence number has parity e
+      const int gbase = lt * nch;
+      for (int j = ((gbase & 1) == e) ? 0 : 1; j < nch; j += 2) {
+        const int gc = gbase + j;
+        if (!aborted && !mbar_wait_warp(&epfull[e], (uint32_t)(gc >> 1) & 1u, a.err)) {
+          if (lane == 0) flags[0] = 1;
+        }
+        named_bar(gbar, 128);
+        if (*(volatile int*)&flags[0] != 0) aborted = true;
+        if (!aborted) {
+          const int j0 = j * kUpChunk;
+          uint32_t v1[16], v2[16];
+          tmem_ld16_nw(t1 + (uint32_t)j0, v1);
+          tmem_ld16_nw(t2 + (uint32_t)j0, v2);
+          const float* Xs = reinterpret_cast<const float*>(ring + e * 3 * EPC);
+          const float* Gs = Xs + kUpM * kUpChunk;
+          const float* Rs = Gs + kUpM * kUpChunk;
+          float dv[48];
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int col = c0 + j0 + c;
-          float xx = 0.f, xrv = 0.f, rr = 0.f;
-          if (row_ok && col < a.p) {
-            const float x = Xs[c * kUpM + et], g = Gs[c * kUpM + et];
-            const float rv = g - __uint_as_float(v1[c]);
-            const float kv = rv - __uint_as_float(v2[c]);
-            R[r + (int64_t)col * a.ldr] = rv;
-            xx = x * x;
-            xrv = x * rv;
-            rr = rv * rv;
-            kk = fmaf(kv, kv, kk);
-            gg = fmaf(g, g, gg);
-            xg = fmaf(x, g, xg);
-            if (kst > 0) {
-              const float rp = Rs[c * kUpM + et];
-              const float sv = __ldg(cprev + 1 + a.p + col) * x - rp * inv_etap;
-              const float yv = rv - rp;
-              ss = fmaf(sv, sv, ss);
-              sy = fmaf(sv, yv, sy);
-              yy = fmaf(yv, yv, yy);
+          for (int c = 0; c < 16; ++c) {
+            const int col = c0 + j0 + c;
+            float xx = 0.f, xrv = 0.f, rr = 0.f;
+            if (row_ok && col < a.p) {
+              const float x = Xs[c * kUpM + et], g = Gs[c * kUpM + et];
+              const float rv = g - __uint_as_float(v1[c]);
+              const float kv = rv - __uint_as_float(v2[c]);
+              R[r + (int64_t)col * a.ldr] = rv;
+              xx = x * x;
+              xrv = x * rv;
+              rr = rv * rv;
+              kk = fmaf(kv, kv, kk);
+              gg = fmaf(g, g, gg);
+              xg = fmaf(x, g, xg);
+              if (kst > 0) {
+                const float rp = Rs[c * kUpM + et];
+                const float sv = __ldg(cprev + 1 + a.p + col) * x - rp * inv_etap;
+                const float yv = rv - rp;
+                ss = fmaf(sv, sv, ss);
+                sy = fmaf(sv, yv, sy);
+                yy = fmaf(yv, yv, yy);
+              }
+            }
+            dv[c] = xx;
+            dv[16 + c] = xrv;
+            dv[32 + c] = rr;
+          }
+          warp_sum48(dv, lane);
+          if ((lane & 1) == 0) {
+            const int bb = 24 * ((lane >> 4) & 1) + 12 * ((lane >> 3) & 1) + 6 * ((lane >> 2) & 1) +
+                           3 * ((lane >> 1) & 1);
+#pragma unroll
+            for (int k3 = 0; k3 < 3; ++k3) {
+              const int idx = bb + k3, d = idx >> 4, c = idx & 15;
+              colred[(q * 3 + d) * N + j0 + c] = dv[k3];
             }
           }
-          dv[c] = xx;
-          dv[16 + c] = xrv;
-          dv[32 + c] = rr;
         }
-        warp_sum48(dv, lane);
-        if ((lane & 1) == 0) {
-          const int bb = 24 * ((lane >> 4) & 1) + 12 * ((lane >> 3) & 1) + 6 * ((lane >> 2) & 1) +
-                         3 * ((lane >> 1) & 1);
-#pragma unroll
-          for (int e = 0; e < 3; ++e) {
-            const int idx = bb + e, d = idx >> 4, c = idx & 15;
-            colred[(q * 3 + d) * N + j0 + c] = dv[e];
-          }
-        }
-        named_bar(1, 128);   // every warp is done with the slot
-        if (leader && j + 2 < nch) issue_chunk(gc + 2, r0, c0 + (j + 2) * kUpChunk);
+        named_bar(gbar, 128);   // every warp of the group is done with the slot
+        if (leader && !aborted) issue_seq(gc + 2);
       }
-      if (abort) break;
       // the accumulators of buffer b are read: the MMA may reuse them
       tc_fence_before();
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&tempty[b]))
@@ -400,23 +418,29 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       }
       if (lane == 0) {
 #pragma unroll
-        for (int d = 0; d < kTotDots; ++d) wsum[q * kTotDots + d] = tot[d];
+        for (int d = 0; d < kTotDots; ++d) wsum[(e * 4 + q) * kTotDots + d] = tot[d];
       }
-      named_bar(1, 128);
-      for (int jj = et; jj < N; jj += 128) {
-        const int col = c0 + jj;
-        if (col < a.p) {
-          float* cp = a.colpart + (size_t)rb * kColDots * a.p;
+      named_bar(4, 256);
+      const bool stop_all = *(volatile int*)&flags[0] != 0;
+      if (!stop_all) {
+        for (int jj = ea; jj < N; jj += 256) {
+          const int col = c0 + jj;
+          if (col < a.p) {
+            float* cp = a.colpart + (size_t)rb * kColDots * a.p;
 #pragma unroll
-          for (int d = 0; d < 3; ++d)
-            cp[(size_t)d * a.p + col] = ((colred[(0 * 3 + d) * N + jj] + colred[(1 * 3 + d) * N + jj]) +
-                                         colred[(2 * 3 + d) * N + jj]) + colred[(3 * 3 + d) * N + jj];
+            for (int d = 0; d < 3; ++d)
+              cp[(size_t)d * a.p + col] = ((colred[(0 * 3 + d) * N + jj] + colred[(1 * 3 + d) * N + jj]) +
+                                           colred[(2 * 3 + d) * N + jj]) + colred[(3 * 3 + d) * N + jj];
+          }
+        }
+        if (ea < kTotDots) {
+          float t8 = wsum[ea];
+          for (int w8 = 1; w8 < 8; ++w8) t8 += wsum[w8 * kTotDots + ea];
+          a.totpart[((size_t)rb * a.nct + ctl) * kTotDots + ea] = t8;
         }
       }
-      if (et < kTotDots)
-        a.totpart[((size_t)rb * a.nct + ctl) * kTotDots + et] =
-            ((wsum[et] + wsum[kTotDots + et]) + wsum[2 * kTotDots + et]) + wsum[3 * kTotDots + et];
-      named_bar(1, 128);   // colred / wsum are free for the next tile
+      named_bar(4, 256);   // colred / wsum are free for the next tile
+      if (stop_all) break;
     }
   }
   __syncwarp();
@@ -431,11 +455,13 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       for (long long i = 0; i < kTcSpin && !mbar_try_wait(&full[g % nst], (uint32_t)(g / nst) & 1u);
            ++i) {
       }
-    const int gc_issued = flags[3];
-    for (int g = gc_issued > 2 ? gc_issued - 2 : 0; g < gc_issued; ++g)
-      for (long long i = 0; i < kTcSpin && !mbar_try_wait(&epfull[g & 1], (uint32_t)(g >> 1) & 1u);
+    for (int sl = 0; sl < 2; ++sl) {   // the last chunk issued into each ring slot has landed
+      const int g = flags[3 + sl] - 1;
+      if (g < 0) continue;
+      for (long long i = 0; i < kTcSpin && !mbar_try_wait(&epfull[sl], (uint32_t)(g >> 1) & 1u);
            ++i) {
       }
+    }
   }
   __syncthreads();
   if (warp == 2) {
