@@ -27,6 +27,12 @@ namespace plam {
 constexpr int kBThreads = 512;
 constexpr int kBMaxP = 64;
 constexpr int kBK = 32;              // inner-index depth of one shared-memory stage
+// Row strides of the staged tiles, padded against bank conflicts: the X tile of
+// A X is written with 32 consecutive lanes on 32 consecutive rows and read as
+// 16-byte vectors (stride 68: a multiple of 4, 4 banks apart per row), the Gram
+// tiles are written the same way and read element-wise (stride 65).
+constexpr int kBXS = kBMaxP + 4;
+constexpr int kBGS = kBMaxP + 1;
 
 // Shared memory of one CTA (dynamic, 16-byte aligned).
 struct BatchSmem {
@@ -44,7 +50,7 @@ struct BatchSmem {
 };
 
 // one stage buffer: a 32 x RB tile of A and a 32 x 64 tile of X (two buffers per CTA)
-__host__ __device__ inline size_t batch_stage_floats(int rb) { return (size_t)kBK * rb + (size_t)kBK * kBMaxP; }
+__host__ __device__ inline size_t batch_stage_floats(int rb) { return (size_t)kBK * rb + (size_t)kBK * kBXS; }
 
 // ---------------------------------------------------------------- step 1: G = A X
 // The sum over n runs in float within each 32-deep stage and is carried across
@@ -90,7 +96,7 @@ __device__ void batch_ax(const BatchDesc& q, float* st0, float* st1) {
 #pragma unroll
       for (int j = 0; j < NX; ++j) {
         const int e = t + j * kBThreads;
-        st[kBK * RB + (e % kBK) * kBMaxP + e / kBK] = px[j];
+        st[kBK * RB + (e % kBK) * kBXS + e / kBK] = px[j];
       }
     };
     fetch(0);
@@ -124,7 +130,7 @@ __device__ void batch_ax(const BatchDesc& q, float* st0, float* st1) {
               a[4 * h + 3] = a4.w;
             }
           }
-          const float4 b = *reinterpret_cast<const float4*>(st + kBK * RB + kk * kBMaxP + 4 * ty);
+          const float4 b = *reinterpret_cast<const float4*>(st + kBK * RB + kk * kBXS + 4 * ty);
 #pragma unroll
           for (int i = 0; i < R4; ++i) {
             acc[i][0] = fmaf(a[i], b.x, acc[i][0]);
@@ -182,18 +188,18 @@ __device__ void batch_grams(const BatchDesc& q, const float* Y, int64_t ldy, flo
       const int rr = e % kBK, c = e / kBK;
       const int64_t r = r0 + rr;
       const bool ok = r < n && c < p;
-      stX[rr * kBMaxP + c] = ok ? q.X[r + (int64_t)c * q.ldx] : 0.f;
-      if (Y) stY[rr * kBMaxP + c] = ok ? Y[r + (int64_t)c * ldy] : 0.f;
+      stX[rr * kBGS + c] = ok ? q.X[r + (int64_t)c * q.ldx] : 0.f;
+      if (Y) stY[rr * kBGS + c] = ok ? Y[r + (int64_t)c * ldy] : 0.f;
     }
     __syncthreads();
     for (int rr = 0; rr < kBK; ++rr) {
       float xi[4], xj[2], yj[2];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) xi[a] = stX[rr * kBMaxP + ti + 16 * a];
+      for (int a = 0; a < 4; ++a) xi[a] = stX[rr * kBGS + ti + 16 * a];
 #pragma unroll
       for (int b = 0; b < 2; ++b) {
-        xj[b] = stX[rr * kBMaxP + tj + 32 * b];
-        yj[b] = Y ? stY[rr * kBMaxP + tj + 32 * b] : 0.f;
+        xj[b] = stX[rr * kBGS + tj + 32 * b];
+        yj[b] = Y ? stY[rr * kBGS + tj + 32 * b] : 0.f;
       }
 #pragma unroll
       for (int a = 0; a < 4; ++a)
@@ -465,7 +471,7 @@ __device__ void batch_solve_one(const BatchDesc& q, const BatchParams& prm, plam
       // ||Q^T Q - I||_F: Q^T Q over 32-row stages of Q staged in shared memory (the stage
       // buffers), thread (ti, tj) owning entries i = ti + 16a, j = tj + 32b
       {
-        double* qs = reinterpret_cast<double*>(stA);      // [32][64] doubles
+        double* qs = reinterpret_cast<double*>(stA);      // [32][65] doubles
         const int ti = t & 15, tj = t >> 4;
         double acc[4][2];
 #pragma unroll
@@ -474,15 +480,15 @@ __device__ void batch_solve_one(const BatchDesc& q, const BatchParams& prm, plam
           for (int e = t; e < kBK * kBMaxP; e += kBThreads) {
             const int rr = e % kBK, c = e / kBK;
             const int64_t r = r0 + rr;
-            qs[rr * kBMaxP + c] = (r < n && c < p) ? q.Q[r + (int64_t)c * q.ldq] : 0.0;
+            qs[rr * kBGS + c] = (r < n && c < p) ? q.Q[r + (int64_t)c * q.ldq] : 0.0;
           }
           __syncthreads();
           for (int rr = 0; rr < kBK; ++rr) {
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-              const double qi = qs[rr * kBMaxP + ti + 16 * a];
-              acc[a][0] = fma(qi, qs[rr * kBMaxP + tj], acc[a][0]);
-              acc[a][1] = fma(qi, qs[rr * kBMaxP + tj + 32], acc[a][1]);
+              const double qi = qs[rr * kBGS + ti + 16 * a];
+              acc[a][0] = fma(qi, qs[rr * kBGS + tj], acc[a][0]);
+              acc[a][1] = fma(qi, qs[rr * kBGS + tj + 32], acc[a][1]);
             }
           }
           __syncthreads();
