@@ -149,6 +149,33 @@ __device__ inline float block_sum_f(float v, float* scratch /* >= 17 */) {
   return scratch[16];
 }
 
+// Two block_sum_f at once: each value is summed in exactly the order block_sum_f
+// uses (butterfly in the warp, then the 16 warp sums in order by one thread),
+// with one set of block barriers for both.
+__device__ inline void block_sum2_f(float& v0, float& v1, float* scratch /* >= 34 */) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+    v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) {
+    scratch[w] = v0;
+    scratch[17 + w] = v1;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    const float* src = scratch + 17 * threadIdx.x;
+    float s = 0.f;
+    for (int i = 0; i < kResThreads / 32; ++i) s += src[i];
+    scratch[16 + 17 * threadIdx.x] = s;
+  }
+  __syncthreads();
+  v0 = scratch[16];
+  v1 = scratch[33];
+}
+
 // Deterministic block-wide inclusive scan of two floats (blockDim = kResThreads).
 __device__ inline void block_scan2(float& a, float& c, float* sh /* 2 x 16 */, float& tot_a,
                                    float& tot_c) {
@@ -244,8 +271,9 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_solve_kernel(Resident
       s2 = (float)(n - gi) * s;
     }
     if (a.kind == kObjHartree) {
-      const double S1 = (double)block_sum_f(s1, fscr);
-      const double S2 = (double)block_sum_f(s2, fscr);
+      block_sum2_f(s1, s2, fscr);
+      const double S1 = (double)s1;
+      const double S2 = (double)s2;
       if (t == 0) {
         a.blk[2 * b] = S1;
         a.blk[2 * b + 1] = S2;
@@ -270,8 +298,9 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_solve_kernel(Resident
         if (j < b) pa += (float)ldcg_d(a.blk + 2 * j);
         if (j > b) qa += (float)ldcg_d(a.blk + 2 * j + 1);
       }
-      const float Pbefore = block_sum_f(pa, fscr);
-      const float Qafter = block_sum_f(qa, fscr);
+      block_sum2_f(pa, qa, fscr);
+      const float Pbefore = pa;
+      const float Qafter = qa;
       const int64_t gi = r0 + t;
       const float rv = (t < nr) ? (float)rho[t] : 0.f;
       float ia = (t < nr) ? (float)(gi + 1) * rv : 0.f;
@@ -418,7 +447,8 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_solve_kernel(Resident
       const int i = e / pp, j = e % pp;
       Ls[e] = (j < p) ? 0.5f * (Ws[(p + j) * p + i] + Ws[(p + i) * p + j]) : 0.f;
     }
-    __syncthreads();
+    // (the block barriers inside block_sum_f below also order these writes of Ls
+    // before the reads of the d loop)
 #define BU(i, j) Ws[(size_t)(j) * p + (i)]
     double feas2 = 0.0;
     {
