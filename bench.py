@@ -119,7 +119,11 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # the raw samples go to PLAM_CLOCKS_DIR (default: the system temporary directory);
+        # the bench line carries their summary
+        import tempfile
+        cdir = os.environ.get("PLAM_CLOCKS_DIR", tempfile.gettempdir())
+        self.path = os.path.join(cdir, f"clocks_bench_{os.getpid()}.csv")
 
     def start(self):
         try:
