@@ -145,3 +145,46 @@ def test_callback_failure_is_reported():
         s.solve(to_dev(w.X0, s))
     assert isinstance(s._cb_error, RuntimeError)
     s.close()
+
+
+@pytest.mark.parametrize("variant", ["pcal", "plam"])
+def test_callback_problem2_nonsymmetric_gram_matches_oracle(variant):
+    """Problem 2 of Section 5.2 (f = 1/2 tr(X^T A X) + tr(G_lin^T X)) through the user-energy
+    path.  Unlike the built-in objectives, X^T grad f is not symmetric away from a solution, so
+    this exercises the multiplier's symmetrisation Psi and eq. (lambda2) with a non-symmetric
+    Gram.  Against the oracle's FP64 solve from the same start: the same objective at the
+    stopping iterate and the same orthonormalised solution (the linear term fixes X, not only
+    its span); and, independently of the oracle, the unsymmetrised X^T grad f of the GPU's
+    final iterate is symmetric (eq. closed-multi)."""
+    from oracle import plam as op
+    from paper_1810_03930_gb300 import Solver
+    from workloads import paper_p2_linear, paper_p3_operator
+    n, p, beta = 200, 6, 3.0
+    A, _ = paper_p3_operator(n, rng_for(6, 0), theta=1.01, xi=1.0)
+    Gl = paper_p2_linear(n, p, rng_for(6, 2))
+    X0 = orthonormal_start(n, p, rng_for(6, 1))
+    obj = oo.QuadLinearObjective(A, Gl)
+    C0 = X0.T @ obj.grad(X0)
+    assert np.linalg.norm(C0 - C0.T) / np.linalg.norm(C0) > 1e-2
+    ref = op.solve(obj, X0, variant=variant, beta=beta, tol=1e-10, maxit=20000, record=False)
+    assert ref.converged
+    At = torch.as_tensor(A, device="cuda")
+    Gt = torch.as_tensor(Gl, device="cuda")
+
+    def energy(X):            # X: (n, p) view of the iterate
+        return 0.5 * torch.sum(X * (At @ X)) + torch.sum(Gt * X)
+    s = Solver(n, p, "callback", energy=energy, variant=variant, beta=beta, tol=1e-10,
+               maxit=20000, precision="fp64", final_orth=1)
+    Xd = to_dev(X0, s)
+    Qd = s.new_matrix(dtype=torch.float64)
+    st, info = s.solve(Xd, Qd)
+    assert st == 0 and info.converged
+    assert abs(info.iters - ref.iters) <= max(5, 0.25 * ref.iters)
+    assert abs(info.f - ref.f_stop) <= 1e-10 * max(1.0, abs(ref.f_stop))
+    Q = to_host(Qd, n)
+    assert rel_err(Q, ref.X_orth) <= 1e-7
+    assert info.feas_orth <= 1e-12
+    X = to_host(Xd, n)
+    C = X.T @ obj.grad(X)
+    assert np.linalg.norm(C - C.T) / np.linalg.norm(C) < 1e-8
+    s.close()
