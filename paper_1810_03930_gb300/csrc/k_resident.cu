@@ -293,6 +293,11 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_solve_kernel(Resident
     // ================= P2: gradient of the own rows, partial Grams
     float fy = 0.f;
     if (a.kind == kObjHartree) {
+      // the neighbours' boundary rows do not depend on the block sums: load them first,
+      // so that their L2 round trip overlaps the one of the block sums
+      float hv = 0.f;
+      if (t < p) hv = (b > 0) ? ldcg_f(a.halo + (size_t)(b - 1) * 2 * p + p + t) : 0.f;
+      else if (t < 2 * p) hv = (r0 + nr < n) ? ldcg_f(a.halo + (size_t)(b + 1) * 2 * p + t - p) : 0.f;
       float pa = 0.f, qa = 0.f;
       for (int j = t; j < a.nblk; j += kResThreads) {
         if (j < b) pa += (float)ldcg_d(a.blk + 2 * j);
@@ -311,9 +316,8 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_solve_kernel(Resident
       const float Q = Qafter + (tot_c - ic);
       const float y = ((float)(n - gi) * P + (float)(gi + 1) * Q) * (float)a.inv_np1;
       fy = block_sum_f((t < nr) ? rv * y : 0.f, fscr);
-      // neighbours' boundary rows, fetched once; alpha y of each row for all threads
-      if (t < p) halo_s[t] = (b > 0) ? ldcg_f(a.halo + (size_t)(b - 1) * 2 * p + p + t) : 0.f;
-      else if (t < 2 * p) halo_s[t] = (r0 + nr < n) ? ldcg_f(a.halo + (size_t)(b + 1) * 2 * p + t - p) : 0.f;
+      // neighbours' boundary rows; alpha y of each row for all threads
+      if (t < 2 * p) halo_s[t] = hv;
       if (t < nr) grp[t] = (float)a.alpha * y;
       __syncthreads();
       {
@@ -466,7 +470,7 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_solve_kernel(Resident
       float s1f = 0.f, s2f = 0.f;
       for (int kk2 = 0; kk2 < p; ++kk2) {
         const float bik = BU(i, kk2);
-        s1f = fmaf(bik, Ls[i * pp + kk2], s1f);
+        s1f = fmaf(bik, Ls[kk2 * pp + i], s1f);   // Psi(C) is symmetric: read along the lanes
         s2f = fmaf(bik, bik, s2f);
       }
       const float d = prm.lambda2 ? (Ws[(p + i) * p + i] - s1f + beta * (s2f - BU(i, i))) : 0.f;
