@@ -16,7 +16,7 @@ from oracle import kernels as ok
 from oracle import objectives as oo
 from oracle import plam as op
 from workloads import (gaussian_symmetric, orthonormal_start, paper_p2_linear, paper_p3_operator,
-                       rng_for, workload_dense_trace)
+                       parameter_study_problems, rng_for, workload_dense_trace)
 
 pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
 
@@ -455,3 +455,36 @@ def test_exchange_term_pins():
     hstep = 1e-5
     dd = (hx.value(X + hstep * D) - hx.value(X - hstep * D)) / (2 * hstep)
     assert abs(dd - np.sum(hx.grad(X) * D)) <= 1e-7 * max(1.0, abs(dd))
+
+
+def parameter_study_set():
+    """The seeded parameter-study problems and s = the largest ||A||_2 of the set (the Hessian
+    norm at 0 of the trace objective)."""
+    As, X0s = parameter_study_problems()
+    s = max(float(np.max(np.abs(np.linalg.eigvalsh(A)))) for A in As)
+    return As, X0s, s
+
+
+@pytest.mark.parametrize("variant", ["plam", "pcal"])
+def test_parameter_study_conclusions_on_trace_problems(variant):
+    """Section 5.1's parameter study (Figs. 'eta' and 'beta'), qualitatively, on 12 seeded trace
+    problems (n = 200, p = 8, relative KKT 1e-6): with beta = s + 0.1 the alternating BB step
+    needs the fewest iterations (median) of ABB, BB1, BB2 and the differential rule, and the
+    constant step reaches the tolerance on none within 3000 iterations; a large penalty
+    (beta = 10 s + 1) is slower than beta = s + 0.1.  (The paper's divergence of PLAM with a small
+    beta shows on its nonlinear problems, not on these.)"""
+    As, X0s, s = parameter_study_set()
+
+    def median_iters(beta, rule):
+        rs = [op.solve(oo.TraceObjective(A), X0, variant=variant, beta=beta, eta_rule=rule,
+                       tol=1e-6, maxit=3000, record=False) for A, X0 in zip(As, X0s)]
+        return float(np.median([r.iters for r in rs])), sum(not r.converged for r in rs)
+
+    med = {rule: median_iters(s + 0.1, rule) for rule in ("abb", "bb1", "bb2", "diff", "const")}
+    for rule in ("abb", "bb1", "bb2", "diff"):
+        assert med[rule][1] == 0, (rule, med[rule])
+        if rule != "abb":
+            assert med["abb"][0] < med[rule][0], med
+    assert med["const"][1] == len(As)
+    slow, _ = median_iters(10 * s + 1, "abb")
+    assert slow > 1.3 * med["abb"][0]

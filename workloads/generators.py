@@ -33,7 +33,7 @@ __all__ = [
     "gaussian_start", "uniform_potential", "paper_p3_operator", "paper_p2_linear", "Workload",
     "workload_dense_trace", "workload_hartree1d", "workload_stencil3d",
     "batched_shapes", "workload_batched_problem", "workload_by_config",
-    "workload_ks_exchange",
+    "workload_ks_exchange", "parameter_study_problems",
 ]
 
 
@@ -175,6 +175,14 @@ def workload_batched_problem(b: int, n: int, p: int, config: int = 4) -> Workloa
     X0 = orthonormal_start(n, p, rng_for(config, 1, sub=b))
     return Workload(name=f"batched_{b}_n{n}_p{p}", kind="dense", n=n, p=p, X0=X0, A=A,
                     params=dict(variant="pcal", beta=1.0, tol=1e-6))
+
+
+def parameter_study_problems(count: int = 12, n: int = 200, p: int = 8) -> tuple[list, list]:
+    """A seeded set of Problem-3-type trace problems for the parameter study of Section 5.1:
+    A_i = (B + B^T)/2 with B iid N(0, 1), orthonormal Gaussian starts (config 7, sub-stream i)."""
+    As = [gaussian_symmetric(n, rng_for(7, 0, sub=i)) for i in range(count)]
+    X0s = [orthonormal_start(n, p, rng_for(7, 1, sub=i)) for i in range(count)]
+    return As, X0s
 
 
 def workload_by_config(config: int) -> Workload:
