@@ -180,6 +180,45 @@ def test_first_twenty_step_sizes_match_oracle_fp64(variant):
     s.close()
 
 
+@pytest.mark.parametrize("rule", ["bb1", "bb2", "diff", "const"])
+@pytest.mark.parametrize("variant", ["plam", "pcal"])
+def test_first_twenty_step_sizes_match_oracle_every_rule(variant, rule):
+    """Every step-size rule of Section 5.1 (BB1, BB2, the differential rule ||Y||/||S||, the
+    constant step), pinned GPU vs oracle on identical inputs like ABB above: the FP64 path's eta,
+    KKT and f over 20 iterations; and the FP32 resident engine's own implementation of the rules
+    over the first 6 iterations (FP32 storage moves the sequence by ~1e-6 relative per step)."""
+    w = workload_dense_trace(500, 20)
+    obj = oo.TraceObjective(w.A)
+    ref = op.solve(obj, w.X0, variant=variant, beta=1.0, eta_rule=rule, tol=0.0, maxit=20)
+    eta_ref = np.array([h.eta for h in ref.history[:20]])
+    s = gpu_solver(w, "fp64", variant=variant, beta=1.0, eta_rule=rule, tol=0.0, maxit=20,
+                   final_orth=0)
+    Xd = to_dev(w.X0, s)
+    st, info = s.solve(Xd)
+    hist = s.history()
+    # the same number of records: 21, or fewer where the rule diverges (PLAM's constant step
+    # here), and then at the same iteration in both
+    assert hist.shape[0] == len(ref.history)
+    assert (st == 3) == ref.diverged
+    # values while the iterate is still bounded (a blow-up amplifies rounding differences)
+    m = 0
+    while m < len(ref.history) and ref.history[m].kkt < 1e3:
+        m += 1
+    assert m >= 5
+    mm = min(m, 20)
+    np.testing.assert_allclose(hist[:mm, 4], eta_ref[:mm], rtol=1e-9)
+    np.testing.assert_allclose(hist[:m, 2], np.array([h.kkt for h in ref.history[:m]]), rtol=1e-8)
+    np.testing.assert_allclose(hist[:m, 1], np.array([h.f for h in ref.history[:m]]), rtol=1e-11)
+    s.close()
+    r = gpu_solver(w, "fp32", variant=variant, beta=1.0, eta_rule=rule, tol=0.0, maxit=6,
+                   final_orth=0, engine="resident")
+    assert r.engine() == "resident"
+    r.solve(to_dev(w.X0, r))
+    hr = r.history()
+    np.testing.assert_allclose(hr[:6, 4], eta_ref[:6], rtol=1e-3)
+    r.close()
+
+
 # ---------------------------------------------------------------- full solves
 
 
