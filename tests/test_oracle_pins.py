@@ -488,3 +488,32 @@ def test_parameter_study_conclusions_on_trace_problems(variant):
     assert med["const"][1] == len(As)
     slow, _ = median_iters(10 * s + 1, "abb")
     assert slow > 1.3 * med["abb"][0]
+
+
+def test_multiplier_study_conclusion_on_problems_1_and_2():
+    """Section 5.3 (Fig. "PCAL_multiplier"), qualitatively: the closed-form multiplier update of
+    PLAM (eq. Lambda1) and PCAL (eq. lambda2) against dual ascent (PLAM-DA / PCAL-DA, the ALM
+    multiplier step of Algorithm 1) on 6 seeded instances each of Problem 1 (dense Gaussian L,
+    alpha = 1) and Problem 2 (the Gao et al. generator, default parameters), n = 200, p = 8,
+    beta = s + 0.1, relative KKT 1e-6, ABB.  The closed form converges on every instance and
+    its median iteration count is well below dual ascent's (which misses 3000 iterations on
+    some instances)."""
+    from workloads import multiplier_study_problems
+    p1, p2 = multiplier_study_problems()
+    cases = []
+    for L, X0 in p1:
+        obj = oo.DenseHartreeObjective(L, alpha=1.0, quad_scale=0.5)
+        cases.append(("P1", obj, obj.hess_norm_bound(), X0))
+    for A, lam, Gl, X0 in p2:
+        cases.append(("P2", oo.QuadLinearObjective(A, Gl), float(np.max(np.abs(lam))), X0))
+    for prob in ("P1", "P2"):
+        for variant, closed in (("plam", "lambda1"), ("pcal", "lambda2")):
+            its = {}
+            for rule in (closed, "da"):
+                rs = [op.solve(obj, X0, variant=variant, beta=s + 0.1, lambda_rule=rule, tol=1e-6,
+                               maxit=3000, record=False)
+                      for name, obj, s, X0 in cases if name == prob]
+                its[rule] = [r.iters if r.converged else 3000 for r in rs]
+                if rule == closed:
+                    assert all(r.converged for r in rs), (prob, variant, its)
+            assert np.median(its["da"]) >= 2.5 * np.median(its[closed]), (prob, variant, its)

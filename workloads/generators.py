@@ -33,7 +33,7 @@ __all__ = [
     "gaussian_start", "uniform_potential", "paper_p3_operator", "paper_p2_linear", "Workload",
     "workload_dense_trace", "workload_hartree1d", "workload_stencil3d",
     "batched_shapes", "workload_batched_problem", "workload_by_config",
-    "workload_ks_exchange", "parameter_study_problems",
+    "workload_ks_exchange", "parameter_study_problems", "multiplier_study_problems",
 ]
 
 
@@ -183,6 +183,24 @@ def parameter_study_problems(count: int = 12, n: int = 200, p: int = 8) -> tuple
     As = [gaussian_symmetric(n, rng_for(7, 0, sub=i)) for i in range(count)]
     X0s = [orthonormal_start(n, p, rng_for(7, 1, sub=i)) for i in range(count)]
     return As, X0s
+
+
+def multiplier_study_problems(count: int = 6, n: int = 200, p: int = 8) -> tuple[list, list]:
+    """Seeded Problem 1 and Problem 2 instances for the comparison of the closed-form multiplier
+    with dual ascent (Section 5.3, Fig. "PCAL_multiplier"), shaped as Section 5.2 states them.
+
+    Problem 1 (config 15): L = (B + B^T)/2 with B iid N(0, 1); returns (L, X0) pairs.
+    Problem 2 (config 16): A = P diag(theta^(1-i)) P^T and G = kappa Q D with the default
+    parameters kappa = 1, theta = zeta = 1.01, xi = 1; returns (A, lam, G, X0) tuples.
+    Starts are orthonormal Gaussian (stream 1 of each config, sub-stream i)."""
+    p1 = [(gaussian_symmetric(n, rng_for(15, 0, sub=i)), orthonormal_start(n, p, rng_for(15, 1, sub=i)))
+          for i in range(count)]
+    p2 = []
+    for i in range(count):
+        A, lam = paper_p3_operator(n, rng_for(16, 0, sub=i))
+        Gl = paper_p2_linear(n, p, rng_for(16, 2, sub=i))
+        p2.append((A, lam, Gl, orthonormal_start(n, p, rng_for(16, 1, sub=i))))
+    return p1, p2
 
 
 def workload_by_config(config: int) -> Workload:
