@@ -12,6 +12,15 @@
 // vanishes as the iterate converges: X E is then small against R and G, so it
 // is taken in plain TF32 while X M is compensated (3xTF32) near convergence.
 //
+// The tensor cores' FP32 accumulation truncates (round toward zero), so a long
+// sum loses up to an ulp of its running value per step.  M is dominated by its
+// diagonal (Lambda's eigenvalue-like diagonal near a solution), so the MMAs
+// take M without its diagonal and the epilogue adds X_rc M_cc in round-to-
+// nearest FP32: R = G - fma(X, diag(M), acc).  The truncated running sums then
+// carry only the off-diagonal terms, which at p = 1000 lowers the floor of the
+// relative KKT value from ~1e-6 (and ~6e-6 with a dense Lambda) to the level of
+// the CUDA-core FP32 update.
+//
 // Persistent and warp-specialised: one CTA per SM walks 128-row x N-column
 // tiles of R; its tensor memory holds two tiles' accumulators (X M, X E), so
 // the epilogue of one tile overlaps the loads and MMAs of the next.
@@ -30,8 +39,8 @@
 //                          copies; group e takes the chunks in slot e (every
 //                          other chunk), so two warps per scheduler share the
 //                          epilogue arithmetic
-// M, its TF32 remainder and E arrive from a small kernel that stores their
-// rounded TF32 parts once per iteration.
+// M (without its diagonal), its TF32 remainder, E and diag(M) arrive from a
+// small kernel that stores them once per iteration.
 //
 // Every wait is bounded; an expired wait raises *err, every role leaves its
 // loop at the same point of the protocol, the CTA lets its copies in flight
@@ -63,6 +72,7 @@ struct TcUpdateArgs {
   uint32_t pipe_bytes;     // shared memory of the K-loop stages
   double refine_switch;
   int force3;
+  const float* mdiag;      // M_cc, c < p (FP32), added by the epilogue
 };
 
 // Sum of v[0..47] over the 32 lanes of a warp by recursive halving (48
@@ -370,7 +380,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
             float xx = 0.f, xrv = 0.f, rr = 0.f;
             if (row_ok && col < a.p) {
               const float x = Xs[c * kUpM + et], g = Gs[c * kUpM + et];
-              const float rv = g - __uint_as_float(v1[c]);
+              const float rv = g - fmaf(x, __ldg(a.mdiag + col), __uint_as_float(v1[c]));
               const float kv = rv - __uint_as_float(v2[c]);
               R[r + (int64_t)col * a.ldr] = rv;
               xx = x * x;
@@ -471,9 +481,10 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   }
 }
 
-// TF32 parts of M and of E = Psi(C) - M (p x p, column-major, leading
-// dimension p in the solver's buffers) into three planes of leading dimension
-// ldm: M hi = RN_tf32(M), M lo = RN_tf32(M - M hi), E hi = RN_tf32(E).
+// TF32 parts of M without its diagonal (M' = M - Diag(M)) and of E = Psi(C) - M
+// (p x p, column-major, leading dimension p in the solver's buffers) into three
+// planes of leading dimension ldm: M' hi = RN_tf32(M'), M' lo = RN_tf32(M' - M' hi),
+// E hi = RN_tf32(E); the fourth plane starts with diag(M) in FP32.
 __global__ void tc_split_m_kernel(int p, const float* __restrict__ Mt, const float* __restrict__ L0t,
                                   int ldm, float* __restrict__ out, const DevState* __restrict__ st) {
   if (st != nullptr && st->stop != kRunning) return;
@@ -481,11 +492,13 @@ __global__ void tc_split_m_kernel(int p, const float* __restrict__ Mt, const flo
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p * p; i += gridDim.x * blockDim.x) {
     const int r = i % p, c = i / p;
     const float m = Mt[i];
-    const float mh = __uint_as_float(tf32_rna(m));
+    const float mo = (r == c) ? 0.f : m;
+    const float mh = __uint_as_float(tf32_rna(mo));
     const size_t o = (size_t)c * ldm + r;
     out[o] = mh;
-    out[plane + o] = __uint_as_float(tf32_rna(m - mh));
+    out[plane + o] = __uint_as_float(tf32_rna(mo - mh));
     out[2 * plane + o] = __uint_as_float(tf32_rna(L0t[i] - m));
+    if (r == c) out[3 * plane + c] = m;
   }
 }
 
@@ -544,6 +557,7 @@ cudaError_t launch_tc_update(int64_t n, int p, const float* X, int64_t ldx, cons
   a.R0 = R0; a.R1 = R1; a.ldr = ldr;
   a.coef = coef; a.st = st; a.colpart = colpart; a.totpart = totpart; a.err = err;
   a.pipe_bytes = pl.pipe_bytes; a.refine_switch = refine_switch; a.force3 = force3;
+  a.mdiag = msplit + 3 * plane;
   cudaError_t e = cudaFuncSetAttribute(tc_update_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
   if (e != cudaSuccess) return e;
