@@ -77,7 +77,11 @@ enum { PLAM_PREC_FP64 = 0, PLAM_PREC_FP32 = 1 };
  *   DENSE      f = 1/2 tr(X^T A X), A symmetric n x n              (Problem 3)
  *   HARTREE1D  f = q tr(X^T L X) + (alpha/4) rho^T L^{-1} rho     (Problem 1, KS form eq. KS-energy;
  *                  - (3 xc / 4) sum rho^{4/3}                      with xc: Problem 6's exchange)
- *              rho = diag(X X^T), L = tridiag(-1,2,-1) Dirichlet
+ *                  + tr(G_lin^T X)                                 (with lin: Problem 2's linear term)
+ *              rho = diag(X X^T), L = tridiag(-1,2,-1) Dirichlet, or with block = b > 0 the
+ *              block-diagonal Diag(L_1, ..., L_s) of such matrices on b consecutive rows each
+ *              (the last on the n - (s-1) b rows left): Section 5.4 runs Problem 1 with b = 5
+ *              and Problem 2 as q = 1/2, alpha = 0, A = L with a random G_lin
  *   STENCIL3D  f = 1/2 tr(X^T (L3 + Diag(V)) X), L3 the 7-point Dirichlet
  *              Laplacian on nx*ny*nz points, index i = x + nx*(y + ny*z);
  *              nx*ny*nz must equal n and stay below 2^31.
@@ -141,6 +145,14 @@ typedef struct {
   void* grad_ctx;       /* CALLBACK: passed to grad unchanged */
   double xc;            /* HARTREE1D: exchange coefficient gamma of Problem 6, adding
                            -(3 gamma / 4) sum_i rho_i^{4/3} (0: none; the resident engine needs 0) */
+  int64_t block;        /* HARTREE1D: rows per Dirichlet block of L; 0 (or >= n): one block of n rows.
+                           With alpha or xc nonzero a block must have 1..64 rows (PLAM_ERR_INVALID
+                           otherwise: L^{-1} rho is then formed block by block in shared memory) */
+  const void* lin;      /* HARTREE1D: device n x p linear term G_lin (storage type, column-major,
+                           leading dimension ldlin >= n, referenced like A), or NULL.  block != 0 or
+                           lin != NULL selects the row-tile x column-group gradient kernels and
+                           rules out the resident engine */
+  int64_t ldlin;        /* HARTREE1D: leading dimension of lin */
 } plam_objective_t;
 
 typedef struct {

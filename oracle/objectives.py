@@ -17,6 +17,8 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
                      Laplacian on an m^3 grid (6 on the diagonal, -1 per
                      neighbour), built as a Kronecker sum of 1D tridiagonals;
                      lexicographic index i = x + m y + m^2 z.
+                     With `block` L is block-diagonal and `lin` adds Problem 2's
+                     linear term tr(G_lin^T X) (Section 5.4's parallel workloads).
   QuadLinearObjective Problem 2 (eq. OCQP): f = 1/2 tr(X^T A X) + tr(G^T X).
   DenseHartreeObjective Problem 1 exactly (eq. nonlinear): dense symmetric L and
                      its pseudo-inverse L^+ (numpy.linalg.pinv), coefficient q.
@@ -65,35 +67,61 @@ class QuadLinearObjective:
         return self.A @ X + self.Glin
 
 
-def laplacian_1d_banded(n: int) -> np.ndarray:
-    """The 3 x n band storage of tridiag(-1, 2, -1) for scipy.linalg.solve_banded."""
-    ab = np.empty((3, n))
-    ab[0, :] = -1.0
+def laplacian_1d_coupled(n: int, block: int = 0) -> np.ndarray:
+    """c[i] = True where rows i and i + 1 are coupled by the off-diagonal -1 of L (length n - 1).
+
+    block = 0: L = tridiag(-1, 2, -1) over all n rows.  block = b > 0: L = Diag(L_1, ..., L_s)
+    with every L_j that tridiagonal matrix on b consecutive rows (the last one on the n - (s-1) b
+    rows left), the block-diagonal Laplacian of Section 5.4's Problem 1; rows b j - 1 and b j
+    are then not coupled."""
+    c = np.ones(max(n - 1, 0), dtype=bool)
+    if block > 0:
+        c[block - 1::block] = False
+    return c
+
+
+def laplacian_1d_banded(n: int, block: int = 0) -> np.ndarray:
+    """The 3 x n band storage of L (see laplacian_1d_coupled) for scipy.linalg.solve_banded."""
+    c = laplacian_1d_coupled(n, block)
+    ab = np.zeros((3, n))
+    ab[0, 1:] = np.where(c, -1.0, 0.0)      # superdiagonal: ab[0, j] = L[j-1, j]
     ab[1, :] = 2.0
-    ab[2, :] = -1.0
+    ab[2, :-1] = np.where(c, -1.0, 0.0)     # subdiagonal: ab[2, j] = L[j+1, j]
     return ab
 
 
-def laplacian_1d_apply(X: np.ndarray) -> np.ndarray:
-    """L X for L = tridiag(-1, 2, -1) with zero (Dirichlet) values outside."""
+def laplacian_1d_apply(X: np.ndarray, block: int = 0) -> np.ndarray:
+    """L X for L = tridiag(-1, 2, -1) with zero (Dirichlet) values outside each block."""
     Y = 2.0 * X
-    Y[1:] -= X[:-1]
-    Y[:-1] -= X[1:]
+    c = laplacian_1d_coupled(X.shape[0], block)
+    if X.ndim == 1:
+        Y[1:] -= np.where(c, X[:-1], 0.0)
+        Y[:-1] -= np.where(c, X[1:], 0.0)
+    else:
+        Y[1:] -= np.where(c[:, None], X[:-1], 0.0)
+        Y[:-1] -= np.where(c[:, None], X[1:], 0.0)
     return Y
 
 
 class HartreeObjective:
-    """f = q tr(X^T L X) + (alpha/4) rho^T L^{-1} rho - (3 xc/4) sum_i rho_i^{4/3}, rho = diag(X X^T).
+    """f = q tr(X^T L X) + (alpha/4) rho^T L^{-1} rho - (3 xc/4) sum_i rho_i^{4/3} + tr(G_lin^T X),
+    rho = diag(X X^T).
 
-    The last term is Problem 6's exchange energy (Section 5.2, gamma = xc); its gradient
-    follows from d rho_i / d X_ij = 2 X_ij: -(3 xc/4)(4/3) rho_i^{1/3} 2 X_ij = -2 xc rho_i^{1/3} X_ij."""
+    The third term is Problem 6's exchange energy (Section 5.2, gamma = xc); its gradient
+    follows from d rho_i / d X_ij = 2 X_ij: -(3 xc/4)(4/3) rho_i^{1/3} 2 X_ij = -2 xc rho_i^{1/3} X_ij.
+    `block` makes L block-diagonal (laplacian_1d_coupled) and `lin` adds the linear term of
+    Problem 2 (gradient + G_lin): Section 5.4 runs Problem 1 with blocks of 5 rows and Problem 2
+    with the tridiagonal A = L and a random G_lin (q = 1/2, alpha = 0)."""
 
-    def __init__(self, n: int, alpha: float = 1.0, quad_scale: float = 0.25, xc: float = 0.0):
+    def __init__(self, n: int, alpha: float = 1.0, quad_scale: float = 0.25, xc: float = 0.0,
+                 block: int = 0, lin: np.ndarray | None = None):
         self.n = int(n)
         self.alpha = float(alpha)
         self.q = float(quad_scale)
         self.xc = float(xc)
-        self._ab = laplacian_1d_banded(self.n)
+        self.block = int(block)
+        self.lin = None if lin is None else np.asarray(lin, dtype=np.float64)
+        self._ab = laplacian_1d_banded(self.n, self.block)
 
     def density(self, X):
         return np.sum(X * X, axis=1)
@@ -105,14 +133,20 @@ class HartreeObjective:
     def value(self, X):
         rho = self.density(X)
         y = self.hartree_potential(rho)
-        return (self.q * float(np.sum(X * laplacian_1d_apply(X))) + 0.25 * self.alpha * float(rho @ y)
-                - 0.75 * self.xc * float(np.sum(np.cbrt(rho) * rho)))
+        f = (self.q * float(np.sum(X * laplacian_1d_apply(X, self.block)))
+             + 0.25 * self.alpha * float(rho @ y) - 0.75 * self.xc * float(np.sum(np.cbrt(rho) * rho)))
+        if self.lin is not None:
+            f += float(np.sum(self.lin * X))
+        return f
 
     def grad(self, X):
         rho = self.density(X)
         y = self.hartree_potential(rho)
-        return (2.0 * self.q * laplacian_1d_apply(X) + self.alpha * (y[:, None] * X)
-                - 2.0 * self.xc * (np.cbrt(rho)[:, None] * X))
+        G = (2.0 * self.q * laplacian_1d_apply(X, self.block) + self.alpha * (y[:, None] * X)
+             - 2.0 * self.xc * (np.cbrt(rho)[:, None] * X))
+        if self.lin is not None:
+            G = G + self.lin
+        return G
 
     def hess_norm_bound(self):
         """Upper bound of ||grad^2 f(0)||_2 = 2 q ||L||_2 <= 8 q (the Hartree part vanishes at 0)."""
@@ -174,7 +208,8 @@ def objective_for(w) -> object:
     if w.kind == "dense":
         return TraceObjective(w.A)
     if w.kind == "hartree1d":
-        return HartreeObjective(w.n, w.alpha, w.quad_scale, getattr(w, "xc", 0.0) or 0.0)
+        return HartreeObjective(w.n, w.alpha, w.quad_scale, getattr(w, "xc", 0.0) or 0.0,
+                                getattr(w, "block", 0) or 0, getattr(w, "lin", None))
     if w.kind == "stencil3d":
         return Stencil3DObjective(w.m, w.V)
     raise ValueError(w.kind)

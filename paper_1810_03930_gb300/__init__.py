@@ -107,7 +107,8 @@ class Solver:
     n x p matrix (ld = leading dimension >= n).
     """
 
-    def __init__(self, n, p, kind, *, A=None, alpha=1.0, quad_scale=0.25, xc=0.0, grid=None, V=None,
+    def __init__(self, n, p, kind, *, A=None, alpha=1.0, quad_scale=0.25, xc=0.0, block=0, lin=None,
+                 grid=None, V=None,
                  variant="pcal", lambda_rule="lambda2", beta=1.0, eta_rule="abb", eta0=0.0,
                  eta_gamma=0.0, tol=1e-8, maxit=3000, precision="fp64", final_orth=1,
                  graph_iters=16, engine="auto", tensor_cores="auto", refine_switch=1e-3,
@@ -142,6 +143,11 @@ class Solver:
         elif kind == "hartree1d":
             obj.kind, obj.alpha, obj.quad_scale = PLAM_OBJ_HARTREE1D, float(alpha), float(quad_scale)
             obj.xc = float(xc)
+            obj.block = int(block)
+            if lin is not None:
+                Lt = lin if isinstance(lin, torch.Tensor) else colmajor_to_device(lin, self.dtype)
+                self._keep.append(Lt)
+                obj.lin, obj.ldlin = Lt.data_ptr(), Lt.stride(0)
         elif kind == "stencil3d":
             nx, ny, nz = grid
             obj.kind, obj.nx, obj.ny, obj.nz = PLAM_OBJ_STENCIL3D, nx, ny, nz

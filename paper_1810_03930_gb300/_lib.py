@@ -51,7 +51,8 @@ class plam_objective_t(C.Structure):
     _fields_ = [("kind", C.c_int), ("A", C.c_void_p), ("lda", C.c_int64), ("alpha", C.c_double),
                 ("quad_scale", C.c_double), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("V", C.c_void_p), ("grad", plam_grad_fn), ("grad_ctx", C.c_void_p),
-                ("xc", C.c_double)]
+                ("xc", C.c_double), ("block", C.c_int64), ("lin", C.c_void_p),
+                ("ldlin", C.c_int64)]
 
 
 class plam_batch_problem_t(C.Structure):

@@ -16,6 +16,8 @@
 //   preceding / following blocks in a fixed order, scans inside its block,
 //   forms y and writes G and the block's share of rho^T y (for f).  rho, y and
 //   the scans are double (O(n) work); G is computed in the storage type.
+// chain kernels         the same 1D objective with a block-diagonal L and Problem 2's linear
+//                       term (Section 5.4), over row tiles x column groups (see below).
 // stencil_grad_kernel   G = (L3 + Diag(V)) X, L3 the 7-point Dirichlet
 //                       Laplacian (6 on the diagonal, -1 per neighbour inside
 //                       the grid), index i = x + nx (y + ny z).
@@ -187,6 +189,144 @@ hartree_grad_kernel(int64_t n, int p, double alpha, double q, double xc, double 
     const T lx = (x + x) - xm - xp;
     G[r + (int64_t)cc * ldg] = fma(q2, lx, ty * x);
   }
+}
+
+// ---------------------------------------------------------------- 1D, block-diagonal L, linear term
+//
+// The parallel forms of Problems 1 and 2 in Section 5.4:
+//   f = q tr(X^T L X) + (alpha/4) rho^T L^{-1} rho - (3 xc/4) sum rho^{4/3} + tr(G_lin^T X),
+//   L = Diag(L_1, ..., L_s), every L_j = tridiag(-1, 2, -1) on `block` rows (the last one on the
+//   rows left; block = 0: one block of n rows), G = 2q L X + Diag(alpha y - 2 xc rho^{1/3}) X + G_lin.
+// Inside a block of m rows the Dirichlet inverse is (L_j^{-1})_uv = min(u,v)(m+1-max(u,v))/(m+1)
+// (1-based positions), so for blocks of at most kChainMaxBlock rows y = L^{-1} rho is a direct sum
+// over the block in shared memory.  The grid is row tiles x column groups, sized to about eight
+// CTAs per SM; when y is needed a tile holds whole blocks (kChainTile rows rounded down to a
+// multiple of the block), so no CTA reads rho of rows outside its tile.
+//   chain_density_kernel  the column group's share of rho_r = sum_c X_rc^2 (storage type, stored
+//                         as double), for every row
+//   chain_grad_kernel     rho (the groups' shares added in group order), y and the row scale of
+//                         its tile; G of its tile and column group; its f partial
+//                         -(alpha/4) rho^T y + (xc/4) sum rho^{4/3} (column group 0) + 1/2 <G_lin, X>,
+//                         so that f = 1/2 <X, G> + (sum of the partials).
+
+constexpr int kChainTile = 256;
+constexpr int kChainTargetCtas = 8 * 152;
+
+ChainPlan chain_plan(int64_t n, int p, int64_t block, bool need_y) {
+  ChainPlan c;
+  c.tile = (need_y && block > 0) ? (int)((kChainTile / block) * block) : kChainTile;
+  c.ntiles = (int)((n + c.tile - 1) / c.tile);
+  const int64_t want = (kChainTargetCtas + (int64_t)c.ntiles - 1) / c.ntiles;
+  const int ncg = (int)std::max<int64_t>(1, std::min<int64_t>(p, want));
+  c.cw = (p + ncg - 1) / ncg;
+  c.ncg = (p + c.cw - 1) / c.cw;
+  return c;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kChainTile)
+chain_density_kernel(int64_t n, int p, int tile, int cw, const T* __restrict__ X, int64_t ldx,
+                     double* __restrict__ rho_part, const DevState* __restrict__ st) {
+  if (st != nullptr && st->stop != kRunning) return;
+  const int t = threadIdx.x;
+  const int64_t r = (int64_t)blockIdx.x * tile + t;
+  if (t >= tile || r >= n) return;
+  const int g = blockIdx.y;
+  const int c0 = g * cw, c1 = min(p, c0 + cw);
+  T s = T(0);
+  for (int c = c0; c < c1; ++c) {
+    const T x = X[r + (int64_t)c * ldx];
+    s = fma(x, x, s);
+  }
+  rho_part[(int64_t)g * n + r] = (double)s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kChainTile)
+chain_grad_kernel(int64_t n, int p, int64_t block, int tile, int cw, int ncg, double alpha,
+                  double q, double xc, const T* __restrict__ X, int64_t ldx,
+                  const T* __restrict__ lin, int64_t ldl, T* __restrict__ G, int64_t ldg,
+                  const double* __restrict__ rho_part, double* __restrict__ fpart,
+                  const DevState* __restrict__ st) {
+  if (st != nullptr && st->stop != kRunning) return;
+  __shared__ double rho_s[kChainTile];
+  __shared__ double scratch[33];
+  const int t = threadIdx.x;
+  const int64_t r0 = (int64_t)blockIdx.x * tile;
+  const int64_t r = r0 + t;
+  const bool row = t < tile && r < n;
+  const int g = blockIdx.y;
+  double scale = 0.0, fr = 0.0;
+  if (alpha != 0.0 || xc != 0.0) {          // the same for every thread of the launch
+    double rv = 0.0;
+    if (row)
+      for (int gg = 0; gg < ncg; ++gg) rv += rho_part[(int64_t)gg * n + r];
+    rho_s[t] = rv;
+    __syncthreads();
+    if (row) {
+      double y = 0.0;
+      if (alpha != 0.0) {
+        // the block of row r lies inside this tile (the tile is a multiple of the block)
+        const int64_t bs = (r / block) * block;
+        const int m = (int)(min(n, bs + block) - bs);
+        const int u = (int)(r - bs) + 1;
+        const double* rb = rho_s + (bs - r0);
+        double acc = 0.0;
+        for (int v = 1; v <= m; ++v) {
+          const int lo = min(u, v), hi = max(u, v);
+          acc += (double)(lo * (m + 1 - hi)) * rb[v - 1];
+        }
+        y = acc / (double)(m + 1);
+      }
+      const double c3 = (xc != 0.0) ? cbrt(rv) : 0.0;
+      scale = alpha * y - 2.0 * xc * c3;
+      if (g == 0) fr = -0.25 * alpha * rv * y + 0.25 * xc * rv * c3;
+    }
+  }
+  if (row) {
+    const bool has_m = (block > 0) ? (r % block != 0) : (r > 0);
+    const bool has_p = (r + 1 < n) && ((block > 0) ? ((r + 1) % block != 0) : true);
+    const T ts = (T)scale;
+    const T q2 = (T)(2.0 * q);
+    const int c0 = g * cw, c1 = min(p, c0 + cw);
+    T fl = T(0);
+    for (int c = c0; c < c1; ++c) {
+      const T* xcol = X + (int64_t)c * ldx;
+      const T x = xcol[r];
+      const T xm = has_m ? xcol[r - 1] : T(0);
+      const T xp = has_p ? xcol[r + 1] : T(0);
+      T gv = fma(q2, (x + x) - xm - xp, ts * x);
+      if (lin != nullptr) {
+        const T l = lin[r + (int64_t)c * ldl];
+        gv += l;
+        fl = fma(l, x, fl);
+      }
+      G[r + (int64_t)c * ldg] = gv;
+    }
+    fr += 0.5 * (double)fl;
+  }
+  const double fs = block_sum(fr, scratch);
+  if (t == 0 && fpart != nullptr) fpart[(int64_t)blockIdx.x * ncg + g] = fs;
+}
+
+template <typename T>
+cudaError_t launch_chain_grad(int64_t n, int p, int64_t block, double alpha, double q, double xc,
+                              const T* X, int64_t ldx, const T* lin, int64_t ldl, T* G,
+                              int64_t ldg, double* rho_part, double* fpart, const DevState* st,
+                              cudaStream_t s, int* launches) {
+  const ChainPlan c = chain_plan(n, p, block, alpha != 0.0);
+  const dim3 grid((unsigned)c.ntiles, (unsigned)c.ncg);
+  *launches = 0;
+  if (alpha != 0.0 || xc != 0.0) {
+    chain_density_kernel<T><<<grid, kChainTile, 0, s>>>(n, p, c.tile, c.cw, X, ldx, rho_part, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    *launches += 1;
+  }
+  chain_grad_kernel<T><<<grid, kChainTile, 0, s>>>(n, p, block, c.tile, c.cw, c.ncg, alpha, q, xc,
+                                                    X, ldx, lin, ldl, G, ldg, rho_part, fpart, st);
+  *launches += 1;
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- 3D stencil
@@ -395,6 +535,10 @@ cudaError_t preload_objective_kernels() {
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, hartree_density_kernel<double>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, hartree_grad_kernel<float>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, hartree_grad_kernel<double>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, chain_density_kernel<float>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, chain_density_kernel<double>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, chain_grad_kernel<float>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, chain_grad_kernel<double>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, stencil_grad_kernel<float>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, stencil_grad_kernel<double>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, stencil_grad_vec_kernel<float>);
@@ -408,6 +552,9 @@ cudaError_t preload_objective_kernels() {
   template cudaError_t launch_hartree_grad<T>(int64_t, int, double, double, double, const T*, int64_t, \
                                               T*, int64_t, double*, double*, double*, double*,    \
                                               const DevState*, cudaStream_t);                     \
+  template cudaError_t launch_chain_grad<T>(int64_t, int, int64_t, double, double, double, const T*, \
+                                            int64_t, const T*, int64_t, T*, int64_t, double*,     \
+                                            double*, const DevState*, cudaStream_t, int*);       \
   template cudaError_t launch_stencil_grad<T>(int, int, int, int, const T*, const T*, int64_t, T*, \
                                               int64_t, const DevState*, cudaStream_t);
 PLAM_INST(float)

@@ -3,11 +3,12 @@
 //     B = R^T R  (Cholesky, R upper triangular, diag(R) > 0),
 //     Q = X R^{-1}.
 //
-// cholesky_inverse_kernel (one CTA, double): right-looking Cholesky of the
-// upper triangle of B in a p x p work matrix, then the columns of Z = R^{-1}
-// by back substitution (one thread per column); for p <= 96 the same steps run
-// in shared memory (cholesky_inverse_smem_kernel).  A pivot that is not positive
-// and finite stops the factorisation and reports 1 + its index in *info.
+// For p <= 96 (cholesky_inverse_smem_kernel, one CTA, double): right-looking
+// Cholesky of the upper triangle of B in shared memory, then the columns of
+// Z = R^{-1} by back substitution (one thread per column).  Larger p: the same
+// factorisation blocked on 32 x 32 tiles over many CTAs (see below).  A pivot
+// that is not positive and finite stops the factorisation and reports 1 + its
+// index in *info.
 // apply_rinv_kernel: Q = X Z over 64 x 64 output tiles, double arithmetic
 // (float inputs are converted exactly), Z upper triangular so column c only
 // needs rows k <= c.
@@ -15,54 +16,163 @@
 
 namespace plam {
 
+// ---- blocked factorisation and inverse for p > kCholSmemMaxP, on 32 x 32 blocks
+// over many CTAs (one launch per step; an earlier failure, recorded in *info,
+// turns the later launches into no-ops).  For block column j (rows j0 .. j1-1):
+//   chol_diag_kernel    R_jj = chol(W_jj) and its inverse Z_jj = R_jj^{-1} (the
+//                       diagonal block of Z), both in shared memory
+//   chol_row_kernel     the row panel R[j, k] = R_jj^{-T} W[j, k] = Z_jj^T W[j, k], k >= j1
+//   chol_update_kernel  the trailing upper triangle W[i, k] -= R[j, i]^T R[j, k],
+//                       j1 <= i <= k, on upper-triangle tiles
+// then Z = R^{-1} by block rows from the bottom (rinv_row_kernel):
+//   Z[b, c] = -Z_bb sum_{b < l <= c} R[b, l] Z[l, c]   (block rows below b are final).
+// Only the upper triangle of W is read; Z is zero below its diagonal.
+
+constexpr int kCB = 32;
+
 __global__ void __launch_bounds__(1024)
-cholesky_inverse_kernel(int p, const double* __restrict__ B, double* __restrict__ W,
-                        double* __restrict__ Z, int* __restrict__ info) {
+chol_diag_kernel(int p, int j0, double* __restrict__ W, double* __restrict__ Z,
+                 int* __restrict__ info) {
+  __shared__ double A[kCB][kCB + 1];
+  __shared__ double Zi[kCB][kCB + 1];
   __shared__ int fail;
-  __shared__ double piv;
-  const int t = threadIdx.x, nt = blockDim.x;
-  for (int e = t; e < p * p; e += nt) W[e] = B[e];
+  if (*(volatile int*)info != 0) return;
+  const int t = threadIdx.x;
+  const int r = t & 31, c = t >> 5;
+  const int nb = min(kCB, p - j0);
+  A[r][c] = (r < nb && c < nb) ? W[(j0 + r) + (size_t)(j0 + c) * p] : 0.0;
   if (t == 0) fail = 0;
   __syncthreads();
-  for (int j = 0; j < p; ++j) {
+  for (int j = 0; j < nb; ++j) {
     if (t == 0) {
-      const double d = W[j + (size_t)j * p];
-      if (!(d > 0.0) || !isfinite(d)) {
-        fail = j + 1;
-        piv = 1.0;
-      } else {
-        piv = sqrt(d);
-        W[j + (size_t)j * p] = piv;
-      }
+      const double d = A[j][j];
+      if (!(d > 0.0) || !isfinite(d)) fail = j0 + j + 1;
+      else A[j][j] = sqrt(d);
     }
     __syncthreads();
     if (fail) break;
-    const double inv = 1.0 / piv;
-    for (int k = j + 1 + t; k < p; k += nt) W[j + (size_t)k * p] *= inv;   // row j of R
+    if (r == j && c > j && c < nb) A[j][c] = A[j][c] / A[j][j];
     __syncthreads();
-    // trailing update of the upper triangle: W[i,k] -= R[j,i] R[j,k], j < i <= k
-    const int m = p - j - 1;
-    const long long tri = (long long)m * (m + 1) / 2;
-    for (long long e = t; e < tri; e += nt) {
-      // decode e -> (a, b) with 0 <= a <= b < m, column-major over b
-      int b = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
-      while ((long long)b * (b + 1) / 2 > e) --b;
-      while ((long long)(b + 1) * (b + 2) / 2 <= e) ++b;
-      const int a = (int)(e - (long long)b * (b + 1) / 2);
-      const int i = j + 1 + a, k = j + 1 + b;
-      W[i + (size_t)k * p] -= W[j + (size_t)i * p] * W[j + (size_t)k * p];
-    }
+    if (r > j && c >= r && c < nb) A[r][c] -= A[j][r] * A[j][c];
     __syncthreads();
   }
-  if (t == 0) *info = fail;
-  if (fail) return;
-  // Z = R^{-1}: column c solves R z = e_c for z_i, i <= c
-  for (int c = t; c < p; c += nt) {
-    for (int i = p - 1; i > c; --i) Z[i + (size_t)c * p] = 0.0;
-    for (int i = c; i >= 0; --i) {
-      double s = (i == c) ? 1.0 : 0.0;
-      for (int k = i + 1; k <= c; ++k) s -= W[i + (size_t)k * p] * Z[k + (size_t)c * p];
-      Z[i + (size_t)c * p] = s / W[i + (size_t)i * p];
+  if (fail) {
+    if (t == 0) *info = fail;
+    return;
+  }
+  if (t < nb) {   // column t of R_jj^{-1} by back substitution
+    for (int i = nb - 1; i > t; --i) Zi[i][t] = 0.0;
+    for (int i = t; i >= 0; --i) {
+      double v = (i == t) ? 1.0 : 0.0;
+      for (int k = i + 1; k <= t; ++k) v -= A[i][k] * Zi[k][t];
+      Zi[i][t] = v / A[i][i];
+    }
+  }
+  __syncthreads();
+  if (r < nb && c < nb) {
+    W[(j0 + r) + (size_t)(j0 + c) * p] = (r <= c) ? A[r][c] : 0.0;
+    Z[(j0 + r) + (size_t)(j0 + c) * p] = (r <= c) ? Zi[r][c] : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+chol_row_kernel(int p, int j0, double* __restrict__ W, const double* __restrict__ Z,
+                const int* __restrict__ info) {
+  __shared__ double Zs[kCB][kCB + 1];
+  __shared__ double Ws[kCB][kCB + 1];
+  if (*(volatile const int*)info != 0) return;
+  const int nb = min(kCB, p - j0), j1 = j0 + nb;
+  const int k0 = j1 + (int)blockIdx.x * kCB;
+  const int nk = min(kCB, p - k0);
+  const int t = threadIdx.x;
+  for (int e = t; e < kCB * kCB; e += 256) {
+    const int m = e & 31, l = e >> 5;
+    Zs[m][l] = (m < nb && l < nb) ? Z[(j0 + m) + (size_t)(j0 + l) * p] : 0.0;
+    Ws[m][l] = (m < nb && l < nk) ? W[(j0 + m) + (size_t)(k0 + l) * p] : 0.0;
+  }
+  __syncthreads();
+  for (int e = t; e < kCB * kCB; e += 256) {
+    const int l = e & 31, kk = e >> 5;
+    if (l < nb && kk < nk) {
+      double v = 0.0;
+      for (int m = 0; m <= l; ++m) v += Zs[m][l] * Ws[m][kk];
+      W[(j0 + l) + (size_t)(k0 + kk) * p] = v;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256)
+chol_update_kernel(int p, int j0, double* __restrict__ W, const int* __restrict__ info) {
+  __shared__ double Ri[kCB][kCB + 1];
+  __shared__ double Rk[kCB][kCB + 1];
+  const int ti = blockIdx.x, tk = blockIdx.y;
+  if (ti > tk || *(volatile const int*)info != 0) return;
+  const int nb = min(kCB, p - j0), j1 = j0 + nb;
+  const int i0 = j1 + ti * kCB, k0 = j1 + tk * kCB;
+  const int ni = min(kCB, p - i0), nk = min(kCB, p - k0);
+  const int t = threadIdx.x;
+  for (int e = t; e < kCB * kCB; e += 256) {
+    const int l = e & 31, a = e >> 5;
+    Ri[l][a] = (l < nb && a < ni) ? W[(j0 + l) + (size_t)(i0 + a) * p] : 0.0;
+    Rk[l][a] = (l < nb && a < nk) ? W[(j0 + l) + (size_t)(k0 + a) * p] : 0.0;
+  }
+  __syncthreads();
+  const int a = t & 31;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int b = (t >> 5) + 8 * v;
+    if (a < ni && b < nk && (ti < tk || a <= b)) {
+      double acc = 0.0;
+      for (int l = 0; l < nb; ++l) acc += Ri[l][a] * Rk[l][b];
+      W[(i0 + a) + (size_t)(k0 + b) * p] -= acc;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256)
+rinv_row_kernel(int p, int bi, const double* __restrict__ W, double* __restrict__ Z,
+                const int* __restrict__ info) {
+  __shared__ double Rs[kCB][kCB + 1];
+  __shared__ double Zs[kCB][kCB + 1];
+  __shared__ double Ts[kCB][kCB + 1];
+  if (*(volatile const int*)info != 0) return;
+  const int bk = bi + 1 + (int)blockIdx.x;
+  const int i0 = bi * kCB, ni = min(kCB, p - i0);
+  const int k0 = bk * kCB, nk = min(kCB, p - k0);
+  const int t = threadIdx.x, a = t & 31;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int bl = bi + 1; bl <= bk; ++bl) {
+    const int l0 = bl * kCB, nl = min(kCB, p - l0);
+    __syncthreads();
+    for (int e = t; e < kCB * kCB; e += 256) {
+      const int x = e & 31, y = e >> 5;
+      Rs[x][y] = (x < ni && y < nl) ? W[(i0 + x) + (size_t)(l0 + y) * p] : 0.0;
+      Zs[x][y] = (x < nl && y < nk) ? Z[(l0 + x) + (size_t)(k0 + y) * p] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int b = (t >> 5) + 8 * v;
+      double sum = acc[v];
+      for (int l = 0; l < kCB; ++l) sum += Rs[a][l] * Zs[l][b];
+      acc[v] = sum;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < 4; ++v) Ts[a][(t >> 5) + 8 * v] = acc[v];
+  for (int e = t; e < kCB * kCB; e += 256) {
+    const int x = e & 31, y = e >> 5;
+    Rs[x][y] = (x < ni && y < ni) ? Z[(i0 + x) + (size_t)(i0 + y) * p] : 0.0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int b = (t >> 5) + 8 * v;
+    if (a < ni && b < nk) {
+      double sum = 0.0;
+      for (int m = a; m < ni; ++m) sum += Rs[a][m] * Ts[m][b];
+      Z[(i0 + a) + (size_t)(k0 + b) * p] = -sum;
     }
   }
 }
@@ -226,8 +336,29 @@ cudaError_t launch_cholesky_inverse(int p, const double* B, double* W, double* Z
     cholesky_inverse_smem_kernel<<<1, 1024, smem, s>>>(p, B, W, Z, info);
     return cudaGetLastError();
   }
-  cholesky_inverse_kernel<<<1, 1024, 0, s>>>(p, B, W, Z, info);
+  cudaError_t e = cudaMemcpyAsync(W, B, (size_t)p * p * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(Z, 0, (size_t)p * p * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(info, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  const int nbt = (p + kCB - 1) / kCB;
+  for (int jb = 0; jb < nbt; ++jb) {
+    const int j0 = jb * kCB;
+    chol_diag_kernel<<<1, 1024, 0, s>>>(p, j0, W, Z, info);
+    const int rest = nbt - 1 - jb;   // block columns to the right
+    if (rest > 0) {
+      chol_row_kernel<<<rest, 256, 0, s>>>(p, j0, W, Z, info);
+      chol_update_kernel<<<dim3(rest, rest), 256, 0, s>>>(p, j0, W, info);
+    }
+  }
+  for (int bi = nbt - 2; bi >= 0; --bi)
+    rinv_row_kernel<<<nbt - 1 - bi, 256, 0, s>>>(p, bi, W, Z, info);
   return cudaGetLastError();
+}
+
+int cholesky_inverse_launches(int p) {
+  if (p <= kCholSmemMaxP) return 1;
+  const int nbt = (p + kCB - 1) / kCB;
+  return nbt + 2 * (nbt - 1) + (nbt - 1);
 }
 
 template <typename T>

@@ -183,6 +183,11 @@ plam_status_t validate_params(const plam_params_t* prm) {
 
 bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 
+// The 1D objective with a block-diagonal L or a linear term runs on the chain kernels.
+bool chain_objective(const plam_handle_s* h) {
+  return h->obj.kind == PLAM_OBJ_HARTREE1D && (h->obj.block != 0 || h->obj.lin != nullptr);
+}
+
 // f = f_xg <X, grad f> + f_part (sum of the objective's f partials): 1/2 <X, A X>
 // for the quadratic objectives; the Hartree term enters through its partials
 // rho^T L^{-1} rho; a user objective supplies f itself.
@@ -225,6 +230,13 @@ int launch_objective(plam_handle_s* h, const T* X, int64_t ldx, T* G, int64_t ld
       *err = launch_dense_grad<T>(h->n, p, (const T*)h->obj.A, h->obj.lda, X, ldx, G, ldg, st, s);
       return 1;
     case PLAM_OBJ_HARTREE1D:
+      if (chain_objective(h)) {
+        int k = 0;
+        *err = launch_chain_grad<T>(h->n, p, h->obj.block, h->obj.alpha, h->obj.quad_scale,
+                                    h->obj.xc, X, ldx, (const T*)h->obj.lin, h->obj.ldlin, G, ldg,
+                                    h->rho, h->fpart, st, s, &k);
+        return k;
+      }
       *err = launch_hartree_grad<T>(h->n, p, h->obj.alpha, h->obj.quad_scale, h->obj.xc, X, ldx, G,
                                     ldg, h->rho,
                                     h->blk, h->y, h->fpart, st, s);
@@ -395,7 +407,7 @@ plam_status_t orthonormalize_impl(plam_handle_s* h, const T* X, int64_t ldx, dou
     CK(launch_cholesky_inverse(p, h->B, h->W, h->Z, h->info, s));
     CK(cudaMemcpyAsync(h->info_host, h->info, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    h->launches += 3;
+    h->launches += 2 + cholesky_inverse_launches(p);
     if (*h->info_host != 0) {
       snprintf(g_err, sizeof(g_err), "Cholesky pivot %d not positive", *h->info_host);
       return PLAM_ERR_CHOLESKY;
@@ -646,10 +658,16 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
     case PLAM_OBJ_DENSE:
       if (!obj->A || obj->lda < n || !aligned(obj->A, esz)) return PLAM_ERR_INVALID;
       break;
-    case PLAM_OBJ_HARTREE1D:
-      if (!std::isfinite(obj->alpha) || !std::isfinite(obj->quad_scale) || !std::isfinite(obj->xc))
+    case PLAM_OBJ_HARTREE1D: {
+      if (!std::isfinite(obj->alpha) || !std::isfinite(obj->quad_scale) || !std::isfinite(obj->xc) ||
+          obj->block < 0)
+        return PLAM_ERR_INVALID;
+      if (obj->lin && (obj->ldlin < n || !aligned(obj->lin, esz))) return PLAM_ERR_INVALID;
+      const int64_t blk = obj->block >= n ? 0 : obj->block;
+      if ((blk != 0 || obj->lin) && obj->alpha != 0.0 && (blk < 1 || blk > kChainMaxBlock))
         return PLAM_ERR_INVALID;
       break;
+    }
     case PLAM_OBJ_STENCIL3D:
       if (obj->nx < 1 || obj->ny < 1 || obj->nz < 1 ||
           (int64_t)obj->nx * obj->ny * obj->nz != n || n > 2147483647 ||
@@ -668,6 +686,7 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
   h->n = n;
   h->p = p;
   h->obj = *obj;
+  if (h->obj.kind == PLAM_OBJ_HARTREE1D && h->obj.block >= n) h->obj.block = 0;   // one block
   h->prm = *prm;
   h->stream = (cudaStream_t)stream;
   h->prec = prm->precision;
@@ -721,7 +740,13 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
             alloc((void**)&h->dotpart, kDotBlocks * sizeof(double)) &&
             alloc((void**)&h->kkt_part, (size_t)kKktBlocksX * ((p + kKktCols - 1) / kKktCols) *
                                             sizeof(double));
-  if (ok && obj->kind == PLAM_OBJ_HARTREE1D) {
+  if (ok && chain_objective(h)) {
+    const ChainPlan c = chain_plan(n, (int)p, h->obj.block, h->obj.alpha != 0.0);
+    h->nfpart = c.ntiles * c.ncg;
+    ok = alloc((void**)&h->fpart, (size_t)h->nfpart * sizeof(double));
+    if (ok && (h->obj.alpha != 0.0 || h->obj.xc != 0.0))
+      ok = alloc((void**)&h->rho, (size_t)c.ncg * n * sizeof(double));
+  } else if (ok && obj->kind == PLAM_OBJ_HARTREE1D) {
     h->nfpart = hartree_blocks(n);
     ok = alloc((void**)&h->rho, n * sizeof(double)) && alloc((void**)&h->y, n * sizeof(double)) &&
          alloc((void**)&h->blk, 2 * (size_t)h->nfpart * sizeof(double)) &&
@@ -735,7 +760,8 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
   if (ok && prm->final_orth == 2) ok = alloc((void**)&h->Qtmp, (size_t)h->ldw * p * sizeof(double));
   if (ok && prm->engine != PLAM_ENGINE_GRAPH && prm->precision == PLAM_PREC_FP32 &&
       prm->lambda_rule != PLAM_LAMBDA_DA &&
-      ((obj->kind == PLAM_OBJ_HARTREE1D && obj->xc == 0.0) || obj->kind == PLAM_OBJ_DENSE)) {
+      ((obj->kind == PLAM_OBJ_HARTREE1D && obj->xc == 0.0 && !chain_objective(h)) ||
+       obj->kind == PLAM_OBJ_DENSE)) {
     int dev = 0, sms = 0, optin = 0, coop = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&

@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "../../include/plam.h"
 
 namespace plam {
@@ -110,6 +112,19 @@ cudaError_t launch_hartree_grad(int64_t n, int p, double alpha, double q, double
                                 int64_t ldx, T* G, int64_t ldg, double* rho, double* blk, double* y,
                                 double* fpart, const DevState* st, cudaStream_t s);
 int hartree_blocks(int64_t n);
+// Block-diagonal 1D objective with an optional linear term (Section 5.4's Problems 1 and 2):
+// row tiles of `tile` rows x `ncg` column groups of `cw` columns; the f partials are
+// ntiles * ncg doubles and rho_part ncg * n doubles (when alpha or xc is nonzero).
+constexpr int kChainMaxBlock = 64;
+struct ChainPlan {
+  int tile, ntiles, ncg, cw;
+};
+ChainPlan chain_plan(int64_t n, int p, int64_t block, bool need_y);
+template <typename T>
+cudaError_t launch_chain_grad(int64_t n, int p, int64_t block, double alpha, double q, double xc,
+                              const T* X, int64_t ldx, const T* lin, int64_t ldl, T* G,
+                              int64_t ldg, double* rho_part, double* fpart, const DevState* st,
+                              cudaStream_t s, int* launches);
 template <typename T>
 cudaError_t launch_stencil_grad(int nx, int ny, int nz, int p, const T* V, const T* X, int64_t ldx,
                                 T* G, int64_t ldg, const DevState* st, cudaStream_t s);
@@ -118,6 +133,7 @@ cudaError_t launch_stencil_grad(int nx, int ny, int nz, int p, const T* V, const
 // output R^{-1} (upper triangular), info: 0 or 1 + the failing pivot.
 cudaError_t launch_cholesky_inverse(int p, const double* B, double* W, double* Z, int* info,
                                     cudaStream_t s);
+int cholesky_inverse_launches(int p);   // kernels launch_cholesky_inverse launches
 template <typename T>
 cudaError_t launch_apply_rinv(int64_t n, int p, const T* X, int64_t ldx, const double* Z,
                               double* Q, int64_t ldq, cudaStream_t s);

@@ -8,8 +8,14 @@
                                       64^3 plus the seeded potential V iid U[0,1], p = 256):
                                       half the sum of the 256 smallest eigenvalues (Ky Fan),
                                       oracle.objectives.trace_min_optimum (about 40 minutes).
+  section54_n10000_p1000.json         Section 5.4's parallel forms of Problems 1 (blocks of 5
+                                      rows, alpha = 1, q = 1/2) and 2 (tridiagonal A, random
+                                      G_lin), n = 10000, p = 1000, seeded starts: the oracle's PCAL
+                                      (beta = 1, eq. lambda2, ABB) to relative KKT 1e-6 and 1e-8,
+                                      iterations, f and feasibility (a few minutes).
 
-Run from the repository root:  python tests/golden/make_golden.py [hartree1d] [stencil3d]
+Run from the repository root:
+    python tests/golden/make_golden.py [hartree1d] [stencil3d] [section54]
 """
 import json
 import os
@@ -22,7 +28,8 @@ sys.path.insert(0, ROOT)
 
 from oracle import objectives as oo  # noqa: E402
 from oracle import plam as op  # noqa: E402
-from workloads import workload_hartree1d, workload_stencil3d  # noqa: E402
+from workloads import (workload_block_hartree, workload_hartree1d, workload_stencil3d,  # noqa: E402
+                       workload_tridiag_linear)
 
 
 def hartree_optimum():
@@ -49,11 +56,34 @@ def stencil_optimum():
             "source": "oracle/objectives.py trace_min_optimum() run by tests/golden/make_golden.py"}
 
 
+def section54_runs():
+    out = {}
+    for w in (workload_block_hartree(), workload_tridiag_linear()):
+        obj = oo.objective_for(w)
+        d = {"n": w.n, "p": w.p, "alpha": w.alpha, "quad_scale": w.quad_scale, "block": w.block,
+             "beta": 1.0}
+        for tol in (1e-6, 1e-8):
+            t0 = time.time()
+            r = op.solve(obj, w.X0, variant="pcal", beta=1.0, tol=tol, maxit=3000, record=False)
+            assert r.converged
+            d[f"tol_{tol:g}"] = {"iters": r.iters, "f_stop": r.f_stop, "f_orth": r.f_orth,
+                                 "kkt_orth": r.kkt_orth, "feas_orth": r.feas_orth, "K0": r.K0,
+                                 "oracle_seconds": round(time.time() - t0, 1)}
+        out[w.name] = d
+    out["source"] = "oracle/plam.py solve() run by tests/golden/make_golden.py"
+    return out
+
+
 if __name__ == "__main__":
     which = sys.argv[1:] or ["hartree1d"]
     if "hartree1d" in which:
         d = hartree_optimum()
         with open(os.path.join(HERE, "hartree1d_n20000_p50_optimum.json"), "w") as fh:
+            json.dump(d, fh, indent=1)
+        print(d)
+    if "section54" in which:
+        d = section54_runs()
+        with open(os.path.join(HERE, "section54_n10000_p1000.json"), "w") as fh:
             json.dump(d, fh, indent=1)
         print(d)
     if "stencil3d" in which:

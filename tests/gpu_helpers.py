@@ -10,8 +10,8 @@ def gpu_solver(w, precision="fp64", **kw):
     if w.kind == "dense":
         return Solver(w.n, w.p, "dense", A=w.A, precision=precision, **kw)
     if w.kind == "hartree1d":
-        return Solver(w.n, w.p, "hartree1d", alpha=w.alpha, quad_scale=w.quad_scale,
-                      precision=precision, **kw)
+        return Solver(w.n, w.p, "hartree1d", alpha=w.alpha, quad_scale=w.quad_scale, xc=w.xc,
+                      block=w.block, lin=w.lin, precision=precision, **kw)
     if w.kind == "stencil3d":
         return Solver(w.n, w.p, "stencil3d", grid=(w.m, w.m, w.m), V=w.V, precision=precision, **kw)
     raise ValueError(w.kind)

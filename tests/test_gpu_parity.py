@@ -359,8 +359,11 @@ def test_stencil3d_random_potential_matches_oracle(precision):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("passes", [1, 2])
-def test_orthonormalize_matches_householder_qr(precision, passes):
-    n, p = 1501, 33
+@pytest.mark.parametrize("p", [33, 97, 130, 301])
+def test_orthonormalize_matches_householder_qr(precision, passes, p):
+    """FP64 Cholesky-QR against the oracle's Householder QR (signed so diag(R) > 0); p = 33 runs
+    the one-CTA factorisation in shared memory, larger p the blocked one (ragged last blocks)."""
+    n = max(1501, 3 * p)
     rng = np.random.default_rng(7)
     X = orthonormal_start(n, p, rng) + 1e-3 * rng.standard_normal((n, p))
     if precision == "fp32":
@@ -377,11 +380,15 @@ def test_orthonormalize_matches_householder_qr(precision, passes):
     s.close()
 
 
-def test_orthonormalize_reports_rank_deficiency():
+@pytest.mark.parametrize("p", [5, 130])
+def test_orthonormalize_reports_rank_deficiency(p):
     from paper_1810_03930_gb300 import _lib
-    n, p = 200, 5
+    n = 200 if p == 5 else 400
     X = orthonormal_start(n, p, np.random.default_rng(1))
-    X[:, 3] = X[:, 1]
+    if p == 5:
+        X[:, 3] = X[:, 1]
+    else:
+        X[:, 100] = 0.0      # a zero pivot in the fourth 32-column block
     s = gpu_solver(workload_hartree1d(n=n, p=p), "fp64")
     Xd = to_dev(X, s)
     Qd = s.new_matrix(dtype=torch.float64)

@@ -120,3 +120,22 @@ def test_noop_orthonormalisation_is_caught(monkeypatch):
     sol = {v: op.solve(obj, w.X0, variant=v, beta=1.0, tol=1e-8, maxit=3000) for v in ("plam", "pcal")}
     with pytest.raises(AssertionError):
         pins.test_final_orthonormalisation((w, obj, ev, U, sol), "plam")
+
+
+def test_block_coupling_kept_across_block_edges_is_caught(monkeypatch):
+    """L with the off-diagonal -1 kept between blocks (one tridiagonal instead of Diag(L_j))."""
+    monkeypatch.setattr(oo, "laplacian_1d_coupled", lambda n, block=0: np.ones(max(n - 1, 0), dtype=bool))
+    with pytest.raises(AssertionError):
+        pins.test_block_laplacian_trace_problem_reaches_ky_fan()
+
+
+def test_dropped_linear_term_gradient_is_caught(monkeypatch):
+    """Problem 2's linear term left out of the gradient (kept in f)."""
+    orig = oo.HartreeObjective.grad
+
+    def bad(self, X):
+        G = orig(self, X)
+        return G - self.lin if self.lin is not None else G
+    monkeypatch.setattr(oo.HartreeObjective, "grad", bad)
+    with pytest.raises(AssertionError):
+        pins.test_gradient_finite_difference("block_hartree_lin_xc")

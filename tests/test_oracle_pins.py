@@ -175,6 +175,62 @@ def test_hartree_alpha0_reduces_to_laplacian_eigenproblem():
     assert abs(r.f_orth - fstar) <= 1e-9 * fstar
 
 
+def test_block_laplacian_spectrum_and_inverse():
+    """Section 5.4's block-diagonal L (blocks of b rows, a ragged last block): the matrix that
+    laplacian_1d_apply assembles column by column has the union of the blocks' Dirichlet spectra
+    {2 - 2 cos(k pi/(m+1)) : k <= m} and no coupling across block edges, and the banded solve
+    L^{-1} rho equals the blocks' closed-form Green's functions min(u,v)(m+1-max(u,v))/(m+1)
+    (the b = 2 block is (1/3)[[2,1],[1,2]])."""
+    n, b = 23, 5
+    Ld = oo.laplacian_1d_apply(np.eye(n), b)
+    sizes = [b] * (n // b) + ([n % b] if n % b else [])
+    ev = sorted(2 - 2 * math.cos(k * math.pi / (m + 1)) for m in sizes for k in range(1, m + 1))
+    np.testing.assert_allclose(np.linalg.eigvalsh(Ld), ev, atol=1e-13)
+    for e in range(b, n, b):                 # rows e-1 and e sit in different blocks
+        assert Ld[e - 1, e] == 0.0 and Ld[e, e - 1] == 0.0
+    obj = oo.HartreeObjective(n, block=b)
+    rho = np.random.default_rng(4).random(n)
+    y = obj.hartree_potential(rho)
+    start = 0
+    for m in sizes:
+        np.testing.assert_allclose(y[start:start + m], _green(m) @ rho[start:start + m], rtol=1e-13)
+        start += m
+    y2 = oo.HartreeObjective(6, block=2).hartree_potential(np.array([1.0, 0.0, 0.0, 3.0, 0.0, 0.0]))
+    np.testing.assert_allclose(y2, [2 / 3, 1 / 3, 1.0, 2.0, 0.0, 0.0], rtol=1e-15)
+
+
+def test_block_hartree_linear_energy_hand_value():
+    """X = [e_1 .. e_p] with blocks of b rows and a linear term: tr(X^T L X) = 2p, rho is the
+    indicator of the first p rows, so rho^T L^{-1} rho adds the Green's function entries of the
+    pairs of those rows inside one block, and tr(G_lin^T X) = sum_i G_lin[i, i]."""
+    n, p, b, alpha, q = 30, 7, 4, 1.1, 0.5
+    lin = np.random.default_rng(9).standard_normal((n, p))
+    X = np.zeros((n, p))
+    X[np.arange(p), np.arange(p)] = 1.0
+    h = 0.0
+    for i in range(p):
+        for j in range(p):
+            if i // b == j // b:
+                u, v = i % b + 1, j % b + 1
+                h += min(u, v) * (b + 1 - max(u, v)) / (b + 1)
+    expect = q * 2 * p + 0.25 * alpha * h + float(np.trace(lin[:p, :]))
+    got = oo.HartreeObjective(n, alpha, q, block=b, lin=lin).value(X)
+    assert abs(got - expect) <= 1e-13 * abs(expect)
+
+
+def test_block_laplacian_trace_problem_reaches_ky_fan():
+    """alpha = 0 with blocks of 5 rows: min q tr(X^T L X) = q times the sum of the p smallest
+    eigenvalues of the union of the blocks' spectra (the Section 5.4 Problem 1 operator)."""
+    n, p, b, q = 60, 6, 5, 0.5
+    obj = oo.HartreeObjective(n, alpha=0.0, quad_scale=q, block=b)
+    X0 = orthonormal_start(n, p, rng_for(19, 1))
+    r = op.solve(obj, X0, variant="pcal", beta=2.1, tol=1e-10, maxit=20000)
+    ev = sorted(2 - 2 * math.cos(k * math.pi / (b + 1)) for _ in range(n // b) for k in range(1, b + 1))
+    fstar = q * sum(ev[:p])
+    assert r.converged
+    assert abs(r.f_orth - fstar) <= 1e-9 * fstar
+
+
 def _fd_check(obj, X, seed=0, h=1e-6):
     E = np.random.default_rng(seed).standard_normal(X.shape)
     fd = (obj.value(X + h * E) - obj.value(X - h * E)) / (2 * h)
@@ -182,7 +238,8 @@ def _fd_check(obj, X, seed=0, h=1e-6):
     return fd, an
 
 
-@pytest.mark.parametrize("kind", ["dense", "hartree", "stencil", "quadlin", "dense_hartree"])
+@pytest.mark.parametrize("kind", ["dense", "hartree", "stencil", "quadlin", "dense_hartree",
+                                  "block_hartree_lin_xc"])
 def test_gradient_finite_difference(kind):
     """Central differences <grad f, E> = (f(X+hE) - f(X-hE)) / 2h for every oracle objective."""
     rng = np.random.default_rng(11)
@@ -196,6 +253,10 @@ def test_gradient_finite_difference(kind):
         m = 4
         n = m ** 3
         obj = oo.Stencil3DObjective(m, rng.random(n))
+    elif kind == "block_hartree_lin_xc":
+        n = 63
+        obj = oo.HartreeObjective(n, alpha=1.3, quad_scale=0.5, xc=0.7, block=5,
+                                  lin=rng.standard_normal((n, 5)))
     elif kind == "quadlin":
         n = 50
         obj = oo.QuadLinearObjective(gaussian_symmetric(n, rng), rng.standard_normal((n, 5)))

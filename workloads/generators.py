@@ -34,6 +34,7 @@ __all__ = [
     "workload_dense_trace", "workload_hartree1d", "workload_stencil3d",
     "batched_shapes", "workload_batched_problem", "workload_by_config",
     "workload_ks_exchange", "parameter_study_problems", "multiplier_study_problems",
+    "workload_block_hartree", "workload_tridiag_linear",
 ]
 
 
@@ -112,6 +113,8 @@ class Workload:
     alpha: float = 1.0             # Hartree coupling (kind == "hartree1d")
     quad_scale: float = 0.25       # coefficient of tr(X^T L X) (kind == "hartree1d")
     xc: float = 0.0                # exchange coefficient gamma (kind == "hartree1d", Problem 6)
+    block: int = 0                 # rows per Dirichlet block of L, 0 = one block (kind == "hartree1d")
+    lin: Optional[np.ndarray] = None  # linear term G_lin, n-by-p (kind == "hartree1d", Problem 2)
     params: dict = field(default_factory=dict)  # suggested solver parameters
 
 
@@ -143,6 +146,28 @@ def workload_ks_exchange(n: int = 2000, p: int = 10, config: int = 6) -> Workloa
     gamma = 2.0 * (3.0 / np.pi) ** (1.0 / 3.0)
     return Workload(name=f"ks_exchange_n{n}_p{p}", kind="hartree1d", n=n, p=p, X0=X0, alpha=2.0,
                     quad_scale=0.5, xc=gamma, params=dict(variant="pcal", beta=100.0, tol=1e-8))
+
+
+def workload_block_hartree(n: int = 10000, p: int = 1000, block: int = 5,
+                           config: int = 17) -> Workload:
+    """Section 5.4's Problem 1: f = 1/2 tr(X^T L X) + 1/4 rho^T L^{-1} rho with the block-diagonal
+    L = Diag(L_1, ..., L_s), each L_j = tridiag(-1, 2, -1) on `block` rows (q = 1/2, alpha = 1);
+    orthonormal Gaussian start."""
+    X0 = orthonormal_start(n, p, rng_for(config, 1))
+    return Workload(name=f"block_hartree_n{n}_p{p}_b{block}", kind="hartree1d", n=n, p=p, X0=X0,
+                    alpha=1.0, quad_scale=0.5, block=block,
+                    params=dict(variant="pcal", beta=1.0, tol=1e-6))
+
+
+def workload_tridiag_linear(n: int = 10000, p: int = 1000, config: int = 18) -> Workload:
+    """Section 5.4's Problem 2: f = 1/2 tr(X^T A X) + tr(G_lin^T X) with A = tridiag(-1, 2, -1)
+    (q = 1/2, alpha = 0) and G_lin iid U[-1, 1] (a "Random(n, p)" matrix); orthonormal
+    Gaussian start."""
+    lin = np.asfortranarray(rng_for(config, 0).uniform(-1.0, 1.0, (n, p)))
+    X0 = orthonormal_start(n, p, rng_for(config, 1))
+    return Workload(name=f"tridiag_linear_n{n}_p{p}", kind="hartree1d", n=n, p=p, X0=X0,
+                    alpha=0.0, quad_scale=0.5, lin=lin,
+                    params=dict(variant="pcal", beta=1.0, tol=1e-6))
 
 
 def workload_stencil3d(m: int = 64, p: int = 256, config: int = 3,
