@@ -184,6 +184,23 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def measured_tf32_tflops():
+    """Dense TF32 tensor peak: the measured bf16 burst GEMM rate times the nominal TF32 / BF16
+    dense ratio (1.1 / 2.25 PFLOP/s); the profiling fallback 1.9 PFLOP/s bf16 without the file."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["bf16_tflops"]) * 1.1 / 2.25, "measured bf16 burst x 1.1/2.25 (nominal TF32/BF16)"
+    except Exception:
+        return 1900.0 * 1.1 / 2.25, "fallback bf16 x 1.1/2.25 (nominal TF32/BF16)"
+
+
+def kernel_flops(wl):
+    """Algorithmic tensor-core flops per launch of the contractions: the Grams X^T X (symmetric,
+    n p^2) and X^T G (2 n p^2), the update X M and X E (2 x 2 n p^2)."""
+    n, p = wl["n"], wl["p"]
+    return {"gram_partial": 3 * n * p * p, "update": 4 * n * p * p}
+
+
 def kernel_bytes(wl, w, nchunks_unused=None):
     """Algorithmic DRAM bytes per launch of each kernel group (w = bytes per element of X)."""
     n, p = wl["n"], wl["p"]
@@ -461,6 +478,18 @@ def run_ours(args, rank, world, local):
                       "unit": "GB/s", "frac": achieved_g / peak_hbm, "peak_source": peak_kind,
                       "traffic": recorded_traffic(kernel_names[dom], wl["name"]),
                       "alg_bytes_per_launch": kb[dom], "launch_ms": kms[dom]}
+    kf = kernel_flops(wl)
+    tf32, tf32_kind = measured_tf32_tflops()
+    if tc and dom in kf and kf[dom] / kb[dom] > tf32 * 1e12 / (peak_hbm * 1e9):
+        # a tensor-core contraction above the ridge point (p = 1000: 3p/8 = 375 flop/B for
+        # the Grams): bound by the TF32 tensor rate, not by HBM
+        achieved_t = kf[dom] / (kms[dom] * 1e-3) / 1e12
+        roofline_graph = {"bound": "tensor", "kernel": kernel_names[dom], "achieved": achieved_t,
+                          "peak": tf32, "unit": "TFLOP/s", "frac": achieved_t / tf32,
+                          "peak_source": tf32_kind,
+                          "traffic": recorded_traffic(kernel_names[dom], wl["name"]),
+                          "alg_flops_per_launch": kf[dom], "alg_bytes_per_launch": kb[dom],
+                          "launch_ms": kms[dom]}
     if engine == "graph":
         roofline = roofline_graph
     # ---- end to end through the public API with host buffers
