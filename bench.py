@@ -78,7 +78,34 @@ def parse_args():
                     help="only time the kernel groups of this many iterations (graph engine's "
                          "kernels launched one by one) and print them; a short, profiler-sized run")
     ap.add_argument("--tensor-cores", choices=["auto", "off", "tf32", "3xtf32"], default="auto")
+    ap.add_argument("--p", type=int, default=0,
+                    help="block_hartree / tridiag_linear only: the width p (Section 5.4 sweeps "
+                         "p = 500 ... 2500 at n = 10000); 0 keeps 1000")
+    ap.add_argument("--beta", type=float, default=0.0,
+                    help="block_hartree / tridiag_linear only: the penalty beta (0 keeps the "
+                         "paper's PCAL default 1; from p ~ 0.18 n on, beta = 1 lets the columns "
+                         "collapse and beta = s + 0.1 = 4.1 converges)")
     return ap.parse_args()
+
+
+def workload_config(args, **extra):
+    """The workload's parameters, with --p applied to Section 5.4's workloads."""
+    wl = dict(WORKLOADS[args.workload], **extra)
+    if getattr(args, "p", 0):
+        if not wl.get("section54"):
+            raise SystemExit("--p applies to the block_hartree and tridiag_linear workloads")
+        if not 1 <= args.p <= wl["n"] // 2:
+            raise SystemExit(f"--p must lie in [1, {wl['n'] // 2}]")
+        wl["name"] = wl["name"].replace(f"_p{wl['p']}", f"_p{args.p}")
+        wl["p"] = args.p
+    if getattr(args, "beta", 0.0):
+        if not wl.get("section54"):
+            raise SystemExit("--beta applies to the block_hartree and tridiag_linear workloads")
+        if not args.beta > 0.0:
+            raise SystemExit("--beta must be positive")
+        wl["beta"] = args.beta
+        wl["name"] += f"_beta{args.beta:g}"
+    return wl
 
 
 # ---------------------------------------------------------------- distributed plumbing
@@ -227,7 +254,7 @@ KERNEL_SOURCES = {
     "chain_grad": ["k_objective.cu"],
     "update": ["k_update.cu"], "primal_update": ["k_update.cu"], "step_size": ["k_update.cu"],
     "gram_partial": ["k_gram.cu"], "gram_finalize": ["k_gram.cu"],
-    "batched_solve": ["k_batched.cu"],
+    "batched_solve": ["k_batched.cu"], "orth": ["k_orth.cu"],
 }
 
 
@@ -370,7 +397,7 @@ def cpu_baseline(w, wl, seconds, gpu_iters):
 def run_ours(args, rank, world, local):
     import torch
     dist_init(world, local)
-    wl = dict(WORKLOADS[args.workload])
+    wl = workload_config(args)
     w = load_inputs(wl)
     from paper_1810_03930_gb300 import colmajor_to_device
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -539,7 +566,7 @@ def run_ours(args, rank, world, local):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    wl = dict(WORKLOADS[args.workload])
+    wl = workload_config(args)
     if wl["kind"] == "batched":        # the oracle on the batch's first problem per step
         from workloads import batched_shapes, workload_batched_problem
         n, p = batched_shapes(count=wl["count"], n_lo=wl["n_lo"], n_hi=wl["n_hi"])[0]
@@ -597,7 +624,7 @@ def run_kernel_iters(args):
         bs.close()
         return
     import numpy as np
-    wl = dict(WORKLOADS[args.workload], tensor_cores=args.tensor_cores)
+    wl = workload_config(args, tensor_cores=args.tensor_cores)
     if wl.get("kernel_only"):
         from workloads import rng_for, uniform_potential
         wl["V"] = uniform_potential(wl["n"], rng_for(5, 0))
@@ -782,6 +809,7 @@ def cpu_baseline_batched(ws, wl, seconds, gpu_s):
 
 def main():
     args = parse_args()
+    workload_config(args)          # refuses a bad --p before any device work
     rank, world, local = dist_env()
     if args.workload == "batched" and args.impl == "ours" and args.kernel_iters == 0:
         run_batched(args, rank, world, local)

@@ -41,3 +41,24 @@ def test_kernel_only_workload_refuses_a_solve():
     r = _run("--workload", "stencil3d_128", timeout=120)
     assert r.returncode != 0
     assert "per-kernel timings only" in r.stderr
+
+
+def test_width_override_applies_to_section54_workloads_only():
+    """--p sets Section 5.4's width (the paper sweeps p = 500 ... 2500 at n = 10000) and names the
+    workload by it; other workloads and widths above n/2 are refused before any GPU work."""
+    import argparse
+    sys.path.insert(0, ROOT)
+    import bench
+    wl = bench.workload_config(argparse.Namespace(workload="block_hartree", p=2500))
+    assert wl["p"] == 2500 and wl["name"] == "block_hartree_n10000_p2500_b5"
+    assert bench.WORKLOADS["block_hartree"]["p"] == 1000
+    wl = bench.workload_config(argparse.Namespace(workload="tridiag_linear", p=0))
+    assert wl["p"] == 1000 and wl["name"] == "tridiag_linear_n10000_p1000"
+    r = _run("--workload", "hartree1d", "--p", "500")
+    assert r.returncode != 0 and "--p applies" in (r.stderr + r.stdout)
+    r = _run("--workload", "block_hartree", "--p", "6000")
+    assert r.returncode != 0 and "--p must lie" in (r.stderr + r.stdout)
+    wl = bench.workload_config(argparse.Namespace(workload="block_hartree", p=2000, beta=4.1))
+    assert wl["beta"] == 4.1 and wl["name"] == "block_hartree_n10000_p2000_b5_beta4.1"
+    r = _run("--workload", "hartree1d", "--beta", "2")
+    assert r.returncode != 0 and "--beta applies" in (r.stderr + r.stdout)
