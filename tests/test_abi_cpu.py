@@ -118,6 +118,31 @@ def test_create_rejects_bad_params_and_objectives(lib):
     assert lib.plam_create(C.byref(h), 100, 5, C.byref(bad), C.byref(prm), None) == _lib.PLAM_ERR_INVALID
 
 
+def test_create_rejects_bad_block_and_linear_term(lib):
+    """The 1D objective's block size and linear term (Section 5.4's Problems 1 and 2) are checked
+    on the host before anything is allocated: a negative block, a Hartree term with blocks of more
+    than 64 rows or with one block of n rows and a linear term, and a linear term whose leading
+    dimension is short or whose address is not aligned to the storage type (the pointers are never
+    dereferenced)."""
+    from paper_1810_03930_gb300 import _lib
+    prm = _lib.plam_default_params()          # FP64: 8-byte storage
+    n, p = 500, 4
+    cases = [dict(block=-1, alpha=0.0), dict(block=65, alpha=1.0),
+             dict(block=0, alpha=1.0, lin=256, ldlin=n), dict(block=5, alpha=1.0, lin=256, ldlin=n - 1),
+             dict(block=5, alpha=0.0, lin=260, ldlin=n)]
+    for c in cases:
+        obj = _lib.plam_objective_t()
+        obj.kind = _lib.PLAM_OBJ_HARTREE1D
+        obj.quad_scale = 0.5
+        obj.alpha = c["alpha"]
+        obj.block = c["block"]
+        if "lin" in c:
+            obj.lin, obj.ldlin = c["lin"], c["ldlin"]
+        h = C.c_void_p()
+        st = lib.plam_create(C.byref(h), n, p, C.byref(obj), C.byref(prm), None)
+        assert st == _lib.PLAM_ERR_INVALID and not h.value, c
+
+
 def test_null_handle_calls_are_rejected(lib):
     from paper_1810_03930_gb300 import _lib
     info = _lib.plam_info_t()
