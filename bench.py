@@ -331,6 +331,15 @@ def load_inputs(wl):
     return w
 
 
+def orth_feasibility(Q, n, torch):
+    """||Q^T Q - I||_F of an FP64 device result (shape (p, ld), column-major n x p), checked
+    outside the timed region: the timed solves skip the library's own feasibility report
+    (orth_metrics off), which costs one more FP64 Gram."""
+    Qt = Q[:, :n]
+    E = Qt @ Qt.T - torch.eye(Q.shape[0], dtype=Q.dtype, device=Q.device)
+    return float(torch.linalg.matrix_norm(E))
+
+
 def timed_solves(solver, X0d, steps, flush, torch, host=None, allow_maxit=False):
     """Run `steps` solves; returns (list of ms, list of iters, last Q, last info, launches)."""
     Xw = torch.empty_like(X0d)
@@ -421,7 +430,7 @@ def run_ours(args, rank, world, local):
     sol64 = make_solver(wl, "fp64", torch)
     G = sol64.new_matrix()
     f_q = sol64.energy_grad(Q, G)
-    parity = {"f_orth": f_q, "feas_orth": info.feas_orth, "kkt_rel": info.kkt_rel}
+    parity = {"f_orth": f_q, "feas_orth": orth_feasibility(Q, wl["n"], torch), "kkt_rel": info.kkt_rel}
     if fstar:
         parity["f_star"] = fstar["f_star"]
         parity["obj_rel_err"] = abs(f_q - fstar["f_star"]) / abs(fstar["f_star"])
@@ -436,7 +445,7 @@ def run_ours(args, rank, world, local):
         f_t = sol64.energy_grad(Q_t, G)
         tight = {"tol_kkt_rel": 1e-7, "time_s": ms_t[0] / 1e3, "iters": its_t[0],
                  "obj_rel_err": abs(f_t - fstar["f_star"]) / abs(fstar["f_star"]),
-                 "feas_orth": info_t.feas_orth}
+                 "feas_orth": orth_feasibility(Q_t, wl["n"], torch)}
         sol_t.close()
     # ---- FP64 GPU path beside it
     X0d64 = colmajor_to_device(w.X0, torch.float64)

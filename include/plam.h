@@ -129,8 +129,10 @@ typedef struct {
                            (= 1 when p >= 128).  Needs 16-byte aligned X and G with leading dimensions
                            that are multiples of 4, otherwise the CUDA-core Grams run */
   double refine_switch; /* relative KKT value below which the tensor-core Grams are compensated */
-  int orth_metrics;     /* 1 (default): plam_solve also evaluates f and the relative KKT value of the
-                           orthonormalised output (plam_info_t.f_orth, kkt_orth); 0: skipped */
+  int orth_metrics;     /* 1 (default): plam_solve also evaluates f, the relative KKT value and the
+                           feasibility ||Q^T Q - I||_F of the orthonormalised output Q
+                           (plam_info_t.f_orth, kkt_orth, feas_orth); 0: skipped (NaN) — the
+                           feasibility alone is one more FP64 Gram of Q, n p^2 / 2 multiply-adds */
 } plam_params_t;
 
 typedef struct {

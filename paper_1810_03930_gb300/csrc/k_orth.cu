@@ -35,6 +35,7 @@ chol_diag_kernel(int p, int j0, double* __restrict__ W, double* __restrict__ Z,
                  int* __restrict__ info) {
   __shared__ double A[kCB][kCB + 1];
   __shared__ double Zi[kCB][kCB + 1];
+  __shared__ double rpiv[kCB];   // reciprocals of the pivots, formed once
   __shared__ int fail;
   if (*(volatile int*)info != 0) return;
   const int t = threadIdx.x;
@@ -46,12 +47,16 @@ chol_diag_kernel(int p, int j0, double* __restrict__ W, double* __restrict__ Z,
   for (int j = 0; j < nb; ++j) {
     if (t == 0) {
       const double d = A[j][j];
-      if (!(d > 0.0) || !isfinite(d)) fail = j0 + j + 1;
-      else A[j][j] = sqrt(d);
+      if (!(d > 0.0) || !isfinite(d)) {
+        fail = j0 + j + 1;
+      } else {
+        A[j][j] = sqrt(d);
+        rpiv[j] = 1.0 / A[j][j];
+      }
     }
     __syncthreads();
     if (fail) break;
-    if (r == j && c > j && c < nb) A[j][c] = A[j][c] / A[j][j];
+    if (r == j && c > j && c < nb) A[j][c] *= rpiv[j];
     __syncthreads();
     if (r > j && c >= r && c < nb) A[r][c] -= A[j][r] * A[j][c];
     __syncthreads();
@@ -65,7 +70,7 @@ chol_diag_kernel(int p, int j0, double* __restrict__ W, double* __restrict__ Z,
     for (int i = t; i >= 0; --i) {
       double v = (i == t) ? 1.0 : 0.0;
       for (int k = i + 1; k <= t; ++k) v -= A[i][k] * Zi[k][t];
-      Zi[i][t] = v / A[i][i];
+      Zi[i][t] = v * rpiv[i];
     }
   }
   __syncthreads();
@@ -314,14 +319,23 @@ apply_rinv_kernel(int64_t n, int p, const T* __restrict__ X, int64_t ldx, const 
   }
 }
 
-__global__ void feas_kernel(int p, const double* __restrict__ B, double* __restrict__ out) {
+// ||B - I||_F: one CTA per column (coalesced), then the column sums in order.
+__global__ void feas_col_kernel(int p, const double* __restrict__ B, double* __restrict__ col) {
   __shared__ double scratch[33];
+  const int j = blockIdx.x;
   double s = 0.0;
-  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-    const int i = e % p, j = e / p;
-    const double d = B[e] - (i == j ? 1.0 : 0.0);
+  for (int i = threadIdx.x; i < p; i += blockDim.x) {
+    const double d = B[i + (size_t)j * p] - (i == j ? 1.0 : 0.0);
     s += d * d;
   }
+  const double tot = block_sum(s, scratch);
+  if (threadIdx.x == 0) col[j] = tot;
+}
+
+__global__ void feas_sum_kernel(int p, const double* __restrict__ col, double* __restrict__ out) {
+  __shared__ double scratch[33];
+  double s = 0.0;
+  for (int j = threadIdx.x; j < p; j += blockDim.x) s += col[j];
   const double tot = block_sum(s, scratch);
   if (threadIdx.x == 0) out[0] = sqrt(tot);
 }
@@ -369,8 +383,11 @@ cudaError_t launch_apply_rinv(int64_t n, int p, const T* X, int64_t ldx, const d
   return cudaGetLastError();
 }
 
-cudaError_t launch_feas(int p, const double* B, double* out, cudaStream_t s) {
-  feas_kernel<<<1, 256, 0, s>>>(p, B, out);
+cudaError_t launch_feas(int p, const double* B, double* col, double* out, cudaStream_t s) {
+  feas_col_kernel<<<p, 128, 0, s>>>(p, B, col);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  feas_sum_kernel<<<1, 256, 0, s>>>(p, col, out);
   return cudaGetLastError();
 }
 

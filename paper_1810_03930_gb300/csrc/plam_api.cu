@@ -428,10 +428,10 @@ plam_status_t orthonormalize_impl(plam_handle_s* h, const T* X, int64_t ldx, dou
     CK((launch_gram_partial<double, double>(h->n, p, Xout, ldo, (const double*)nullptr, 0,
                                              h->rows_per_chunk, h->nchunks, h->part64, nullptr, s)));
     CK(launch_gram_reduce<double>(p, h->nchunks, 0, h->part64, h->B, nullptr, s));
-    CK(launch_feas(p, h->B, h->feas_dev, s));
+    CK(launch_feas(p, h->B, h->feas_row, h->feas_dev, s));
     CK(cudaMemcpyAsync(h->scal_host, h->feas_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    h->launches += 3;
+    h->launches += 4;
     *feas = h->scal_host[0];
   }
   return PLAM_OK;
@@ -954,7 +954,8 @@ plam_status_t plam_solve(plam_handle_t h, void* X, int64_t ldx, double* Xout, in
   if (stop == kDiverged) return PLAM_ERR_DIVERGED;
   if (h->prm.final_orth > 0 && Xout) {
     double feas = NAN;
-    st = plam_orthonormalize(h, X, ldx, Xout, ldo, h->prm.final_orth, &feas);
+    st = plam_orthonormalize(h, X, ldx, Xout, ldo, h->prm.final_orth,
+                             h->prm.orth_metrics ? &feas : nullptr);
     if (st != PLAM_OK) return st;
     inf->feas_orth = feas;
     // Table "orth step": f and KKT of the orthonormalised output

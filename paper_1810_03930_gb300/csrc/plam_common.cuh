@@ -137,8 +137,8 @@ int cholesky_inverse_launches(int p);   // kernels launch_cholesky_inverse launc
 template <typename T>
 cudaError_t launch_apply_rinv(int64_t n, int p, const T* X, int64_t ldx, const double* Z,
                               double* Q, int64_t ldq, cudaStream_t s);
-// out[0] = ||B - I||_F (one CTA).
-cudaError_t launch_feas(int p, const double* B, double* out, cudaStream_t s);
+// out[0] = ||B - I||_F (p x p, FP64); col: p doubles of per-column sums.
+cudaError_t launch_feas(int p, const double* B, double* col, double* out, cudaStream_t s);
 
 // Message returned by plam_last_error() on this host thread ("what: detail").
 void set_last_error(const char* what, const char* detail);
