@@ -172,7 +172,7 @@ typedef struct {
                            storage precision: FP32 mode rounds the FP64 output to float first) */
   double kkt_orth;      /* relative KKT after the final orthonormalisation (likewise; NaN when
                            p x 16 storage-type values exceed 227 KB of shared memory) */
-  double feas_orth;     /* ||Q^T Q - I||_F of the orthonormalised output */
+  double feas_orth;     /* ||Q^T Q - I||_F of the orthonormalised output (NaN with orth_metrics off) */
 } plam_info_t;
 
 typedef struct plam_handle_s* plam_handle_t;
