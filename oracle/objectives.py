@@ -20,6 +20,7 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
                      With `block` L is block-diagonal and `lin` adds Problem 2's
                      linear term tr(G_lin^T X) (Section 5.4's parallel workloads).
   QuadLinearObjective Problem 2 (eq. OCQP): f = 1/2 tr(X^T A X) + tr(G^T X).
+  QAPObjective       Problem 4 (eq. QAP): f = 1/2 tr(A^T X B X^T), grad = A X B.
   DenseHartreeObjective Problem 1 exactly (eq. nonlinear): dense symmetric L and
                      its pseudo-inverse L^+ (numpy.linalg.pinv), coefficient q.
   trace_min_optimum  the optimum of a trace problem f = 1/2 tr(X^T H X) over
@@ -65,6 +66,27 @@ class QuadLinearObjective:
 
     def grad(self, X):
         return self.A @ X + self.Glin
+
+
+class QAPObjective:
+    """f = 1/2 tr(A^T X B X^T) with A, B symmetric (Problem 4, Section 5.2 eq. QAP).
+
+    d/dX tr(A^T X B X^T) = A X B^T + A^T X B, so grad f = 1/2 (A X B + A X B) = A X B for
+    symmetric A and B.  s = ||A||_2 ||B||_2 bounds the Hessian at 0."""
+
+    def __init__(self, A: np.ndarray, B: np.ndarray):
+        self.A = np.asarray(A, dtype=np.float64)
+        self.B = np.asarray(B, dtype=np.float64)
+        self.n = self.A.shape[0]
+
+    def value(self, X):
+        return 0.5 * float(np.sum((self.A @ X) * (X @ self.B)))
+
+    def grad(self, X):
+        return self.A @ X @ self.B
+
+    def hess_norm_bound(self):
+        return float(np.max(np.abs(np.linalg.eigvalsh(self.A))) * np.max(np.abs(np.linalg.eigvalsh(self.B))))
 
 
 def laplacian_1d_coupled(n: int, block: int = 0) -> np.ndarray:

@@ -139,3 +139,10 @@ def test_dropped_linear_term_gradient_is_caught(monkeypatch):
     monkeypatch.setattr(oo.HartreeObjective, "grad", bad)
     with pytest.raises(AssertionError):
         pins.test_gradient_finite_difference("block_hartree_lin_xc")
+
+
+def test_problem4_gradient_without_b_is_caught(monkeypatch):
+    """Problem 4's gradient with the right factor B dropped (A X instead of A X B)."""
+    monkeypatch.setattr(oo.QAPObjective, "grad", lambda self, X: self.A @ X)
+    with pytest.raises(AssertionError):
+        pins.test_gradient_finite_difference("qap")

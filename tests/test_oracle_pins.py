@@ -231,6 +231,27 @@ def test_block_laplacian_trace_problem_reaches_ky_fan():
     assert abs(r.f_orth - fstar) <= 1e-9 * fstar
 
 
+def test_problem4_special_cases():
+    """Problem 4 (Section 5.2, eq. QAP): with B = I it is Problem 3 (the same value and gradient as
+    f = 1/2 tr(X^T A X)); with B = diag(3, 2, 1) its minimum over X^T X = I is
+    1/2 sum_i b_i lambda_i(A), the largest b_i paired with the smallest eigenvalues of A (the
+    rearrangement behind Ky Fan's principle), which the oracle's PCAL reaches."""
+    n, p = 40, 3
+    A = gaussian_symmetric(n, rng_for(23, 0))
+    X = np.random.default_rng(2).standard_normal((n, p))
+    q, t = oo.QAPObjective(A, np.eye(p)), oo.TraceObjective(A)
+    assert abs(q.value(X) - t.value(X)) <= 1e-12 * abs(t.value(X))
+    np.testing.assert_allclose(q.grad(X), t.grad(X), rtol=1e-13, atol=1e-13)
+    b = np.array([3.0, 2.0, 1.0])
+    obj = oo.QAPObjective(A, np.diag(b))
+    lam = np.linalg.eigvalsh(A)
+    fstar = 0.5 * float(b @ lam[:p])
+    r = op.solve(obj, orthonormal_start(n, p, rng_for(23, 1)), variant="pcal",
+                 beta=obj.hess_norm_bound() + 0.1, tol=1e-10, maxit=20000)
+    assert r.converged
+    assert abs(r.f_orth - fstar) <= 1e-10 * abs(fstar)
+
+
 def _fd_check(obj, X, seed=0, h=1e-6):
     E = np.random.default_rng(seed).standard_normal(X.shape)
     fd = (obj.value(X + h * E) - obj.value(X - h * E)) / (2 * h)
@@ -239,7 +260,7 @@ def _fd_check(obj, X, seed=0, h=1e-6):
 
 
 @pytest.mark.parametrize("kind", ["dense", "hartree", "stencil", "quadlin", "dense_hartree",
-                                  "block_hartree_lin_xc"])
+                                  "block_hartree_lin_xc", "qap"])
 def test_gradient_finite_difference(kind):
     """Central differences <grad f, E> = (f(X+hE) - f(X-hE)) / 2h for every oracle objective."""
     rng = np.random.default_rng(11)
@@ -257,6 +278,10 @@ def test_gradient_finite_difference(kind):
         n = 63
         obj = oo.HartreeObjective(n, alpha=1.3, quad_scale=0.5, xc=0.7, block=5,
                                   lin=rng.standard_normal((n, 5)))
+    elif kind == "qap":
+        n = 45
+        B0 = rng.standard_normal((5, 5))
+        obj = oo.QAPObjective(gaussian_symmetric(n, rng), 0.5 * (B0 + B0.T))
     elif kind == "quadlin":
         n = 50
         obj = oo.QuadLinearObjective(gaussian_symmetric(n, rng), rng.standard_normal((n, 5)))
@@ -549,6 +574,31 @@ def test_parameter_study_conclusions_on_trace_problems(variant):
     assert med["const"][1] == len(As)
     slow, _ = median_iters(10 * s + 1, "abb")
     assert slow > 1.3 * med["abb"][0]
+
+
+@pytest.mark.parametrize("variant", ["plam", "pcal"])
+def test_parameter_study_conclusion_on_problem4(variant):
+    """Section 5.1's step-size study (Fig. "eta") on Problem 4 (8 seeded instances, n = 200,
+    p = 8, A and B symmetrised Gaussians, beta = s + 0.1 with s = ||A|| ||B||, relative KKT
+    1e-6): ABB converges on every instance with the smallest median iteration count, ahead of
+    BB1 and BB2, and the constant step reaches the tolerance within 3000 iterations on none of
+    the instances it is run on."""
+    from workloads import paper_p4_matrices
+    its = {"abb": [], "bb1": [], "bb2": [], "const": []}
+    conv_abb = 0
+    for i in range(8):
+        A, B = paper_p4_matrices(200, 8, rng_for(22, 0, sub=i))
+        X0 = orthonormal_start(200, 8, rng_for(22, 1, sub=i))
+        obj = oo.QAPObjective(A, B)
+        beta = obj.hess_norm_bound() + 0.1
+        for rule in ("abb", "bb1", "bb2") + (("const",) if i < 2 else ()):
+            r = op.solve(obj, X0, variant=variant, beta=beta, eta_rule=rule, tol=1e-6, maxit=3000,
+                         record=False)
+            its[rule].append(r.iters if r.converged else 3000)
+            conv_abb += int(rule == "abb" and r.converged)
+    assert conv_abb == 8
+    assert np.median(its["abb"]) < np.median(its["bb1"]) and np.median(its["abb"]) < np.median(its["bb2"])
+    assert all(k == 3000 for k in its["const"])
 
 
 def test_multiplier_study_conclusion_on_problems_1_and_2():

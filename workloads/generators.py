@@ -34,7 +34,7 @@ __all__ = [
     "workload_dense_trace", "workload_hartree1d", "workload_stencil3d",
     "batched_shapes", "workload_batched_problem", "workload_by_config",
     "workload_ks_exchange", "parameter_study_problems", "multiplier_study_problems",
-    "workload_block_hartree", "workload_tridiag_linear",
+    "workload_block_hartree", "workload_tridiag_linear", "paper_p4_matrices",
 ]
 
 
@@ -97,6 +97,14 @@ def paper_p2_linear(n: int, p: int, rng: np.random.Generator, kappa: float = 1.0
     Qt = rng.random((n, p))
     Q = Qt / np.linalg.norm(Qt, axis=0)[None, :]
     return np.asfortranarray(kappa * Q * (zeta ** np.arange(p))[None, :])
+
+
+def paper_p4_matrices(n: int, p: int, rng: np.random.Generator) -> tuple[np.ndarray, np.ndarray]:
+    """Problem 4's data (Section 5.2): A = (A0 + A0^T)/2 with A0 = randn(n), B = (B0 + B0^T)/2 with
+    B0 = randn(p)."""
+    A0 = rng.standard_normal((n, n))
+    B0 = rng.standard_normal((p, p))
+    return np.asfortranarray(0.5 * (A0 + A0.T)), 0.5 * (B0 + B0.T)
 
 
 @dataclass
