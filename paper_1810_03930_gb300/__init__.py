@@ -105,6 +105,11 @@ class Solver:
 
     Matrices are torch tensors of shape (p, ld) whose memory is the column-major
     n x p matrix (ld = leading dimension >= n).
+
+    kind: "dense" (A), "hartree1d" (alpha, quad_scale, xc; block = rows per Dirichlet block
+    of L, 0 for one block; lin = the linear term G_lin of Problem 2, n x p), "stencil3d"
+    (grid = (nx, ny, nz), V) or "callback" (energy = a torch function of the (n, p) iterate).
+    The other keywords are the fields of plam_params_t (include/plam.h).
     """
 
     def __init__(self, n, p, kind, *, A=None, alpha=1.0, quad_scale=0.25, xc=0.0, block=0, lin=None,
