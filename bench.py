@@ -586,9 +586,14 @@ def run_reference(args, rank, world):
     from oracle import objectives as oo
     from oracle import plam as op
     obj = oo.objective_for(w)
-    per_step = 20
-    for _ in range(args.warmup):
-        op.solve(obj, w.X0, variant="pcal", beta=wl["beta"], tol=wl["tol"], maxit=2, record=False)
+    per_it = 0.0
+    for _ in range(max(1, args.warmup)):
+        t0 = time.perf_counter()
+        r = op.solve(obj, w.X0, variant="pcal", beta=wl["beta"], tol=wl["tol"], maxit=2, record=False)
+        per_it = (time.perf_counter() - t0) / (r.iters + 1)
+    # each step a bounded sample of the solve: 20 iterations, fewer where one takes long (about 8 s
+    # of CPU work per step), so that a --steps K --warmup W run ends within minutes
+    per_step = int(max(3, min(20, 8.0 / max(per_it, 1e-9))))
     times, iters = [], []
     for _ in range(args.steps):
         t0 = time.perf_counter()
