@@ -62,3 +62,22 @@ def test_width_override_applies_to_section54_workloads_only():
     assert wl["beta"] == 4.1 and wl["name"] == "block_hartree_n10000_p2000_b5_beta4.1"
     r = _run("--workload", "hartree1d", "--beta", "2")
     assert r.returncode != 0 and "--beta applies" in (r.stderr + r.stdout)
+
+
+def test_output_feasibility_check_of_the_bench():
+    """bench's check of the output, ||Q^T Q - I||_F on the (p, ld) column-major layout the library
+    writes: about 1e-15 for an orthonormal Q, and hypot(0.21, -0.19) for one whose first two
+    columns are scaled by 1.1 and 0.9 (the diagonal of Q^T Q - I; the columns stay orthogonal)."""
+    import numpy as np
+    import torch
+    sys.path.insert(0, ROOT)
+    import bench
+    n, p, ld = 50, 4, 56
+    Q, _ = np.linalg.qr(np.random.default_rng(0).standard_normal((n, p)))
+    t = torch.zeros((p, ld), dtype=torch.float64)
+    t[:, :n] = torch.as_tensor(Q.T)
+    assert bench.orth_feasibility(t, n, torch) < 1e-14
+    t[0, :n] *= 1.1
+    t[1, :n] *= 0.9
+    expect = float(np.hypot(1.1 ** 2 - 1.0, 0.9 ** 2 - 1.0))
+    assert abs(bench.orth_feasibility(t, n, torch) - expect) < 1e-13
