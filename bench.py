@@ -272,14 +272,16 @@ def csrc_hash(kernel=None):
 
 def recorded_traffic(kernel, workload):
     """dram bytes per launch recorded by an ncu capture summarised under profiles/, if the
-    kernel's sources have not changed since (the summary carries their hash)."""
+    kernel's sources have not changed since: the summary carries the hash of the sources it was
+    captured on, and may list later hashes whose sources differ from them only in host-side
+    declarations of the shared header (`same_kernel_sources_sha256_16:`, with the diff named)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    hsh = re.search(r"kernel_sources_sha256_16:\s*([0-9a-f]+)", text)
-    if not m or not hsh or hsh.group(1) != csrc_hash(kernel):
+    hashes = re.findall(r"kernel_sources_sha256_16:\s*([0-9a-f]+)", text)
+    if not m or csrc_hash(kernel) not in hashes:
         return None
     return float(m.group(1))
 
