@@ -81,3 +81,19 @@ def test_output_feasibility_check_of_the_bench():
     t[1, :n] *= 0.9
     expect = float(np.hypot(1.1 ** 2 - 1.0, 0.9 ** 2 - 1.0))
     assert abs(bench.orth_feasibility(t, n, torch) - expect) < 1e-13
+
+
+def test_flop_accounting_matches_table_cost():
+    """Table "cost": one PLAM or PCAL iteration is 7np^2 + O(np) flops, namely grad f^T X (2np^2),
+    X^T X (np^2), X (X^T X - I) (2np^2) and X Psi(grad f^T X) (2np^2).  The roofline flops of the
+    fused kernels add up to it: the Grams X^T [X | G] (3np^2) and the update's two products
+    X M and X E (2np^2 each), for every workload the bench runs on the graph engine."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for name, wl in bench.WORKLOADS.items():
+        if wl["kind"] == "batched":
+            continue
+        n, p = wl["n"], wl["p"]
+        kf = bench.kernel_flops(wl)
+        assert kf["gram_partial"] == 3 * n * p * p and kf["update"] == 4 * n * p * p, name
+        assert kf["gram_partial"] + kf["update"] == 7 * n * p * p, name
