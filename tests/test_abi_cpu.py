@@ -151,3 +151,12 @@ def test_null_handle_calls_are_rejected(lib):
     assert lib.plam_solve(None, None, 0, None, 0, C.byref(info)) == _lib.PLAM_ERR_INVALID
     assert lib.plam_destroy(None) == _lib.PLAM_ERR_INVALID
     assert lib.plam_kernel_launches(None) == -1
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
+    """No CPU fallback: with the shared library absent the binding raises instead of computing
+    anything (the loader is pointed at an empty directory in a fresh module state)."""
+    from paper_1810_03930_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        _lib.load(str(tmp_path / "libplam.so"))
