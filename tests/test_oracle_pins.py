@@ -601,6 +601,26 @@ def test_parameter_study_conclusion_on_problem4(variant):
     assert all(k == 3000 for k in its["const"])
 
 
+@pytest.mark.parametrize("variant", ["plam", "pcal"])
+def test_feasibility_follows_kkt_on_problem1(variant):
+    """Section 5.3 (Fig. "feasibility", Lemma 2): on Problem 1 the feasibility violation
+    ||X^T X - I||_F decays nonmonotonically with the same tendency as the KKT violation.  From the
+    orthonormal start it first rises, then falls with the KKT value: over the run the two logs
+    correlate above 0.85 (0.91-0.94 on these instances), and it rises at many iterations."""
+    from workloads import multiplier_study_problems
+    p1, _ = multiplier_study_problems(count=3)
+    for L, X0 in p1:
+        obj = oo.DenseHartreeObjective(L, alpha=1.0, quad_scale=0.5)
+        r = op.solve(obj, X0, variant=variant, beta=obj.hess_norm_bound() + 0.1, tol=1e-8,
+                     maxit=3000)
+        assert r.converged
+        feas = np.array([h.feas for h in r.history[1:]])
+        kkt = np.array([h.kkt for h in r.history[1:]])
+        assert np.corrcoef(np.log10(feas), np.log10(kkt))[0, 1] > 0.85
+        assert np.sum(np.diff(feas) > 0) >= 10
+        assert feas[-1] < 1e-7 < feas.max()
+
+
 def test_multiplier_study_conclusion_on_problems_1_and_2():
     """Section 5.3 (Fig. "PCAL_multiplier"), qualitatively: the closed-form multiplier update of
     PLAM (eq. Lambda1) and PCAL (eq. lambda2) against dual ascent (PLAM-DA / PCAL-DA, the ALM
