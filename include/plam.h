@@ -124,11 +124,14 @@ typedef struct {
   int graph_iters;      /* iterations per captured CUDA graph in plam_solve; 0 = plain launches */
   int engine;           /* plam_solve engine: PLAM_ENGINE_AUTO, _GRAPH or _RESIDENT */
   int tensor_cores;     /* FP32 mode Grams on tcgen05 (kind::tf32, operands rounded to nearest TF32):
-                           0 off; 1 TF32, switching to compensated 3xTF32 (hi*hi + hi*lo + lo*hi) once
-                           the relative KKT value is below refine_switch; 2 always 3xTF32; -1 auto
-                           (= 1 when p >= 128).  Needs 16-byte aligned X and G with leading dimensions
+                           0 off; 1 TF32, switching for the rest of the run to compensated 3xTF32
+                           (hi*hi + hi*lo + lo*hi) once the relative KKT value is below refine_switch
+                           or has not halved its best value for 100 iterations (TF32 rounding can
+                           floor it above refine_switch); 2 always 3xTF32; -1 auto (= 1 when
+                           p >= 128).  Needs 16-byte aligned X and G with leading dimensions
                            that are multiples of 4, otherwise the CUDA-core Grams run */
-  double refine_switch; /* relative KKT value below which the tensor-core Grams are compensated */
+  double refine_switch; /* relative KKT value below which the tensor-core kernels are compensated
+                           (0: neither rule switches, plain TF32 throughout) */
   int orth_metrics;     /* 1 (default): plam_solve also evaluates f, the relative KKT value and the
                            feasibility ||Q^T Q - I||_F of the orthonormalised output Q
                            (plam_info_t.f_orth, kkt_orth, feas_orth); 0: skipped (NaN) — the
@@ -322,12 +325,33 @@ plam_status_t plam_time_kernels(plam_handle_t h, void* X, int64_t ldx, int iters
  * process exits; requests with 2 p^2 partial sums of one chunk above that
  * (p > 1024 in FP32 mode, p > 724 in FP64 mode) return PLAM_ERR_INVALID.
  * precision: PLAM_PREC_FP64 (X, G double) or PLAM_PREC_FP32 (float).  The
- * first call on a device looks up the array's device address (do it before
- * any stream capture).  The work is ordered on `stream` and the call returns
- * without synchronising.  All calls share the one array: calls whose kernels
- * overlap on the GPU race and must be serialised by the caller. */
+ * first call in each CUDA context looks up the array's device address and
+ * caches it under the context's id (do that first call before any stream
+ * capture; after cudaDeviceReset the next call looks it up again).  The work
+ * is ordered on `stream` and the call returns without synchronising.  All
+ * calls share the one array: calls whose kernels overlap on the GPU race and
+ * must be serialised by the caller.  Every error return leaves a message for
+ * plam_last_error(). */
 plam_status_t plam_grams_noalloc(int64_t n, int64_t p, int precision, const void* X, int64_t ldx,
                                  const void* G, int64_t ldg, double* B, double* C, void* stream);
+
+/* Internals of the latest evaluated iterate X^k of the handle's current run,
+ * for checking the kernels one by one (plam_step / pcal_step / the graph
+ * engine; after a resident-engine solve the contents are unspecified):
+ *   R        device, storage type, n x p, leading dimension ldr: the residual
+ *            R^k = G - X M = grad_X L_beta(X^k, Lambda) of eq. S1 that the
+ *            update kernel wrote (NULL: not copied);
+ *   M        device, storage type, p x p column-major (leading dimension p):
+ *            M = Lambda - beta (B - I) as the update consumed it (eqs.
+ *            Lambda1 / lambda2, S1; NULL: not copied);
+ *   colsums  host, 3p doubles: ||X_i||^2 (p), <X_i, R_i> (p), ||R_i||^2 (p),
+ *            the reduced column dots that give PCAL's column norms (Algorithm 3);
+ *   bb       host, 3 doubles: <S,S>, <S,Y>, <Y,Y> with S = X^k - X^{k-1},
+ *            Y = R^k - R^{k-1} (Section 5.1; zeros at k = 0).
+ * Synchronises the handle's stream.  PLAM_ERR_INVALID before any iterate was
+ * evaluated (after plam_create or plam_reset). */
+plam_status_t plam_last_iteration(plam_handle_t h, void* R, int64_t ldr, void* M, double* colsums,
+                                  double* bb);
 
 /* Copies up to `cap` per-iteration records (k, f, kkt_rel, feas, eta as 5
  * doubles each, in that order) of the current run to host memory `out`;
@@ -338,7 +362,8 @@ plam_status_t plam_history(plam_handle_t h, double* out, int cap, int* count);
  * counts its kernel nodes). */
 int64_t plam_kernel_launches(plam_handle_t h);
 
-/* Message of the last PLAM_ERR_CUDA on this thread (static storage). */
+/* Message of the last PLAM_ERR_CUDA on this thread, and of any error returned by
+ * plam_grams_noalloc (static storage; not cleared by successful calls). */
 const char* plam_last_error(void);
 
 /* Library version as major*10000 + minor*100 + patch. */

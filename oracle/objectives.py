@@ -27,6 +27,13 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
                      X^T X = I_p: half the sum of the p smallest eigenvalues of H
                      (Ky Fan), by a shift-invert Lanczos eigensolve (ARPACK) of a
                      sparse H.
+  separable_trace_min_optimum  the same optimum for H = L3 + Diag(V) with a
+                     separable potential V(x, y, z) = v_x(x) + v_y(y) + v_z(z):
+                     H is then the Kronecker sum of three 1D operators
+                     T_k = tridiag(-1, 2, -1) + Diag(v_k), so its eigenvalues are
+                     the sums mu_a + mu_b + mu_c of theirs (three symmetric
+                     tridiagonal eigensolves, LAPACK stev), and f* is half the
+                     sum of the p smallest such sums (Ky Fan), exact at any size.
 """
 from __future__ import annotations
 
@@ -198,19 +205,27 @@ class DenseHartreeObjective:
         return 2.0 * self.q * float(np.max(np.abs(np.linalg.eigvalsh(self.L))))
 
 
-def laplacian_3d(m: int) -> sp.csr_matrix:
-    """7-point Dirichlet Laplacian on an m^3 grid as I(x)I(x)T + I(x)T(x)I + T(x)I(x)I."""
-    T = sp.diags([-np.ones(m - 1), 2.0 * np.ones(m), -np.ones(m - 1)], [-1, 0, 1], format="csr")
-    Im = sp.identity(m, format="csr")
-    return (sp.kron(Im, sp.kron(Im, T)) + sp.kron(Im, sp.kron(T, Im)) + sp.kron(T, sp.kron(Im, Im))).tocsr()
+def laplacian_3d(m) -> sp.csr_matrix:
+    """7-point Dirichlet Laplacian on an m^3 grid (m an int) or an nx x ny x nz grid (m a tuple),
+    index x + nx (y + ny z), as I(x)I(x)T_x + I(x)T_y(x)I + T_z(x)I(x)I."""
+    nx, ny, nz = (m, m, m) if np.isscalar(m) else tuple(int(t) for t in m)
+
+    def T(k):
+        return sp.diags([-np.ones(k - 1), 2.0 * np.ones(k), -np.ones(k - 1)], [-1, 0, 1], format="csr")
+
+    Ix, Iy, Iz = (sp.identity(k, format="csr") for k in (nx, ny, nz))
+    return (sp.kron(Iz, sp.kron(Iy, T(nx))) + sp.kron(Iz, sp.kron(T(ny), Ix))
+            + sp.kron(T(nz), sp.kron(Iy, Ix))).tocsr()
 
 
 class Stencil3DObjective:
-    """f = 1/2 tr(X^T (L3 + Diag(V)) X) on an m^3 grid."""
+    """f = 1/2 tr(X^T (L3 + Diag(V)) X) on an m^3 grid (m an int) or an nx x ny x nz grid
+    (m a tuple: a slab of z-planes, with Dirichlet ends in every direction)."""
 
-    def __init__(self, m: int, V: np.ndarray):
-        self.m = int(m)
-        self.n = self.m ** 3
+    def __init__(self, m, V: np.ndarray):
+        self.grid = (m, m, m) if np.isscalar(m) else tuple(int(t) for t in m)
+        self.m = int(m) if np.isscalar(m) else self.grid
+        self.n = self.grid[0] * self.grid[1] * self.grid[2]
         self.V = np.asarray(V, dtype=np.float64)
         self.H = (laplacian_3d(self.m) + sp.diags(self.V)).tocsr()
 
@@ -251,3 +266,20 @@ def trace_min_optimum(H, p: int, shift: float | None = None):
     ev = spla.eigsh(H, k=p, sigma=shift, which="LM", return_eigenvectors=False)
     ev = np.sort(ev)
     return 0.5 * float(ev.sum()), ev
+
+
+def separable_trace_min_optimum(v_x, v_y, v_z, p: int):
+    """(f*, the p + 1 smallest eigenvalues) of H = L3 + Diag(V) on an nx x ny x nz grid with
+    V[x + nx (y + ny z)] = v_x[x] + v_y[y] + v_z[z]: H = T_z (x) I (x) I + I (x) T_y (x) I
+    + I (x) I (x) T_x with T_k = tridiag(-1, 2, -1) + Diag(v_k) (Dirichlet), whose eigenvalues
+    are all sums of one eigenvalue of each T_k; f* = 1/2 (lambda_1 + ... + lambda_p)."""
+    mus = []
+    for v in (v_x, v_y, v_z):
+        v = np.asarray(v, dtype=np.float64)
+        mus.append(sla.eigh_tridiagonal(2.0 + v, -np.ones(len(v) - 1), eigvals_only=True))
+    mx, my, mz = mus
+    sums = (mz[:, None, None] + my[None, :, None] + mx[None, None, :]).ravel()
+    k = min(p + 1, sums.size)
+    ev = np.sort(np.partition(sums, k - 1)[:k])
+    return 0.5 * float(ev[:p].sum()), ev
+

@@ -260,6 +260,17 @@ class Solver:
         check(st, "plam_time_kernels")
         return ms, done
 
+    def last_iteration(self):
+        """The latest evaluated iterate's residual R (a (p, n) tensor), update matrix M (p x p,
+        as a (p, p) tensor holding it column-major: M is symmetric), reduced column dots
+        (3p: ||X_i||^2, <X_i, R_i>, ||R_i||^2) and Barzilai-Borwein dots (<S,S>, <S,Y>, <Y,Y>)."""
+        torch = _torch()
+        R = torch.empty((self.p, self.n), dtype=self.dtype, device="cuda")
+        M = torch.empty((self.p, self.p), dtype=self.dtype, device="cuda")
+        st, cols, bb = _lib.plam_last_iteration(self.h, R.data_ptr(), self.n, M.data_ptr(), self.p)
+        check(st, "plam_last_iteration")
+        return R, M, cols, bb
+
     def history(self):
         return plam_history(self.h, self.params.maxit + 2)
 

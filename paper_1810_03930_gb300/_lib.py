@@ -94,6 +94,8 @@ SIGNATURES = {
     "plam_time_kernels": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int,
                                     C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "plam_history": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]),
+    "plam_last_iteration": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                      C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "plam_kernel_launches": (C.c_int64, [C.c_void_p]),
     "plam_solve_engine": (C.c_int, [C.c_void_p]),
     "plam_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(plam_batch_problem_t), C.c_int,
@@ -227,6 +229,16 @@ def plam_time_kernels(h, X: int, ldx: int, iters: int):
     done = C.c_int(0)
     st = load().plam_time_kernels(h, C.c_void_p(X), ldx, iters, ms, C.byref(done))
     return st, dict(zip(KERNEL_GROUPS, list(ms))), done.value
+
+
+def plam_last_iteration(h, R: int | None, ldr: int, M: int | None, p: int):
+    """(status, colsums[3p], bb[3]) of the latest evaluated iterate; R and M are device
+    pointers (or None) that receive the residual and the update matrix."""
+    import numpy as np
+    cols = (C.c_double * (3 * p))()
+    bb = (C.c_double * 3)()
+    st = load().plam_last_iteration(h, C.c_void_p(R or 0), ldr, C.c_void_p(M or 0), cols, bb)
+    return st, np.array(cols[:]), np.array(bb[:])
 
 
 def plam_history(h, cap: int):

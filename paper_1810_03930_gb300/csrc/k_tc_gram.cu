@@ -47,7 +47,7 @@ struct TcGramArgs {
   float* part;           // nchunks x 2p x p
   int* err;
   const DevState* st;    // iteration state (null outside the solver)
-  double refine_switch;  // 3xTF32 once the relative KKT value is below this (<= 0: never)
+  double refine_switch;  // > 0: 3xTF32 once the step kernel latched DevState.refine (<= 0: never)
   int force3;            // 1: always 3xTF32
 };
 
@@ -123,8 +123,7 @@ tc_gram_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   const uint32_t pad = (1024u - (smem_addr(smem_raw) & 1023u)) & 1023u;
   unsigned char* base = smem_raw + pad;
   // compensated (3xTF32) mode: decided once per launch from the device state
-  const bool split = a.force3 || (a.refine_switch > 0.0 && a.st != nullptr && a.st->k > 0 &&
-                                  a.st->kkt < a.refine_switch);
+  const bool split = a.force3 || (a.refine_switch > 0.0 && a.st != nullptr && a.st->refine);
   const uint32_t A_BYTES = kTcM * kTcK * 4;
   const uint32_t B_BYTES = (uint32_t)a.N * kTcK * 4;
   const uint32_t HALF = A_BYTES + B_BYTES;           // one (A, B) pair

@@ -139,8 +139,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t pad = (1024u - (smem_addr(smem_raw) & 1023u)) & 1023u;
   unsigned char* base = smem_raw + pad;
-  const bool split = a.force3 || (a.refine_switch > 0.0 && a.st->k > 0 &&
-                                  a.st->kkt < a.refine_switch);
+  const bool split = a.force3 || (a.refine_switch > 0.0 && a.st->refine);
   const int N = a.N;
   const uint32_t A = kUpM * kUpK * 4, BT = (uint32_t)N * kUpK * 4;
   const uint32_t STAGE = up_stage_bytes(N, split);

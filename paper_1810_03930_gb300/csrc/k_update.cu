@@ -296,6 +296,13 @@ step_size_kernel(int nrt, int nct, const T* __restrict__ colpart, const T* __res
     st->feas = feas;
     st->f = f;
     st->ss = ss; st->sy = sy; st->yy = yy;
+    if (!st->refine && prm.refine_switch > 0.0 && isfinite(kkt)) {
+      if (k == 0 || kkt < 0.5 * st->kkt_best) {
+        st->kkt_best = kkt;
+        st->k_best = k;
+      }
+      if (kkt < prm.refine_switch || k - st->k_best >= kStallIters) st->refine = 1;
+    }
     const int rec = st->nrec;
     if (rec < prm.hist_cap) {
       double* h = hist + (size_t)rec * 5;

@@ -217,6 +217,7 @@ IterParams iter_params(const plam_handle_s* h, int variant, int lambda2) {
   f_coefficients(h, &ip.f_xg, &ip.f_part);
   ip.lambda_da = h->prm.lambda_rule == PLAM_LAMBDA_DA;
   ip.lam = h->lam;
+  ip.refine_switch = h->use_tc ? h->prm.refine_switch : 0.0;
   return ip;
 }
 
@@ -694,14 +695,9 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
   h->ldw = round_up(n, 32);
   const int pi = (int)p;
   const int nt = (pi + kTile - 1) / kTile;
-  const int tiles = nt * (nt + 1) / 2 + nt * nt;
-  const int64_t target_ctas = 2 * 152;
-  int64_t nch = (target_ctas + tiles - 1) / tiles;
-  const int64_t max_ch = (n + kKStep - 1) / kKStep;
-  if (nch > max_ch) nch = max_ch;
-  if (nch < 1) nch = 1;
-  h->rows_per_chunk = round_up((n + nch - 1) / nch, kKStep);
-  h->nchunks = (int)((n + h->rows_per_chunk - 1) / h->rows_per_chunk);
+  const GramChunkPlan gcp = gram_chunk_plan(n, pi, true, device_sm_count(), 0);
+  h->rows_per_chunk = gcp.rows_per_chunk;
+  h->nchunks = gcp.nchunks;
   h->nrt = (int)((n + kTile - 1) / kTile);
   h->nct = nt;
   h->hist_cap = prm->maxit + 2;
@@ -1083,6 +1079,34 @@ plam_status_t plam_time_kernels(plam_handle_t h, void* X, int64_t ldx, int iters
   for (int i = 0; i < 6; ++i) ms[i] = it > 0 ? acc[i] / it : 0.0;
   *done = it;
   return st;
+}
+
+plam_status_t plam_last_iteration(plam_handle_t h, void* R, int64_t ldr, void* M,
+                                  double* colsums, double* bb) {
+  if (!h || (R && (ldr < h->n || !aligned(R, h->esz))) || (M && !aligned(M, h->esz)))
+    return PLAM_ERR_INVALID;
+  CK(cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const DevState s = *h->st_host;
+  if (s.nrec == 0) return PLAM_ERR_INVALID;            // no iterate evaluated since the reset
+  // the latest evaluated iterate: k - 1 after an update, k when the run stopped at k
+  const int k_last = s.k - (s.stop == kRunning ? 1 : 0);
+  const int64_t n = h->n, p = h->p;
+  if (R) {
+    const void* src = h->R[k_last & 1];
+    CK(cudaMemcpy2DAsync(R, (size_t)ldr * h->esz, src, (size_t)h->ldw * h->esz, (size_t)n * h->esz,
+                         (size_t)p, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  if (M)
+    CK(cudaMemcpyAsync(M, h->Mt, (size_t)p * p * h->esz, cudaMemcpyDeviceToDevice, h->stream));
+  if (colsums)
+    CK(cudaMemcpyAsync(colsums, h->sums, (size_t)kColDots * p * sizeof(double),
+                       cudaMemcpyDeviceToHost, h->stream));
+  if (bb)
+    CK(cudaMemcpyAsync(bb, h->sums + kColDots * p, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                       h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return PLAM_OK;
 }
 
 plam_status_t plam_history(plam_handle_t h, double* out, int cap, int* count) {

@@ -38,7 +38,16 @@ struct DevState {
   double feas;    // ||X^T X - I||_F there
   double f;       // f there
   double ss, sy, yy;  // latest Barzilai-Borwein inner products
+  int refine;     // 1 once the tensor-core kernels run compensated (latched for the run)
+  int k_best;     // iteration of the last halving of the best relative KKT value
+  double kkt_best;
 };
+
+// The plain-TF32 phase of the tensor-core kernels hands over to the compensated phase
+// when the relative KKT value falls below refine_switch, or when it stalls: no halving of
+// the best value seen for kStallIters iterations (TF32 rounding can floor the KKT value
+// above refine_switch, and the Barzilai-Borwein steps are not monotone).
+constexpr int kStallIters = 100;
 
 // Parameters of one iteration, passed by value.
 struct IterParams {
@@ -57,6 +66,7 @@ struct IterParams {
   double f_xg, f_part;   // f = f_xg <X, G> + f_part (sum of the objective's f partials)
   int lambda_da;         // 1: dual ascent Lambda^k = Lambda^{k-1} - beta (B^k - I) (PLAM-DA, PCAL-DA)
   double* lam;           // p x p FP64 multiplier carried across iterations (dual ascent only)
+  double refine_switch;  // <= 0: the compensated phase never starts on its own (see DevState.refine)
 };
 
 // Number of per-column dot products written by the update kernel and the
@@ -143,6 +153,31 @@ cudaError_t launch_feas(int p, const double* B, double* col, double* out, cudaSt
 // Message returned by plam_last_error() on this host thread ("what: detail").
 void set_last_error(const char* what, const char* detail);
 
+// Row chunking of the CUDA-core split-K Grams (one rule for every entry point, so that
+// plam_grams and plam_grams_noalloc reduce in the same order whenever max_chunks does not
+// bind): about two CTAs per SM over the (upper) tiles of X^T X and, with_g, the tiles of
+// X^T G; chunks are whole kKStep-row stages; at most max_chunks chunks (<= 0: no cap).
+struct GramChunkPlan {
+  int64_t rows_per_chunk;
+  int nchunks;
+};
+inline GramChunkPlan gram_chunk_plan(int64_t n, int p, bool with_g, int sms, int64_t max_chunks) {
+  const int nt = (p + kTile - 1) / kTile;
+  const int64_t tiles = (int64_t)nt * (nt + 1) / 2 + (with_g ? (int64_t)nt * nt : 0);
+  const int64_t target_ctas = 2 * (int64_t)(sms > 0 ? sms : 1);
+  int64_t nch = (target_ctas + tiles - 1) / tiles;
+  const int64_t by_rows = (n + kKStep - 1) / kKStep;
+  if (nch > by_rows) nch = by_rows;
+  if (max_chunks > 0 && nch > max_chunks) nch = max_chunks;
+  if (nch < 1) nch = 1;
+  int64_t rows = (n + nch - 1) / nch;
+  rows = (rows + kKStep - 1) / kKStep * kKStep;
+  GramChunkPlan pl;
+  pl.rows_per_chunk = rows;
+  pl.nchunks = (int)((n + rows - 1) / rows);
+  return pl;
+}
+
 // Resident (persistent, cooperative) solve: FP32, p <= 64, Hartree or dense.
 struct ResidentLaunch {
   int64_t n;
@@ -187,7 +222,7 @@ struct TcGramPlan {
 };
 void tc_gram_plan(int64_t n, int p, int with_g, TcGramPlan* pl);
 bool tc_gram_supported(const void* X, int64_t ldx, const void* G, int64_t ldg);
-// st / refine_switch: compensated 3xTF32 once st->kkt < refine_switch (st may be
+// st / refine_switch: compensated 3xTF32 once st->refine is latched (st may be
 // null); force3 = 1 always uses it.
 cudaError_t launch_tc_gram(int64_t n, int p, const float* X, int64_t ldx, const float* G,
                            int64_t ldg, const TcGramPlan& pl, float* part, int* err,

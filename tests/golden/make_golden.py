@@ -8,6 +8,13 @@
                                       64^3 plus the seeded potential V iid U[0,1], p = 256):
                                       half the sum of the 256 smallest eigenvalues (Ky Fan),
                                       oracle.objectives.trace_min_optimum (about 40 minutes).
+  stencil3d_separable_n2097152_p1024_optimum.json
+                                      f* of the 128^3, p = 1024 companion workload whose potential
+                                      is separable, V = v_x(x) + v_y(y) + v_z(z) (each v_k iid
+                                      U[0, 1/3], seeded stream 3 of configuration 5): half the sum
+                                      of the 1024 smallest eigenvalues, exact through the
+                                      Kronecker-sum spectrum (oracle.objectives.
+                                      separable_trace_min_optimum, seconds).
   section54_n10000_p1000.json         Section 5.4's parallel forms of Problems 1 (blocks of 5
                                       rows, alpha = 1, q = 1/2) and 2 (tridiagonal A, random
                                       G_lin), n = 10000, p = 1000, seeded starts: the oracle's PCAL
@@ -15,7 +22,7 @@
                                       iterations, f and feasibility (a few minutes).
 
 Run from the repository root:
-    python tests/golden/make_golden.py [hartree1d] [stencil3d] [section54]
+    python tests/golden/make_golden.py [hartree1d] [stencil3d] [section54] [separable128]
 """
 import json
 import os
@@ -28,8 +35,8 @@ sys.path.insert(0, ROOT)
 
 from oracle import objectives as oo  # noqa: E402
 from oracle import plam as op  # noqa: E402
-from workloads import (workload_block_hartree, workload_hartree1d, workload_stencil3d,  # noqa: E402
-                       workload_tridiag_linear)
+from workloads import (stencil3d_separable_potential, workload_block_hartree,  # noqa: E402
+                       workload_hartree1d, workload_stencil3d, workload_tridiag_linear)
 
 
 def hartree_optimum():
@@ -54,6 +61,21 @@ def stencil_optimum():
             "lambda_1": float(ev[0]), "lambda_p": float(ev[-1]),
             "oracle_seconds": round(time.time() - t0, 1),
             "source": "oracle/objectives.py trace_min_optimum() run by tests/golden/make_golden.py"}
+
+
+def separable128_optimum():
+    m, p = 128, 1024
+    t0 = time.time()
+    V, vx, vy, vz = stencil3d_separable_potential(m)
+    f, ev = oo.separable_trace_min_optimum(vx, vy, vz, p)
+    return {"workload": "stencil3d_separable_n2097152_p1024", "n": m ** 3, "p": p, "m": m,
+            "potential": "V[x + m (y + m z)] = v_x[x] + v_y[y] + v_z[z], v_k iid U[0, 1/3], "
+                         "workloads.stencil3d_separable_potential (seed stream 3 of config 5)",
+            "f_star": f, "lambda_1": float(ev[0]), "lambda_p": float(ev[p - 1]),
+            "lambda_p_plus_1": float(ev[p]), "gap": float(ev[p] - ev[p - 1]),
+            "oracle_seconds": round(time.time() - t0, 1),
+            "source": "oracle/objectives.py separable_trace_min_optimum() run by "
+                      "tests/golden/make_golden.py"}
 
 
 def section54_runs():
@@ -84,6 +106,11 @@ if __name__ == "__main__":
     if "section54" in which:
         d = section54_runs()
         with open(os.path.join(HERE, "section54_n10000_p1000.json"), "w") as fh:
+            json.dump(d, fh, indent=1)
+        print(d)
+    if "separable128" in which:
+        d = separable128_optimum()
+        with open(os.path.join(HERE, "stencil3d_separable_n2097152_p1024_optimum.json"), "w") as fh:
             json.dump(d, fh, indent=1)
         print(d)
     if "stencil3d" in which:

@@ -150,6 +150,7 @@ def test_null_handle_calls_are_rejected(lib):
     assert lib.pcal_step(None, None, 0, C.byref(info)) == _lib.PLAM_ERR_INVALID
     assert lib.plam_solve(None, None, 0, None, 0, C.byref(info)) == _lib.PLAM_ERR_INVALID
     assert lib.plam_destroy(None) == _lib.PLAM_ERR_INVALID
+    assert lib.plam_last_iteration(None, None, 0, None, None, None) == _lib.PLAM_ERR_INVALID
     assert lib.plam_kernel_launches(None) == -1
 
 

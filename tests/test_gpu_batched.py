@@ -5,7 +5,7 @@ import pytest
 
 from oracle import objectives as oo
 from oracle import plam as op
-from tests.gpu_helpers import rel_err, to_host
+from tests.gpu_helpers import ITER_FACTOR, assert_entrywise, to_host
 from workloads import batched_shapes, workload_batched_problem
 
 pytestmark = pytest.mark.gpu
@@ -56,7 +56,7 @@ def test_batched_three_iterations_match_oracle():
         ref = op.solve(oo.TraceObjective(A), X0f, variant="pcal", beta=1.5, tol=0.0, maxit=3)
         assert info.iters == 3 and info.status == 2          # PLAM_ERR_NOT_CONVERGED at maxit
         X3 = to_host(Xd, w.n)
-        assert rel_err(X3 - X0f, ref.X - X0f) <= 1e-4, w.name
+        assert_entrywise(X3 - X0f, ref.X - X0f, ITER_FACTOR * 1e-4, what=w.name)
         assert abs(info.eta - ref.history[2].eta) <= 1e-4 * ref.history[2].eta
         assert abs(info.kkt_rel - ref.history[3].kkt) <= 1e-4 * ref.history[3].kkt
     bs.close()

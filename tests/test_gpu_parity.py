@@ -19,7 +19,7 @@ import pytest
 from oracle import kernels as ok
 from oracle import objectives as oo
 from oracle import plam as op
-from tests.gpu_helpers import gpu_solver, rel_err, to_dev, to_host
+from tests.gpu_helpers import ITER_FACTOR, assert_entrywise, gpu_solver, to_dev, to_host
 from workloads import (gaussian_symmetric, orthonormal_start, rng_for, workload_dense_trace,
                        workload_hartree1d, workload_stencil3d)
 
@@ -89,7 +89,7 @@ def test_energy_grad_matches_oracle(precision, kind):
     Gref = obj.grad(X)
     fref = obj.value(X)
     tol = (1e-10 if kind == "hartree1d" else 1e-12) if precision == "fp64" else 2e-6
-    assert rel_err(G, Gref) <= tol
+    assert_entrywise(G, Gref, tol, what=f"{kind} gradient")
     assert abs(f - fref) <= tol * max(1.0, abs(fref)) * 10
     s.close()
 
@@ -128,7 +128,7 @@ def test_stencil_gradient_on_non_cubic_grids(precision, grid):
     G = to_host(Gd, n)
     Gref = L3 @ X + V[:, None] * X
     tol = 1e-14 if precision == "fp64" else 1e-6
-    assert rel_err(G, Gref) <= tol
+    assert_entrywise(G, Gref, tol, what=f"stencil gradient on {grid}")
     assert abs(f - 0.5 * np.sum(X * Gref)) <= 10 * tol * abs(0.5 * np.sum(X * Gref))
     s.close()
 
@@ -149,7 +149,7 @@ def test_one_iteration_matches_oracle_fp64(variant, rule, n, p):
     st, info = s.step(Xd, variant)
     assert st == 0
     X1 = to_host(Xd, n)
-    assert rel_err(X1, ref.X) <= 1e-11
+    assert_entrywise(X1, ref.X, 1e-11, what="X^1")
     h0 = ref.history[0]
     assert abs(info.kkt_rel - h0.kkt) <= 1e-12
     assert abs(info.feas - h0.feas) <= 1e-11 * max(1.0, h0.feas)
@@ -176,7 +176,7 @@ def test_first_twenty_step_sizes_match_oracle_fp64(variant):
     np.testing.assert_allclose(hist[:20, 4], eta_ref, rtol=1e-9)
     np.testing.assert_allclose(hist[:, 2], kkt_ref, rtol=1e-8)
     np.testing.assert_allclose(hist[:, 1], f_ref, rtol=1e-11)
-    assert rel_err(to_host(Xd, w.n), ref.X) <= 1e-9
+    assert_entrywise(to_host(Xd, w.n), ref.X, ITER_FACTOR * 1e-9, what="X^20")
     s.close()
 
 
@@ -217,6 +217,87 @@ def test_first_twenty_step_sizes_match_oracle_every_rule(variant, rule):
     hr = r.history()
     np.testing.assert_allclose(hr[:6, 4], eta_ref[:6], rtol=1e-3)
     r.close()
+
+
+# ---------------------------------------------------------------- single kernels, entry by entry
+
+
+@pytest.mark.parametrize("precision,tc", [("fp64", "off"), ("fp32", "off"), ("fp32", "tf32")])
+@pytest.mark.parametrize("variant", ["plam", "pcal"])
+def test_single_kernels_match_their_definitions(precision, tc, variant):
+    """Each kernel of an iteration against the definition of its step (oracle.kernels), fed the
+    inputs the GPU itself used, so that one kernel is checked at a time (n = 777: a ragged last
+    row tile; p = 130: a ragged column tile of both the CUDA-core and the tensor-core kernels):
+      Grams + multiplier   M = Lambda - beta (B - I) (eqs. Lambda1 / lambda2, S1) vs ok.multiplier
+      update               R = G - X M_gpu (eq. S1) vs ok.update
+      column dots          ||X_i||^2, <X_i, R_i>, ||R_i||^2 of R_gpu vs ok.column_dots
+      primal update        X^{k+1} from (X^k, R_gpu, eta_gpu) vs ok.primal_update
+      Barzilai-Borwein     <S,S>, <S,Y>, <Y,Y> of (X^1, R^1_gpu, X^0, R^0_gpu) vs ok.bb_dots
+      final Cholesky-QR    R = Q^T X of the GPU's Q vs ok.cholesky_qr_factor (Householder)."""
+    n, p, beta = 777, 130, 1.5
+    w = workload_dense_trace(n, p)
+    A = w.A if precision == "fp64" else w.A.astype(np.float32).astype(np.float64)
+    obj = oo.TraceObjective(A)
+    X0 = w.X0 + 0.02 * rng_for(13, 2).standard_normal(w.X0.shape)
+    if precision == "fp32":
+        X0 = X0.astype(np.float32).astype(np.float64)
+    # FP64: rounding of sums of n (Grams) or p (update) products; FP32 CUDA cores: single-precision
+    # sums; TF32 tensor cores: operands rounded to 2^-11 (M and the update product)
+    tol_m, tol_r, tol_x = {("fp64", "off"): (1e-12, 1e-12, 1e-13), ("fp32", "off"): (2e-6, 2e-6, 1e-6),
+                           ("fp32", "tf32"): (2e-3, 2e-3, 1e-6)}[(precision, tc)]
+    s = gpu_solver(w, precision, variant=variant, beta=beta, tol=0.0, maxit=5, final_orth=0,
+                   tensor_cores=tc, refine_switch=0.0, engine="graph")
+    Xd = to_dev(X0, s)
+    Gd = s.new_matrix()
+    Xs, Rs = [X0], []
+    for k in range(2):
+        # the gradient kernel's own output (checked against the oracle by the gradient tests)
+        # feeds the definitions below, so that each of the other kernels is checked alone
+        s.energy_grad(Xd, Gd)
+        G = to_host(Gd, n)
+        assert_entrywise(G, obj.grad(Xs[-1]), 1e-12 if precision == "fp64" else 2e-5,
+                         what=f"G at k={k}")
+        st, info = s.step(Xd, variant)
+        assert st == 0 and info.iters == k + 1
+        Rd, Md, cols, bb = s.last_iteration()
+        Xk = Xs[-1]
+        R = to_host(Rd, n)
+        M = Md.double().cpu().numpy()          # column-major p x p, symmetric
+        lam_rule = "lambda2" if variant == "pcal" else "lambda1"
+        M_ref = ok.multiplier(Xk, G, beta, variant=variant, lambda_rule=lam_rule)[3]
+        # M's entries are O(p^{-1/2}) sums of n products: the scale is the RMS of M's column
+        assert_entrywise(M.T, M_ref, tol_m, what=f"M at k={k}")
+        R_ref, _ = ok.update(Xk, G, M, np.zeros((p, p)))
+        assert_entrywise(R, R_ref, tol_r, scale=np.sqrt(np.mean(G * G, axis=0))[None, :],
+                         what=f"R at k={k}")
+        xx, xr, rr = ok.column_dots(Xk, R)
+        dots_tol = 1e-12 if precision == "fp64" else 2e-6
+        assert_entrywise(cols[:p], xx, dots_tol, scale=np.mean(xx), what="||X_i||^2")
+        assert_entrywise(cols[p:2 * p], xr, dots_tol, scale=np.sqrt(np.mean(xx) * np.mean(rr)),
+                         what="<X_i, R_i>")
+        assert_entrywise(cols[2 * p:], rr, dots_tol, scale=np.mean(rr), what="||R_i||^2")
+        X1 = to_host(Xd, n)
+        assert_entrywise(X1, ok.primal_update(Xk, R, info.eta, variant=variant), tol_x,
+                         what=f"X^{k + 1}")
+        if k == 1:
+            ss, sy, yy = ok.bb_dots(Xk, R, Xs[0], Rs[0])
+            bb_tol = 1e-10 if precision == "fp64" else 1e-4
+            np.testing.assert_allclose(bb, [ss, sy, yy], rtol=bb_tol,
+                                       atol=bb_tol * np.sqrt(ss * yy))
+        else:
+            assert np.all(bb == 0.0)
+        Xs.append(X1)
+        Rs.append(R)
+    # the final orthonormalisation: Q = X R^{-1} gives R = Q^T X
+    Qd = s.new_matrix(dtype=torch.float64)
+    s.orthonormalize(Xd, Qd)
+    Q = to_host(Qd, n)
+    Xlast = to_host(Xd, n)
+    Rq = Q.T @ Xlast
+    R_ref = ok.cholesky_qr_factor(Xlast)
+    assert_entrywise(np.triu(Rq), R_ref, 1e-12, scale=np.abs(np.diag(R_ref)).mean(), what="R")
+    assert np.abs(np.tril(Rq, -1)).max() <= 1e-12 * np.abs(np.diag(R_ref)).max()
+    s.close()
 
 
 # ---------------------------------------------------------------- full solves
@@ -495,7 +576,7 @@ def test_leading_dimension_padding():
     Xd = to_dev(w.X0, s, ld=320)
     Xd[:, 300:] = float("nan")       # padding must never be read
     st, info = s.solve(Xd)
-    assert rel_err(to_host(Xd, 300), ref.X) <= 1e-11
+    assert_entrywise(to_host(Xd, 300), ref.X, ITER_FACTOR * 1e-11, what="X^3 with padding")
     s.close()
 
 
@@ -551,7 +632,7 @@ def test_resident_and_graph_engines_agree_on_early_iterations():
     np.testing.assert_allclose(hr[:, 2], hg[:, 2], rtol=1e-3)     # KKT
     np.testing.assert_allclose(hr[:8, 4], hg[:8, 4], rtol=1e-3)   # eta
     np.testing.assert_allclose(hr[:, 1], hg[:, 1], rtol=1e-5)     # f
-    assert rel_err(xr, xg) <= 1e-3
+    assert_entrywise(xr, xg, ITER_FACTOR * 1e-3, what="resident vs graph X^8")
 
 
 def test_resident_dense_small():
@@ -586,7 +667,8 @@ def test_resident_engine_odd_shapes_match_graph_engine(n, p):
         s.close()
     np.testing.assert_allclose(out["resident"][0][:, 2], out["graph"][0][:, 2], rtol=2e-3)
     np.testing.assert_allclose(out["resident"][0][:, 1], out["graph"][0][:, 1], rtol=1e-5)
-    assert rel_err(out["resident"][1], out["graph"][1]) <= 2e-3
+    assert_entrywise(out["resident"][1], out["graph"][1], ITER_FACTOR * 2e-3,
+                     what="resident vs graph X^6")
 
 
 def test_resident_engine_rejects_what_it_cannot_run():
@@ -636,7 +718,7 @@ def test_dual_ascent_iterations_match_oracle(variant, precision):
     tol = 1e-9 if precision == "fp64" else 2e-4
     np.testing.assert_allclose(hist[:20, 4], [h.eta for h in ref.history[:20]], rtol=tol)
     np.testing.assert_allclose(hist[:, 2], [h.kkt for h in ref.history], rtol=tol)
-    assert rel_err(to_host(Xd, w.n), ref.X) <= tol
+    assert_entrywise(to_host(Xd, w.n), ref.X, ITER_FACTOR * tol, what="X^20 (dual ascent)")
     s.close()
 
 
@@ -656,7 +738,7 @@ def test_exchange_energy_and_solve_match_oracle(precision):
     Gd = s.new_matrix()
     f = s.energy_grad(to_dev(X, s), Gd)
     tol = 1e-10 if precision == "fp64" else 2e-6
-    assert rel_err(to_host(Gd, w.n), obj.grad(X)) <= tol
+    assert_entrywise(to_host(Gd, w.n), obj.grad(X), tol, what="exchange gradient")
     assert abs(f - obj.value(X)) <= tol * abs(obj.value(X)) * 10
     s.close()
     ref = op.solve(obj, w.X0, variant="pcal", beta=100.0, tol=1e-9, maxit=20000, record=False)

@@ -161,7 +161,7 @@ def test_tensor_core_update_three_iterations(n, p, variant, tc, tol):
     with a ragged tail (p = 130), a single column (p = 1)."""
     from oracle import objectives as oo
     from oracle import plam as op
-    from tests.gpu_helpers import gpu_solver, rel_err, to_host
+    from tests.gpu_helpers import ITER_FACTOR, assert_entrywise, gpu_solver, to_host
     w, X0 = _dense_case(n, p, 17)
     obj = oo.TraceObjective(w.A)
     beta = 1.5
@@ -173,7 +173,7 @@ def test_tensor_core_update_three_iterations(n, p, variant, tc, tol):
     hist = s.history()
     X3 = to_host(Xd, n)
     X0f = X0.astype(np.float32).astype(np.float64)
-    assert rel_err(X3 - X0f, ref.X - X0) <= 5 * tol
+    assert_entrywise(X3 - X0f, ref.X - X0, ITER_FACTOR * 5 * tol, what="X^3 - X^0")
     eta_ref = np.array([h.eta for h in ref.history[:3]])
     kkt_ref = np.array([h.kkt for h in ref.history])
     np.testing.assert_allclose(hist[:3, 4], eta_ref, rtol=5 * tol)
@@ -205,7 +205,7 @@ def test_tensor_core_update_persistent_tiles(m, p, tc, tol):
     two-slot epilogue ring; three PCAL iterations on the 3D stencil against the FP64 oracle."""
     from oracle import objectives as oo
     from oracle import plam as op
-    from tests.gpu_helpers import gpu_solver, rel_err, to_host
+    from tests.gpu_helpers import ITER_FACTOR, assert_entrywise, gpu_solver, to_host
     from workloads import workload_stencil3d
     w = workload_stencil3d(m=m, p=p)
     obj = oo.Stencil3DObjective(w.m, w.V.astype(np.float32).astype(np.float64))
@@ -219,7 +219,7 @@ def test_tensor_core_update_persistent_tiles(m, p, tc, tol):
     hist = s.history()
     X3 = to_host(Xd, n)
     X0f = X0.astype(np.float32).astype(np.float64)
-    assert rel_err(X3 - X0f, ref.X - X0) <= 5 * tol
+    assert_entrywise(X3 - X0f, ref.X - X0, ITER_FACTOR * 5 * tol, what="X^3 - X^0")
     # eta^2 = <Y,Y>/|<S,Y>| (BB2) divides differences of residuals, Y = R^2 - R^1: the TF32 error
     # of R is amplified by |R| / |Y| (up to ~10% here), so plain TF32 is held to eta^0, eta^1
     ne = 3 if tc == "3xtf32" else 2

@@ -298,20 +298,30 @@ def test_gradient_finite_difference(kind):
 
 def test_stencil3d_operator_brute_force():
     """L3 + V against a dense matrix assembled point by point from the 7-point rule (m = 3)."""
-    m = 3
-    n = m ** 3
+    _stencil_brute_force((3, 3, 3))
+
+
+def test_stencil3d_operator_brute_force_non_cubic():
+    """The same on a slab whose three axes all differ (2 x 3 x 4), as the oracle's timed sample
+    of the 128^3 workload (its first z-planes) uses."""
+    _stencil_brute_force((2, 3, 4))
+
+
+def _stencil_brute_force(grid):
+    nx, ny, nz = grid
+    n = nx * ny * nz
     V = np.random.default_rng(5).random(n)
     H = np.zeros((n, n))
-    for z in range(m):
-        for y in range(m):
-            for x in range(m):
-                i = x + m * y + m * m * z
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                i = x + nx * y + nx * ny * z
                 H[i, i] = 6.0 + V[i]
                 for dx, dy, dz in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
                     xx, yy, zz = x + dx, y + dy, z + dz
-                    if 0 <= xx < m and 0 <= yy < m and 0 <= zz < m:
-                        H[i, xx + m * yy + m * m * zz] = -1.0
-    obj = oo.Stencil3DObjective(m, V)
+                    if 0 <= xx < nx and 0 <= yy < ny and 0 <= zz < nz:
+                        H[i, xx + nx * yy + nx * ny * zz] = -1.0
+    obj = oo.Stencil3DObjective(nx if nx == ny == nz else grid, V)
     X = np.random.default_rng(6).standard_normal((n, 3))
     np.testing.assert_allclose(obj.grad(X), H @ X, rtol=1e-14, atol=1e-14)
 
@@ -473,6 +483,40 @@ def test_trace_min_optimum_against_dense_eigensolve_and_closed_form():
     closed = sorted(one[a] + one[b] + one[d] + c for a in range(m) for b in range(m) for d in range(m))
     f2, _ = oo.trace_min_optimum(oo.Stencil3DObjective(m, np.full(m ** 3, c)).H, p)
     assert abs(f2 - 0.5 * sum(closed[:p])) <= 1e-11 * f2
+
+
+def test_separable_potential_optimum_against_dense_eigensolve_and_closed_form():
+    """oracle.objectives.separable_trace_min_optimum (three tridiagonal eigensolves and the
+    Kronecker-sum spectrum) against (i) a dense LAPACK eigensolve of the assembled operator on
+    a non-cubic grid, assembled point by point from the generator's V (so a potential laid out
+    with another axis fastest, or a dropped axis term, would move the spectrum), and (ii) the
+    constant-potential closed form, v_k = c / 3."""
+    from workloads import separable_potential
+    rng = np.random.default_rng(11)
+    nx, ny, nz, p = 7, 5, 6, 17
+    V, vx, vy, vz = separable_potential(nx, ny, nz, rng)
+    import scipy.sparse as sp
+
+    def second_difference(m):
+        return sp.diags([-np.ones(m - 1), 2 * np.ones(m), -np.ones(m - 1)], [-1, 0, 1])
+
+    Ix, Iy, Iz = sp.identity(nx), sp.identity(ny), sp.identity(nz)
+    # point by point: index x + nx (y + ny z), x fastest
+    H = (sp.kron(Iz, sp.kron(Iy, second_difference(nx))) +
+         sp.kron(Iz, sp.kron(second_difference(ny), Ix)) +
+         sp.kron(second_difference(nz), sp.kron(Iy, Ix)) + sp.diags(V)).toarray()
+    for z, y, x in ((0, 0, 1), (3, 2, 6), (5, 4, 0)):
+        assert abs(V[x + nx * (y + ny * z)] - (vx[x] + vy[y] + vz[z])) <= 1e-15
+    ev_dense = np.linalg.eigvalsh(H)
+    f, ev = oo.separable_trace_min_optimum(vx, vy, vz, p)
+    np.testing.assert_allclose(ev, ev_dense[:p + 1], rtol=1e-13, atol=1e-13)
+    assert abs(f - 0.5 * ev_dense[:p].sum()) <= 1e-13 * abs(f)
+    m, c = 9, 0.45
+    one = [2 - 2 * math.cos(math.pi * t / (m + 1)) for t in range(1, m + 1)]
+    closed = sorted(one[a] + one[b] + one[d] + c for a in range(m) for b in range(m) for d in range(m))
+    f3, ev3 = oo.separable_trace_min_optimum(*(np.full(m, c / 3.0),) * 3, 30)
+    assert abs(f3 - 0.5 * sum(closed[:30])) <= 1e-13 * f3
+    np.testing.assert_allclose(ev3, closed[:31], rtol=1e-13)
 
 
 @pytest.mark.parametrize("variant", ["plam", "pcal"])

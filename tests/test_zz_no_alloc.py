@@ -1,9 +1,12 @@
 """plam_grams_noalloc: the Grams for callers that cannot allocate device memory.
 
 It must give the same B = X^T X and C = X^T G as plam_grams (the handle-based
-entry point) within the Gram tolerances of tests/test_gpu_parity.py, on two
-calls in a row with different shapes (the second call reuses the static
-scratch the first one filled), and reject requests beyond its scratch.
+entry point): bit for bit where its scratch does not cap the row chunks (both
+entry points plan the chunks with one rule), within the Gram tolerances of
+tests/test_gpu_parity.py where it does, on two calls in a row with different
+shapes (the second call reuses the static scratch the first one filled); it
+must handle the largest p its scratch admits and reject larger requests, and
+every rejection leaves a message.
 Collected last on purpose (file name), so a failure here leaves every other
 test already run.
 """
@@ -20,7 +23,7 @@ def _handle_grams(precision, X, G):
     from workloads import Workload
     n, p = X.shape
     w = Workload(name="grams", kind="hartree1d", n=n, p=p, X0=X)
-    s = gpu_solver(w, precision)
+    s = gpu_solver(w, precision, tensor_cores="off")
     B, Cm = s.grams(to_dev(X, s), to_dev(G, s) if G is not None else None)
     s.close()
     return B.cpu().numpy(), (Cm.cpu().numpy() if Cm is not None else None)
@@ -48,6 +51,7 @@ def _noalloc_grams(precision, X, G):
                                  torch.cuda.current_stream().cuda_stream)
     assert st == _lib.PLAM_OK, _lib.load().plam_last_error()
     torch.cuda.synchronize()
+    del Xd, Gd
     # column-major p x p outputs held in (p, p) row-major tensors: transpose back
     return B.t().cpu().numpy(), (Cm.t().cpu().numpy() if Cm is not None else None)
 
@@ -71,11 +75,34 @@ def test_noalloc_grams_match_plam_grams_on_two_calls_in_a_row(precision):
                 G = G.astype(np.float32).astype(np.float64)
         B_ref, C_ref = _handle_grams(precision, X, G)
         B, Cm = _noalloc_grams(precision, X, G)
-        assert _close(B, B_ref, n, precision), (n, p)
+        # the scratch does not cap these chunkings: the same reduction order, bit for bit
+        assert np.array_equal(B, B_ref), (n, p)
         if with_g:
-            assert _close(Cm, C_ref, n, precision), (n, p)
+            assert np.array_equal(Cm, C_ref), (n, p)
+            assert _close(Cm, X.T @ G, n, precision)
         # and against the definition
         assert _close(B, X.T @ X, n, precision)
+
+
+@pytest.mark.parametrize("precision,n,p", [("fp64", 1500, 724), ("fp32", 2100, 1024),
+                                           ("fp64", 40000, 300)])
+def test_noalloc_grams_at_the_largest_p_and_where_the_scratch_caps_the_chunks(precision, n, p):
+    """p = 724 (FP64) and p = 1024 (FP32) fill the 8 MiB scratch with one row chunk; at FP64
+    p = 300 the handle's rule asks for 8 chunks and the scratch holds 5, so the cap binds."""
+    rng = np.random.default_rng(7 + p)
+    X = rng.standard_normal((n, p))
+    G = rng.standard_normal((n, p)) if p < 1000 else None
+    if precision == "fp32":
+        X = X.astype(np.float32).astype(np.float64)
+    for _ in range(2):          # two calls in a row on the shared scratch
+        B, Cm = _noalloc_grams(precision, X, G)
+        assert _close(B, X.T @ X, n, precision), (n, p)
+        if G is not None:
+            assert _close(Cm, X.T @ G, n, precision), (n, p)
+    B_ref, C_ref = _handle_grams(precision, X, G)
+    assert _close(B, B_ref, n, precision)
+    if G is not None:
+        assert _close(Cm, C_ref, n, precision)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
@@ -91,3 +118,12 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     st = _lib.plam_grams_noalloc(2000, 800, _lib.PLAM_PREC_FP64, Xd.data_ptr(), 2000, None, 0,
                                  Bd.data_ptr(), None, 0)
     assert st == _lib.PLAM_ERR_INVALID
+    st = _lib.plam_grams_noalloc(2000, 725, _lib.PLAM_PREC_FP64, Xd.data_ptr(), 2000, None, 0,
+                                 Bd.data_ptr(), None, 0)         # p = 725: one past the FP64 limit
+    assert st == _lib.PLAM_ERR_INVALID
+    assert b"8 MiB" in _lib.load().plam_last_error()
+    # argument errors leave their own message (not a stale one)
+    st = _lib.plam_grams_noalloc(2000, 8, _lib.PLAM_PREC_FP64, Xd.data_ptr(), 1999, None, 0,
+                                 Bd.data_ptr(), None, 0)
+    assert st == _lib.PLAM_ERR_INVALID
+    assert b"leading dimension" in _lib.load().plam_last_error()

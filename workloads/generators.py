@@ -35,6 +35,7 @@ __all__ = [
     "batched_shapes", "workload_batched_problem", "workload_by_config",
     "workload_ks_exchange", "parameter_study_problems", "multiplier_study_problems",
     "workload_block_hartree", "workload_tridiag_linear", "paper_p4_matrices",
+    "separable_potential", "stencil3d_separable_potential",
 ]
 
 
@@ -75,6 +76,17 @@ def gaussian_start(n: int, p: int, rng: np.random.Generator) -> np.ndarray:
 def uniform_potential(n: int, rng: np.random.Generator) -> np.ndarray:
     """Diagonal potential V, iid U[0,1]."""
     return rng.random(n)
+
+
+def separable_potential(nx: int, ny: int, nz: int, rng: np.random.Generator,
+                        high: float = 1.0 / 3.0) -> tuple[np.ndarray, np.ndarray, np.ndarray,
+                                                          np.ndarray]:
+    """A potential that is a sum of one function per grid axis, V[x + nx (y + ny z)] =
+    v_x[x] + v_y[y] + v_z[z], each v_k iid U[0, high] (default 1/3, so V lies in [0, 1] with
+    mean 1/2 like the iid U[0, 1] potential).  Returns (V, v_x, v_y, v_z)."""
+    vx, vy, vz = rng.random(nx) * high, rng.random(ny) * high, rng.random(nz) * high
+    V = (vz[:, None, None] + vy[None, :, None] + vx[None, None, :]).ravel()
+    return V, vx, vy, vz
 
 
 def paper_p3_operator(n: int, rng: np.random.Generator, theta: float = 1.01,
@@ -187,6 +199,12 @@ def workload_stencil3d(m: int = 64, p: int = 256, config: int = 3,
     X0 = orthonormal_start(n, p, r1) if start == "orthonormal" else gaussian_start(n, p, r1)
     return Workload(name=f"stencil3d_m{m}_p{p}", kind="stencil3d", n=n, p=p, X0=X0, V=V, m=m,
                     params=dict(variant="pcal", beta=1.0, tol=1e-6))
+
+
+def stencil3d_separable_potential(m: int = 128, config: int = 5):
+    """The separable potential of the 128^3 workload's companion instance (stream 3 of
+    configuration 5), whose optimum is exact: (V, v_x, v_y, v_z)."""
+    return separable_potential(m, m, m, rng_for(config, 3))
 
 
 def batched_shapes(count: int = 512, n_lo: int = 64, n_hi: int = 2048, p_lo: int = 4,
