@@ -44,11 +44,17 @@ WORKLOADS = {
     # [4, min(64, n/2)], beta = 1, PCAL to relative KKT 1e-6 in one persistent launch.
     "batched": dict(kind="batched", count=512, n_lo=64, n_hi=2048, beta=1.0, tol=1e-6,
                     name="batched_512_dense_trace_n64-2048_p4-64", fp64_sample=6),
-    # 3D Laplacian plus potential on a 128^3 grid, p = 1024 (8.6 GB per n x p FP32 buffer):
-    # per-kernel timings only (--kernel-iters), from a Gaussian start generated on the device
-    # (a host FP64 start would take 17 GB).
+    # 3D Laplacian plus potential on a 128^3 grid, p = 1024 (8.6 GB per n x p FP32 buffer),
+    # V iid U[0,1]: the largest single-GPU workload, and the default.  One step = one PCAL
+    # iteration (all rows of the hot path) in the compensated phase that dominates the solve;
+    # beside the steps: one complete solve (time-to-KKT, end to end with host copies), the same
+    # solve on the companion instance with a separable potential whose optimum is exact
+    # (tests/golden), the FP64 path over its first iterations (extrapolated) and the oracle on
+    # the grid's first 8 z-planes (cpu_baseline).  The start is the Q factor of a seeded
+    # Gaussian generated on the device (a host FP64 start would take 17 GB).
     "stencil3d_128": dict(kind="stencil3d", m=128, n=2097152, p=1024, beta=1.0, tol=1e-5,
-                          name="stencil3d_n2097152_p1024", kernel_only=True),
+                          tol_separable=1e-6, maxit=3000, name="stencil3d_n2097152_p1024",
+                          fp64_iters=1, slab_planes=8),
     # Section 5.4's parallel workloads at n = 10000, p = 1000, PCAL with beta = 1 (the paper's
     # default): Problem 1 with L = Diag(L_1, ..., L_2000) of 5 x 5 Dirichlet blocks (alpha = 1),
     # and Problem 2 with the tridiagonal A and a random linear term; FP32 storage with
@@ -70,7 +76,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="hartree1d")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="stencil3d_128")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -301,11 +307,11 @@ def golden_fstar(name):
 
 # ---------------------------------------------------------------- our arm
 
-def make_solver(wl, precision, torch, engine="auto", final_orth=1, maxit=3000):
+def make_solver(wl, precision, torch, engine="auto", final_orth=1, maxit=3000, tensor_cores=None):
     from paper_1810_03930_gb300 import Solver
     kw = dict(variant="pcal", lambda_rule="lambda2", beta=wl["beta"], tol=wl["tol"], maxit=maxit,
               precision=precision, final_orth=final_orth, graph_iters=16, engine=engine,
-              tensor_cores=wl.get("tensor_cores", "auto"), orth_metrics=False)
+              tensor_cores=tensor_cores or wl.get("tensor_cores", "auto"), orth_metrics=False)
     if wl["kind"] == "stencil3d":
         m = wl["m"]
         return Solver(wl["n"], wl["p"], "stencil3d", grid=(m, m, m), V=wl["V"], **kw)
@@ -572,40 +578,415 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- the 128^3, p = 1024 workload
+
+STENCIL128_SEED = 1810039300 + 10 * 5 + 1      # stream 1 (the start) of configuration 5
+
+
+def device_start(sol, n, p, torch):
+    """The seeded orthonormal start on the device: the Q factor (FP64 Cholesky-QR of the library,
+    rounded to FP32) of an iid N(0, 1) n x p matrix drawn by torch's Philox generator."""
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(STENCIL128_SEED)
+    Z = torch.randn((p, n), generator=gen, device="cuda", dtype=torch.float32)
+    Q = torch.empty((p, n), dtype=torch.float64, device="cuda")
+    sol.orthonormalize(Z, Q)
+    del Z
+    X0 = Q.to(torch.float32)
+    del Q
+    torch.cuda.empty_cache()
+    return X0
+
+
+def stencil_energy64(Q, V64, m, torch):
+    """f(Q) = 1/2 tr(Q^T (L3 + Diag(V)) Q) in FP64 with torch, 32 columns at a time: the parity
+    check of a result (outside every timed region).  Q: (p, ld) FP64 holding n x p column-major."""
+    n = m ** 3
+    Vg = V64.view(m, m, m)
+    tot = 0.0
+    for c0 in range(0, Q.shape[0], 32):
+        q = Q[c0:c0 + 32, :n].reshape(-1, m, m, m)
+        g = (6.0 + Vg) * q
+        g[:, 1:] -= q[:, :-1]
+        g[:, :-1] -= q[:, 1:]
+        g[:, :, 1:] -= q[:, :, :-1]
+        g[:, :, :-1] -= q[:, :, 1:]
+        g[:, :, :, 1:] -= q[:, :, :, :-1]
+        g[:, :, :, :-1] -= q[:, :, :, 1:]
+        tot += float((q * g).sum())
+        del g, q
+    return 0.5 * tot
+
+
+def timed_solve_e2e(sol, Xh, Xw, Q, Qh, torch):
+    """One complete solve through the public API with the start copied in from pinned host memory
+    and the FP64 result copied back: CUDA events split it into H2D, solve (time-to-KKT from the
+    start resident in HBM) and D2H; returns (seconds solve, seconds end to end, status, info)."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    Xw.copy_(Xh, non_blocking=True)
+    ev[1].record()
+    st, info = sol.solve(Xw, Q)
+    ev[2].record()
+    if Qh is not None:
+        Qh.copy_(Q, non_blocking=True)
+    ev[3].record()
+    torch.cuda.synchronize()
+    return ev[1].elapsed_time(ev[2]) / 1e3, ev[0].elapsed_time(ev[3]) / 1e3, st, info
+
+
+def result_parity(Q, V64, m, info, torch, fstar=None):
+    n = m ** 3
+    f = stencil_energy64(Q, V64, m, torch)
+    Qs = Q[:, :n]
+    E = Qs @ Qs.T
+    E.diagonal().sub_(1.0)
+    out = {"iters": info.iters, "kkt_rel": info.kkt_rel, "converged": bool(info.converged),
+           "f_orth": f, "feas_orth": float(torch.linalg.matrix_norm(E))}
+    del E
+    if fstar is not None:
+        out["f_star"] = fstar
+        out["obj_rel_err"] = abs(f - fstar) / abs(fstar)
+    return out
+
+
+def run_stencil128_sharded(args, rank, world, local, wl):
+    """N > 1: ONE 128^3, p = 1024 problem whose z-planes are split over the ranks
+    (plam_create_sharded; the Grams and dots all-gathered over NCCL, halo planes exchanged with
+    the neighbours): the timed steps are iterations of that problem, then one complete solve.
+    Strong scaling: the problem does not grow with N."""
+    import torch
+    from paper_1810_03930_gb300.dist import ShardedStencil, TorchDistComm, sharded_solver
+    from workloads import rng_for, uniform_potential
+    m, n, p = wl["m"], wl["n"], wl["p"]
+    sl = ShardedStencil((m, m, m), rank, world)
+    rows = slice(sl.row0, sl.row0 + sl.n_local)
+    V = torch.as_tensor(uniform_potential(n, rng_for(5, 0))[rows], device="cuda").to(torch.float32)
+    comm = TorchDistComm()
+
+    def solver(tc, maxit, final_orth):
+        return sharded_solver(comm, "stencil3d", sl.n_local, p, sl.row0, n, grid=(m, m, sl.nz_local),
+                              V=V, variant="pcal", lambda_rule="lambda2", beta=wl["beta"],
+                              tol=wl["tol"], maxit=maxit, precision="fp32", final_orth=final_orth,
+                              tensor_cores=tc)
+
+    sol_s = solver("3xtf32", 100000, 0)
+    # the same seeded start as one GPU: every rank draws the whole Gaussian and keeps its rows;
+    # the orthonormalisation's Gram is summed over the ranks
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(STENCIL128_SEED)
+    Z = torch.randn((p, n), generator=gen, device="cuda", dtype=torch.float32)[:, rows].contiguous()
+    buf, Zl = sl.new_x(p, torch.float32)
+    Zl[:, :sl.n_local] = Z
+    del Z
+    Q = torch.empty((p, sl.n_local), dtype=torch.float64, device="cuda")
+    sol_s.orthonormalize(Zl, Q)
+    X0 = Q.to(torch.float32)
+    del Q
+    xbuf, X = sl.new_x(p, torch.float32)
+    X[:, :sl.n_local] = X0
+    for _ in range(max(3, args.warmup)):
+        sol_s.step(X)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    clk = ClockSampler(local)
+    barrier(world)
+    clk.start()
+    launches0 = sol_s.kernel_launches()
+    for e0, e1 in evs:
+        e0.record()
+        sol_s.step(X)
+        e1.record()
+    barrier(world)
+    clocks = clk.stop()
+    launches = sol_s.kernel_launches() - launches0
+    sol_s.close()
+    t_max, _ = reduce_max_sum(world, sum(e0.elapsed_time(e1) for e0, e1 in evs) / 1e3, 0.0)
+    value = args.steps / t_max
+    # one complete solve, the start in from pinned host memory and the result back
+    sol = solver("auto", wl["maxit"], 1)
+    Xh = torch.empty((p, sl.n_local), dtype=torch.float32, pin_memory=True)
+    Xh.copy_(X0)
+    Qh = torch.empty((p, sl.n_local), dtype=torch.float64, pin_memory=True)
+    Q = torch.empty((p, sl.n_local), dtype=torch.float64, device="cuda")
+    barrier(world)
+    t_solve, t_e2e, st, info = timed_solve_e2e(sol, Xh, X, Q, Qh, torch)
+    t_solve, _ = reduce_max_sum(world, t_solve, 0.0)
+    t_e2e, _ = reduce_max_sum(world, t_e2e, 0.0)
+    sol.close()
+    out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+           "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": wl["name"], "n": n, "p": p, "solver": "PCAL eq.(lambda2), ABB",
+                      "beta": wl["beta"], "tol_kkt_rel": wl["tol"], "maxit": wl["maxit"],
+                      "step": "one PCAL iteration of the whole problem, compensated 3xTF32",
+                      "l2": "inputs larger than L2",
+                      "parallelism": f"rows sharded over {world} GPUs (z-slabs; NCCL all-gather of "
+                                     "the Grams and dots, halo planes with the neighbours)"},
+           "time_to_kkt_s": t_solve, "iters_per_solve": info.iters,
+           "parity": {"iters": info.iters, "kkt_rel": info.kkt_rel,
+                      "status": {0: "converged", 2: "maxit"}.get(st, str(st))},
+           "e2e": {"value": info.iters / t_e2e, "unit": "iters/s", "time_to_kkt_s": t_e2e,
+                   "h2d_bytes_per_step": int(n * p * 4), "d2h_bytes_per_step": int(n * p * 8)},
+           "gpu_launches": int(launches), "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    import torch.distributed as dist
+    dist.destroy_process_group()
+
+
+def run_stencil128(args, rank, world, local):
+    import numpy as np
+    import torch
+    dist_init(world, local)
+    wl = workload_config(args)
+    if world > 1:
+        run_stencil128_sharded(args, rank, world, local, wl)
+        return
+    m, n, p = wl["m"], wl["n"], wl["p"]
+    from workloads import rng_for, stencil3d_separable_potential, uniform_potential
+    V64 = torch.as_tensor(uniform_potential(n, rng_for(5, 0)), device="cuda")
+    wl["V"] = V64.to(torch.float32)
+    # ---- the timed steps: PCAL iterations in the compensated phase (3xTF32 Grams and update)
+    sol_s = make_solver(wl, "fp32", torch, engine="graph", final_orth=0, maxit=100000,
+                        tensor_cores="3xtf32")
+    X0 = device_start(sol_s, n, p, torch)
+    Xs = X0.clone()
+    for _ in range(max(3, args.warmup)):
+        sol_s.step(Xs)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    clk = ClockSampler(local)
+    barrier(world)
+    clk.start()
+    launches0 = sol_s.kernel_launches()
+    for e0, e1 in evs:
+        e0.record()
+        sol_s.step(Xs)
+        e1.record()
+    barrier(world)
+    clocks = clk.stop()
+    launches = sol_s.kernel_launches() - launches0
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    t_max, iters_all = reduce_max_sum(world, sum(step_ms) / 1e3, float(args.steps))
+    value = iters_all / t_max
+    ms_per_step = 1e3 * t_max / args.steps
+    # per-kernel attribution of the same iterations (CUDA events between the kernel groups)
+    kms, _ = sol_s.time_kernels(Xs, 3)
+    sol_s.close()
+    del Xs
+    torch.cuda.empty_cache()
+    # ---- one complete solve of the workload: time-to-KKT and end to end
+    sol = make_solver(wl, "fp32", torch, engine="graph", maxit=wl["maxit"])
+    Xh = torch.empty((p, n), dtype=torch.float32, pin_memory=True)
+    Xh.copy_(X0)
+    Qh = torch.empty((p, n), dtype=torch.float64, pin_memory=True)
+    Xw = torch.empty_like(X0)
+    Q = torch.empty((p, n), dtype=torch.float64, device="cuda")
+    t_solve, t_e2e, st, info = timed_solve_e2e(sol, Xh, Xw, Q, Qh, torch)
+    launches_solve = sol.kernel_launches()
+    parity = result_parity(Q, V64, m, info, torch)
+    parity["status"] = {0: "converged", 2: "maxit"}.get(st, str(st))
+    sol.close()
+    del Qh
+    # ---- the companion instance with a separable potential: exact optimum (tests/golden)
+    Vs64 = torch.as_tensor(stencil3d_separable_potential(m)[0], device="cuda")
+    wls = dict(wl, V=Vs64.to(torch.float32), tol=wl["tol_separable"])
+    sol_p = make_solver(wls, "fp32", torch, engine="graph", maxit=wl["maxit"])
+    t_sep, _, st_p, info_p = timed_solve_e2e(sol_p, Xh, Xw, Q, None, torch)
+    g = golden_fstar("stencil3d_separable_n2097152_p1024")
+    fstar = g["f_star"] if g else None
+    parity_sep = result_parity(Q, Vs64, m, info_p, torch, fstar)
+    parity_sep.update({"tol_kkt_rel": wls["tol"], "time_s": t_sep,
+                       "status": {0: "converged", 2: "maxit"}.get(st_p, str(st_p)),
+                       "potential": "V = v_x(x) + v_y(y) + v_z(z), v_k iid U[0, 1/3] (exact optimum "
+                                    "from three tridiagonal eigensolves)"})
+    if fstar is not None:
+        # the first iterate whose objective is within 1e-6 of f* (the device's f of the iterate
+        # X^k, which PCAL keeps at unit column norms: the orthonormalisation moves f only at
+        # second order), and the time to it at the solve's mean rate
+        hist = sol_p.history()
+        ok = [int(h[0]) for h in hist if abs(h[1] - fstar) <= 1e-6 * abs(fstar)]
+        if ok:
+            k6 = ok[0]
+            parity_sep["objective_1e-6"] = {"iteration": k6, "time_s_est": t_sep * k6 / max(1, info_p.iters),
+                                            "kkt_rel_there": float(hist[k6][2])}
+    sol_p.close()
+    del Xh, Q, Vs64
+    torch.cuda.empty_cache()
+    # ---- the FP64 GPU path: its first iterations, extrapolated to the mixed path's count
+    sol64 = make_solver(wl, "fp64", torch, engine="graph", final_orth=0, maxit=100000)
+    X64 = X0.to(torch.float64)
+    sol64.step(X64)                       # warm-up (first launch of every kernel)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(wl["fp64_iters"]):
+        sol64.step(X64)
+    e1.record()
+    torch.cuda.synchronize()
+    t64 = e0.elapsed_time(e1) / 1e3 / wl["fp64_iters"]
+    sol64.close()
+    del X64
+    fp64 = {"s_per_iter": t64, "iters_per_s": 1.0 / t64, "iters_timed": wl["fp64_iters"],
+            "time_to_kkt_s": info.iters * t64,
+            "time_to_kkt_note": "extrapolated: the mixed path's iteration count x the FP64 path's "
+                                f"time per iteration over iterations 2..{1 + wl['fp64_iters']}"}
+    # ---- roofline of the dominant kernel group of the timed steps
+    peak_hbm, peak_kind = measured_peaks()
+    tf32, tf32_kind = measured_tf32_tflops()
+    kf = kernel_flops(wl)
+    kb = kernel_bytes(wl, 4)
+    dom = max(kms, key=lambda k: kms[k])
+    names = {"objective": "stencil_grad", "gram_partial": "tc_gram", "gram_finalize": "gram_finalize",
+             "update": "tc_update", "step_size": "step_size", "primal_update": "primal_update"}
+    if dom in kf:
+        ach = kf[dom] / (kms[dom] * 1e-3) / 1e12
+        roofline = {"bound": "tensor", "kernel": names[dom], "achieved": ach, "peak": tf32,
+                    "unit": "TFLOP/s", "frac": ach / tf32, "peak_source": tf32_kind,
+                    "traffic": recorded_traffic(names[dom], wl["name"]),
+                    "alg_flops_per_launch": kf[dom], "launch_ms": kms[dom],
+                    "mode": "compensated 3xTF32 (three MMAs per product; the flops counted are the "
+                            "algorithm's, Table 'cost')"}
+    else:
+        ach = kb[dom] / (kms[dom] * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": names[dom], "achieved": ach, "peak": peak_hbm,
+                    "unit": "GB/s", "frac": ach / peak_hbm, "peak_source": peak_kind,
+                    "traffic": recorded_traffic(names[dom], wl["name"]),
+                    "alg_bytes_per_launch": kb[dom], "launch_ms": kms[dom]}
+    kernels = {}
+    for k, ms in kms.items():
+        d = {"ms": ms}
+        if k in kf:
+            d["tflops"] = kf[k] / (ms * 1e-3) / 1e12
+            d["frac_tf32"] = d["tflops"] / tf32
+        else:
+            d["gbs"] = kb[k] / (ms * 1e-3) / 1e9
+            d["frac_hbm"] = d["gbs"] / peak_hbm
+        kernels[names[k]] = d
+    h2d = int(n * p * 4)
+    d2h = int(n * p * 8)
+    out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": wl["name"],
+                      "objective": "1/2 tr(X^T (L3 + Diag(V)) X), 7-point Dirichlet L3 on 128^3, "
+                                   "V iid U[0,1]",
+                      "n": n, "p": p, "solver": "PCAL eq.(lambda2), ABB", "beta": wl["beta"],
+                      "tol_kkt_rel": wl["tol"], "maxit": wl["maxit"],
+                      "step": "one PCAL iteration, compensated 3xTF32 tensor-core Grams and update",
+                      "final_orth": "FP64 Cholesky-QR",
+                      "l2": "inputs larger than L2 (8.6 GB per n x p buffer)",
+                      "parallelism": "single GPU" if world == 1 else f"{world} replicas"},
+           "time_to_kkt_s": t_solve, "iters_per_solve": info.iters,
+           "iters_per_s_solve": info.iters / t_solve,
+           "fp64": fp64, "mixed_speedup_vs_fp64": fp64["time_to_kkt_s"] / t_solve,
+           "parity": parity, "parity_separable": parity_sep, "engine": "graph",
+           "roofline": roofline, "kernels_ms_per_launch": kernels,
+           "e2e": {"value": info.iters / t_e2e, "unit": "iters/s", "time_to_kkt_s": t_e2e,
+                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                   "note": "one complete solve through Solver.solve: the start from pinned host "
+                           "memory in, the FP64 result out"},
+           "gpu_launches": int(launches), "gpu_launches_solve": int(launches_solve),
+           "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_slab(wl, V64.cpu().numpy(), args.cpu_seconds, info.iters)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def slab_problem(wl, V, planes):
+    """The first `planes` z-planes of the 128^3 workload as a Dirichlet problem of their own (the
+    oracle's bounded sample): the same p, the potential of those planes, a seeded orthonormal
+    start.  Its iteration cost is that of the full grid times planes / 128 (Table "cost":
+    7 n p^2 + O(n p) is linear in n)."""
+    import numpy as np
+    from workloads import orthonormal_start, rng_for
+    m, p = wl["m"], wl["p"]
+    ns = m * m * planes
+    return (m, m, planes), np.asarray(V[:ns]), orthonormal_start(ns, p, rng_for(5, 4)), ns
+
+
+def cpu_baseline_slab(wl, V, seconds, gpu_iters):
+    """The oracle as it stands on the host cores, PCAL iterations on the first z-planes of the
+    grid (bounded by `seconds`), scaled to whole-grid iterations/s by the row count."""
+    from oracle import objectives as oo
+    from oracle import plam as op
+    planes = wl["slab_planes"]
+    grid, Vs, X0s, ns = slab_problem(wl, V, planes)
+    obj = oo.Stencil3DObjective(grid, Vs)
+    t0 = time.perf_counter()
+    op.solve(obj, X0s, variant="pcal", beta=wl["beta"], tol=0.0, maxit=1, record=False)
+    per_it = time.perf_counter() - t0          # one iteration plus the final Householder QR
+    k = int(max(1, min(50, seconds / max(per_it, 1e-6))))
+    t0 = time.perf_counter()
+    r = op.solve(obj, X0s, variant="pcal", beta=wl["beta"], tol=0.0, maxit=k, record=False)
+    dt = time.perf_counter() - t0
+    scale = ns / wl["n"]
+    rate = (r.iters + 1) / dt * scale
+    return {"value": rate, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"FP64 NumPy/SciPy oracle PCAL, {r.iters} iterations (plus its final "
+                       f"Householder QR) on the first {planes} of the 128 z-planes (n = {ns}, "
+                       f"p = {wl['p']}) in {dt:.1f} s on {os.cpu_count()} host cores; iterations/s "
+                       f"x {scale:g} = the full grid's rate; time-to-KKT at the GPU's {gpu_iters} "
+                       f"iterations: {gpu_iters / rate:.0f} s"),
+            "time_to_kkt_s_est": gpu_iters / rate}
+
+
 # ---------------------------------------------------------------- reference arm (the oracle)
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
     wl = workload_config(args)
+    scale, X0 = 1.0, None
+    from oracle import objectives as oo
+    from oracle import plam as op
     if wl["kind"] == "batched":        # the oracle on the batch's first problem per step
         from workloads import batched_shapes, workload_batched_problem
         n, p = batched_shapes(count=wl["count"], n_lo=wl["n_lo"], n_hi=wl["n_hi"])[0]
         w = workload_batched_problem(0, n, p)
         wl.update(kind="dense", n=n, p=p, A=w.A)
+        obj = oo.objective_for(w)
+    elif wl.get("slab_planes"):        # 128^3: iterations on the grid's first z-planes, scaled
+        from workloads import rng_for, uniform_potential
+        grid, Vs, X0, ns = slab_problem(wl, uniform_potential(wl["n"], rng_for(5, 0)),
+                                        wl["slab_planes"])
+        obj = oo.Stencil3DObjective(grid, Vs)
+        scale = ns / wl["n"]
     else:
         w = load_inputs(wl)
-    from oracle import objectives as oo
-    from oracle import plam as op
-    obj = oo.objective_for(w)
+        obj = oo.objective_for(w)
+    if X0 is None:
+        X0 = w.X0
     per_it = 0.0
     for _ in range(max(1, args.warmup)):
         t0 = time.perf_counter()
-        r = op.solve(obj, w.X0, variant="pcal", beta=wl["beta"], tol=wl["tol"], maxit=2, record=False)
+        r = op.solve(obj, X0, variant="pcal", beta=wl["beta"], tol=wl["tol"],
+                     maxit=1 if scale != 1.0 else 2, record=False)
         per_it = (time.perf_counter() - t0) / (r.iters + 1)
     # each step a bounded sample of the solve: 20 iterations, fewer where one takes long (about 8 s
-    # of CPU work per step), so that a --steps K --warmup W run ends within minutes
-    per_step = int(max(3, min(20, 8.0 / max(per_it, 1e-9))))
+    # of CPU work per step), so that a --steps K --warmup W run ends within minutes; two on the
+    # 128^3 workload's slab (seconds per iteration)
+    per_step = 2 if scale != 1.0 else int(max(3, min(20, 8.0 / max(per_it, 1e-9))))
     times, iters = [], []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        r = op.solve(obj, w.X0, variant="pcal", beta=wl["beta"], tol=wl["tol"], maxit=per_step,
+        r = op.solve(obj, X0, variant="pcal", beta=wl["beta"], tol=wl["tol"], maxit=per_step,
                      record=False)
         times.append(time.perf_counter() - t0)
         iters.append(r.iters + 1)
-    value = sum(iters) / sum(times)
+    value = sum(iters) / sum(times) * scale
     sample = (f"FP64 NumPy/SciPy oracle PCAL, the first {per_step} iterations of the {wl['name']} "
               f"solve from the seeded X0 per step, on {os.cpu_count()} host cores")
+    if scale != 1.0:
+        sample = (f"FP64 NumPy/SciPy oracle PCAL, {per_step} iterations (and its final Householder "
+                  f"QR) per step on the first {wl['slab_planes']} of the 128 z-planes (n = "
+                  f"{int(scale * wl['n'])}, p = {wl['p']}), on {os.cpu_count()} host cores; "
+                  f"iterations/s x {scale:g} = the full grid's rate")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -641,15 +1022,11 @@ def run_kernel_iters(args):
         return
     import numpy as np
     wl = workload_config(args, tensor_cores=args.tensor_cores)
-    if wl.get("kernel_only"):
+    if wl.get("slab_planes"):
         from workloads import rng_for, uniform_potential
         wl["V"] = uniform_potential(wl["n"], rng_for(5, 0))
         sol = make_solver(wl, "fp32", torch, engine="graph")
-        gen = torch.Generator(device="cuda")
-        gen.manual_seed(1810039300 + 10 * 5 + 1)
-        # column-major n x p: a (p, n) row-major tensor; iid N(0, 1/n) entries
-        X = torch.randn((wl["p"], wl["n"]), generator=gen, device="cuda",
-                        dtype=torch.float32) / float(np.sqrt(wl["n"]))
+        X = device_start(sol, wl["n"], wl["p"], torch)
     else:
         w = load_inputs(wl)
         from paper_1810_03930_gb300 import colmajor_to_device
@@ -834,10 +1211,11 @@ def main():
         if rank == 0:
             run_kernel_iters(args)
         return
-    if WORKLOADS[args.workload].get("kernel_only"):
-        raise SystemExit(f"workload {args.workload}: per-kernel timings only (use --kernel-iters K)")
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if WORKLOADS[args.workload].get("slab_planes"):
+        run_stencil128(args, rank, world, local)
         return
     run_ours(args, rank, world, local)
 

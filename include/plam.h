@@ -85,13 +85,16 @@ enum { PLAM_PREC_FP64 = 0, PLAM_PREC_FP32 = 1 };
  *   STENCIL3D  f = 1/2 tr(X^T (L3 + Diag(V)) X), L3 the 7-point Dirichlet
  *              Laplacian on nx*ny*nz points, index i = x + nx*(y + ny*z);
  *              nx*ny*nz must equal n and stay below 2^31.
+ *   QAP        f = 1/2 tr(A^T X B X^T), A n x n and B p x p symmetric          (Problem 4, eq. QAP)
+ *              (A in A / lda, B in Bq / ldbq); grad f = A X B.
  * and a user objective (the problem statement of Section 2 admits any f with
  * a gradient):
  *   CALLBACK   f and grad f from plam_objective_t.grad, called on the host
  *              once per gradient evaluation (see plam_grad_fn).  plam_solve
  *              then launches each iteration directly (no CUDA graph; the
  *              resident engine does not apply). */
-enum { PLAM_OBJ_DENSE = 0, PLAM_OBJ_HARTREE1D = 1, PLAM_OBJ_STENCIL3D = 2, PLAM_OBJ_CALLBACK = 3 };
+enum { PLAM_OBJ_DENSE = 0, PLAM_OBJ_HARTREE1D = 1, PLAM_OBJ_STENCIL3D = 2, PLAM_OBJ_CALLBACK = 3,
+       PLAM_OBJ_QAP = 4 };
 
 /* User gradient of PLAM_OBJ_CALLBACK: reads X (device, storage type, n x p,
  * leading dimension ldx), writes G = grad f(X) (device, storage type, leading
@@ -140,8 +143,8 @@ typedef struct {
 
 typedef struct {
   int kind;             /* PLAM_OBJ_* */
-  const void* A;        /* DENSE: device, n x n symmetric, storage type, column-major */
-  int64_t lda;          /* DENSE: leading dimension >= n */
+  const void* A;        /* DENSE, QAP: device, n x n symmetric, storage type, column-major */
+  int64_t lda;          /* DENSE, QAP: leading dimension >= n */
   double alpha;         /* HARTREE1D: Hartree coupling alpha */
   double quad_scale;    /* HARTREE1D: q, the coefficient of tr(X^T L X) (1/4 Kohn-Sham, 1/2 Problem 1) */
   int nx, ny, nz;       /* STENCIL3D: grid, nx*ny*nz == n */
@@ -158,6 +161,8 @@ typedef struct {
                            lin != NULL selects the row-tile x column-group gradient kernels and
                            rules out the resident engine */
   int64_t ldlin;        /* HARTREE1D: leading dimension of lin */
+  const void* Bq;       /* QAP: device, p x p symmetric, storage type, column-major */
+  int64_t ldbq;         /* QAP: leading dimension of Bq (>= p) */
 } plam_objective_t;
 
 typedef struct {
@@ -193,6 +198,54 @@ plam_status_t plam_default_params(plam_params_t* prm);
  * Errors: PLAM_ERR_INVALID, PLAM_ERR_NOMEM, PLAM_ERR_CUDA; *h is NULL then. */
 plam_status_t plam_create(plam_handle_t* h, int64_t n, int64_t p, const plam_objective_t* obj,
                           const plam_params_t* prm, void* stream);
+
+/* ---- Row-sharded solves (Section 5.4's parallel structure): the rows of X, G and R are
+ * split into contiguous blocks over `size` ranks (processes, usually one per GPU).  Every
+ * O(np) and O(np^2) kernel works on a rank's own rows; per iteration the ranks exchange the
+ * reduced Grams [X^T X | X^T G] (2 p^2 doubles) and the column and Barzilai-Borwein dots
+ * (3p + 7 doubles) through the caller's all-gather, each rank adds the gathered buffers in
+ * rank order (so every rank holds the same sums bit for bit and takes the same step size
+ * and stop decision), and the 3D stencil exchanges one z-plane of halo rows per neighbour.
+ * The final orthonormalisation gathers X^T X the same way.
+ *
+ * allgather: recv (device, size * count doubles) receives every rank's send (device, count
+ *            doubles) in rank order; all device work ordered on `stream`; returns 0 on success.
+ * exchange:  (STENCIL3D only) sends send_lo (the first `count` halo values: this rank's first
+ *            z-plane of every column, contiguous, storage type) to rank - 1 and send_hi (its
+ *            last plane) to rank + 1, and receives rank - 1's last plane into recv_lo and
+ *            rank + 1's first plane into recv_hi (the library leaves the buffers of a
+ *            missing neighbour alone and uses zeros, the Dirichlet boundary, there).
+ * A nonzero return of a callback stops the entry point with PLAM_ERR_CUDA. */
+typedef int (*plam_allgather_fn)(void* ctx, const double* send, double* recv, int64_t count,
+                                 void* stream);
+typedef int (*plam_exchange_fn)(void* ctx, const void* send_lo, const void* send_hi, void* recv_lo,
+                                void* recv_hi, int64_t count, void* stream);
+typedef struct {
+  int rank, size;                 /* this rank, number of ranks (>= 1) */
+  int64_t row0;                   /* first global row of this rank's block */
+  int64_t n_global;               /* rows of the whole problem (2p <= n_global) */
+  plam_allgather_fn allgather;    /* required when size > 1 */
+  plam_exchange_fn exchange;      /* required for STENCIL3D when size > 1 */
+  void* ctx;                      /* passed to the callbacks unchanged */
+} plam_comm_t;
+
+/* A handle on this rank's n_local rows of a row-sharded problem (n_local >= 1; the objective
+ * describes the rank's own rows).  Supported objectives:
+ *   STENCIL3D  nx * ny * nz = n_local: the rank's z-slab of the global nx x ny grid, row0 a
+ *              multiple of nx * ny.  X passed to the calls must have halo rows: for every
+ *              column, the nx * ny rows before X and after X + n_local are valid memory that
+ *              the library overwrites with the neighbours' planes (ldx >= n_local + 2 nx ny).
+ *   HARTREE1D  with block b >= 1 (block-diagonal L, as Section 5.4 runs Problem 1; the blocks
+ *              never cross ranks: row0 a multiple of b, and n_local a multiple of b on every
+ *              rank but the last).
+ * Others return PLAM_ERR_UNSUPPORTED.  The handle runs plain launches (graph_iters and the
+ * resident engine do not apply: the callbacks run on the host between kernels) and skips
+ * the output's f / KKT / feasibility report (orth_metrics is taken as 0).  plam_step,
+ * pcal_step, plam_solve, plam_orthonormalize and plam_last_iteration apply (on local rows);
+ * every rank must make the same sequence of calls. */
+plam_status_t plam_create_sharded(plam_handle_t* h, int64_t n_local, int64_t p,
+                                  const plam_objective_t* obj, const plam_params_t* prm,
+                                  const plam_comm_t* comm, void* stream);
 
 /* The engine plam_solve runs on this handle: PLAM_ENGINE_RESIDENT or
  * PLAM_ENGINE_GRAPH (graph_iters > 0), or 0 for direct launches. */

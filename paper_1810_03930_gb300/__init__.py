@@ -106,18 +106,19 @@ class Solver:
     Matrices are torch tensors of shape (p, ld) whose memory is the column-major
     n x p matrix (ld = leading dimension >= n).
 
-    kind: "dense" (A), "hartree1d" (alpha, quad_scale, xc; block = rows per Dirichlet block
+    kind: "dense" (A), "qap" (A and the p x p B of Problem 4, f = 1/2 tr(A^T X B X^T)),
+    "hartree1d" (alpha, quad_scale, xc; block = rows per Dirichlet block
     of L, 0 for one block; lin = the linear term G_lin of Problem 2, n x p), "stencil3d"
     (grid = (nx, ny, nz), V) or "callback" (energy = a torch function of the (n, p) iterate).
     The other keywords are the fields of plam_params_t (include/plam.h).
     """
 
-    def __init__(self, n, p, kind, *, A=None, alpha=1.0, quad_scale=0.25, xc=0.0, block=0, lin=None,
+    def __init__(self, n, p, kind, *, A=None, B=None, alpha=1.0, quad_scale=0.25, xc=0.0, block=0, lin=None,
                  grid=None, V=None,
                  variant="pcal", lambda_rule="lambda2", beta=1.0, eta_rule="abb", eta0=0.0,
                  eta_gamma=0.0, tol=1e-8, maxit=3000, precision="fp64", final_orth=1,
                  graph_iters=16, engine="auto", tensor_cores="auto", refine_switch=1e-3,
-                 energy=None, orth_metrics=True, stream=None):
+                 energy=None, orth_metrics=True, stream=None, shard=None):
         torch = _torch()
         self.n, self.p = int(n), int(p)
         self.precision = precision
@@ -141,10 +142,14 @@ class Solver:
         self.params = prm
         obj = _lib.plam_objective_t()
         self._keep = []
-        if kind == "dense":
+        if kind in ("dense", "qap"):
             At = A if isinstance(A, torch.Tensor) else colmajor_to_device(A, self.dtype)
             self._keep.append(At)
             obj.kind, obj.A, obj.lda = PLAM_OBJ_DENSE, At.data_ptr(), At.stride(0)
+            if kind == "qap":
+                Bt = B if isinstance(B, torch.Tensor) else colmajor_to_device(B, self.dtype)
+                self._keep.append(Bt)
+                obj.kind, obj.Bq, obj.ldbq = _lib.PLAM_OBJ_QAP, Bt.data_ptr(), Bt.stride(0)
         elif kind == "hartree1d":
             obj.kind, obj.alpha, obj.quad_scale = PLAM_OBJ_HARTREE1D, float(alpha), float(quad_scale)
             obj.xc = float(xc)
@@ -170,7 +175,13 @@ class Solver:
             raise ValueError(kind)
         self.objective = obj
         self.stream = stream if stream is not None else torch.cuda.current_stream().cuda_stream
-        self.h = plam_create(self.n, self.p, obj, prm, self.stream)
+        if shard is not None:
+            # a row-sharded handle (plam_create_sharded): n is this rank's row count and the
+            # objective describes its rows; shard = (comm struct, its Python callbacks)
+            self.comm, self._comm_keep = shard
+            self.h = _lib.plam_create_sharded(self.n, self.p, obj, prm, self.comm, self.stream)
+        else:
+            self.h = plam_create(self.n, self.p, obj, prm, self.stream)
 
     def _make_callback(self, energy):
         """The C gradient callback of a user energy: f = energy(X) on an (n, p) view of X,

@@ -30,7 +30,7 @@ PLAM_VARIANT_PLAM, PLAM_VARIANT_PCAL = 0, 1
 PLAM_LAMBDA1, PLAM_LAMBDA2, PLAM_LAMBDA_DA = 0, 1, 2
 PLAM_ETA_ABB, PLAM_ETA_BB1, PLAM_ETA_BB2, PLAM_ETA_CONST, PLAM_ETA_DIFF = 0, 1, 2, 3, 4
 PLAM_PREC_FP64, PLAM_PREC_FP32 = 0, 1
-PLAM_OBJ_DENSE, PLAM_OBJ_HARTREE1D, PLAM_OBJ_STENCIL3D, PLAM_OBJ_CALLBACK = 0, 1, 2, 3
+PLAM_OBJ_DENSE, PLAM_OBJ_HARTREE1D, PLAM_OBJ_STENCIL3D, PLAM_OBJ_CALLBACK, PLAM_OBJ_QAP = 0, 1, 2, 3, 4
 PLAM_ENGINE_AUTO, PLAM_ENGINE_GRAPH, PLAM_ENGINE_RESIDENT = 0, 1, 2
 
 
@@ -52,7 +52,21 @@ class plam_objective_t(C.Structure):
                 ("quad_scale", C.c_double), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("V", C.c_void_p), ("grad", plam_grad_fn), ("grad_ctx", C.c_void_p),
                 ("xc", C.c_double), ("block", C.c_int64), ("lin", C.c_void_p),
-                ("ldlin", C.c_int64)]
+                ("ldlin", C.c_int64), ("Bq", C.c_void_p), ("ldbq", C.c_int64)]
+
+
+# int allgather(void* ctx, const double* send, double* recv, int64_t count, void* stream)
+plam_allgather_fn = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p)
+# int exchange(void* ctx, const void* send_lo, const void* send_hi, void* recv_lo, void* recv_hi,
+#              int64_t count, void* stream)
+plam_exchange_fn = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                               C.c_int64, C.c_void_p)
+
+
+class plam_comm_t(C.Structure):
+    _fields_ = [("rank", C.c_int), ("size", C.c_int), ("row0", C.c_int64), ("n_global", C.c_int64),
+                ("allgather", plam_allgather_fn), ("exchange", plam_exchange_fn),
+                ("ctx", C.c_void_p)]
 
 
 class plam_batch_problem_t(C.Structure):
@@ -74,6 +88,9 @@ SIGNATURES = {
     "plam_default_params": (C.c_int, [C.POINTER(plam_params_t)]),
     "plam_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int64, C.c_int64,
                               C.POINTER(plam_objective_t), C.POINTER(plam_params_t), C.c_void_p]),
+    "plam_create_sharded": (C.c_int, [C.POINTER(C.c_void_p), C.c_int64, C.c_int64,
+                                      C.POINTER(plam_objective_t), C.POINTER(plam_params_t),
+                                      C.POINTER(plam_comm_t), C.c_void_p]),
     "plam_destroy": (C.c_int, [C.c_void_p]),
     "plam_reset": (C.c_int, [C.c_void_p]),
     "plam_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(plam_info_t)]),
@@ -157,6 +174,14 @@ def plam_create(n: int, p: int, obj: plam_objective_t, prm: plam_params_t, strea
     h = C.c_void_p()
     check(load().plam_create(C.byref(h), n, p, C.byref(obj), C.byref(prm), C.c_void_p(stream)),
           "plam_create")
+    return h
+
+
+def plam_create_sharded(n_local: int, p: int, obj: plam_objective_t, prm: plam_params_t,
+                        comm: plam_comm_t, stream: int = 0) -> C.c_void_p:
+    h = C.c_void_p()
+    check(load().plam_create_sharded(C.byref(h), n_local, p, C.byref(obj), C.byref(prm),
+                                     C.byref(comm), C.c_void_p(stream)), "plam_create_sharded")
     return h
 
 

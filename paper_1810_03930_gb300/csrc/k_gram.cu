@@ -281,12 +281,15 @@ cudaError_t launch_gram_reduce(int p, int nchunks, int with_g, const T* part, do
 template <typename T>
 cudaError_t launch_gram_finalize(int p, int nchunks, const T* part, double* red, double* B,
                                  double* L0, T* Mt, T* L0t, double* feas_row, const DevState* st,
-                                 IterParams prm, cudaStream_t s) {
-  const size_t E = (size_t)2 * p * p;
-  gram_chunk_reduce_kernel<T><<<(unsigned)((E + 31) / 32), 32 * kRedWarps, 0, s>>>(p, nchunks, part,
-                                                                                 red, st);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+                                 IterParams prm, cudaStream_t s, int stage) {
+  cudaError_t e = cudaSuccess;
+  if (stage != 2) {
+    const size_t E = (size_t)2 * p * p;
+    gram_chunk_reduce_kernel<T><<<(unsigned)((E + 31) / 32), 32 * kRedWarps, 0, s>>>(p, nchunks,
+                                                                                   part, red, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || stage == 1) return e;
+  }
   const size_t smem = (size_t)2 * p * sizeof(double);
   if (smem > 48 * 1024) {
     e = cudaFuncSetAttribute(gram_finalize_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -327,9 +330,9 @@ template cudaError_t launch_gram_reduce<double>(int, int, int, const double*, do
                                                 cudaStream_t);
 template cudaError_t launch_gram_finalize<float>(int, int, const float*, double*, double*, double*,
                                                  float*, float*, double*, const DevState*,
-                                                 IterParams, cudaStream_t);
+                                                 IterParams, cudaStream_t, int);
 template cudaError_t launch_gram_finalize<double>(int, int, const double*, double*, double*,
                                                   double*, double*, double*, double*,
-                                                  const DevState*, IterParams, cudaStream_t);
+                                                  const DevState*, IterParams, cudaStream_t, int);
 
 }  // namespace plam

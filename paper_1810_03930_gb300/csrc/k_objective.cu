@@ -3,6 +3,8 @@
 //
 // dense_grad_kernel     G = A X for f = 1/2 tr(X^T A X) (Problem 3), a tiled
 //                       64 x 64 GEMM over shared-memory stages of A and X.
+// right_multiply_kernel Y = X B (n x p times p x p): with the dense kernel, Problem 4's
+//                       gradient A X B of f = 1/2 tr(A^T X B X^T) (eq. QAP).
 // hartree kernels       f = q tr(X^T L X) + (alpha/4) rho^T L^{-1} rho - (3 xc / 4) sum rho^{4/3}
 //                       (the last term: Problem 6's exchange, 0 unless xc is set)
 //                       (eq. KS-energy, Problem 1 with L = tridiag(-1,2,-1)),
@@ -484,6 +486,84 @@ stencil_grad_vec_kernel(int nx, int ny, int nz, int p, const T* __restrict__ V,
 
 // ---------------------------------------------------------------- launchers
 
+// Y = X Bm: an n x p times p x p product (Bm column-major, leading dimension ldb), 64 x 64
+// output tiles over shared-memory stages of X and Bm.  Problem 4's gradient A X B is the
+// dense kernel's A X followed by this.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+right_multiply_kernel(int64_t n, int p, const T* __restrict__ X, int64_t ldx,
+                      const T* __restrict__ Bm, int64_t ldb, T* __restrict__ Y, int64_t ldy,
+                      const DevState* __restrict__ st) {
+  if (st != nullptr && st->stop != kRunning) return;
+  constexpr int KS = sizeof(T) == 8 ? 16 : kKStep;
+  __shared__ T Xs[KS][kTile];        // X(r0 + r, k0 + q) at Xs[q][r]
+  __shared__ T Bs[kTile][KS + 1];    // Bm(k0 + q, c0 + c) at Bs[c][q]
+  const int64_t r0 = (int64_t)blockIdx.x * kTile;
+  const int c0 = blockIdx.y * kTile;
+  const int t = threadIdx.x;
+  const int tx = t & 15, ty = t >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+  for (int k0 = 0; k0 < p; k0 += KS) {
+    {
+      const int r = t & (kTile - 1);
+      const int64_t row = r0 + r;
+#pragma unroll
+      for (int s = 0; s < KS / 4; ++s) {
+        const int q = (t >> 6) + 4 * s;
+        const int col = k0 + q;
+        Xs[q][r] = (row < n && col < p) ? X[row + (int64_t)col * ldx] : T(0);
+      }
+    }
+    {
+      const int q = t & (KS - 1);
+      const int kr = k0 + q;
+#pragma unroll
+      for (int s = 0; s < kTile * KS / kThreads; ++s) {
+        const int c = t / KS + (kThreads / KS) * s;
+        const int cc = c0 + c;
+        Bs[c][q] = (kr < p && cc < p) ? Bm[kr + (int64_t)cc * ldb] : T(0);
+      }
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int q = 0; q < KS; ++q) {
+      T xa[4], bb[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) xa[u] = Xs[q][tx + 16 * u];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) bb[v] = Bs[ty + 16 * v][q];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(xa[u], bb[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int c = c0 + ty + 16 * v;
+    if (c >= p) continue;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t r = r0 + tx + 16 * u;
+      if (r < n) Y[r + (int64_t)c * ldy] = acc[u][v];
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_right_multiply(int64_t n, int p, const T* X, int64_t ldx, const T* Bm,
+                                  int64_t ldb, T* Y, int64_t ldy, const DevState* st,
+                                  cudaStream_t s) {
+  dim3 grid((unsigned)((n + kTile - 1) / kTile), (p + kTile - 1) / kTile);
+  right_multiply_kernel<T><<<grid, kThreads, 0, s>>>(n, p, X, ldx, Bm, ldb, Y, ldy, st);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_dense_grad(int64_t n, int p, const T* A, int64_t lda, const T* X, int64_t ldx,
                               T* G, int64_t ldg, const DevState* st, cudaStream_t s) {
@@ -531,6 +611,8 @@ cudaError_t preload_objective_kernels() {
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, dense_grad_kernel<float>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, dense_grad_kernel<double>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, right_multiply_kernel<float>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, right_multiply_kernel<double>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, hartree_density_kernel<float>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, hartree_density_kernel<double>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, hartree_grad_kernel<float>);
@@ -549,6 +631,9 @@ cudaError_t preload_objective_kernels() {
 #define PLAM_INST(T)                                                                              \
   template cudaError_t launch_dense_grad<T>(int64_t, int, const T*, int64_t, const T*, int64_t,   \
                                             T*, int64_t, const DevState*, cudaStream_t);          \
+  template cudaError_t launch_right_multiply<T>(int64_t, int, const T*, int64_t, const T*,       \
+                                                int64_t, T*, int64_t, const DevState*,            \
+                                                cudaStream_t);                                    \
   template cudaError_t launch_hartree_grad<T>(int64_t, int, double, double, double, const T*, int64_t, \
                                               T*, int64_t, double*, double*, double*, double*,    \
                                               const DevState*, cudaStream_t);                     \

@@ -233,37 +233,51 @@ step_size_kernel(int nrt, int nct, const T* __restrict__ colpart, const T* __res
                  T* __restrict__ dsum, const double* __restrict__ feas_row,
                  const double* __restrict__ fpart, int nfpart, double* __restrict__ sums,
                  unsigned int* __restrict__ ticket, DevState* st, double* __restrict__ nubuf,
-                 T* __restrict__ coef, double* __restrict__ hist, IterParams prm) {
+                 T* __restrict__ coef, double* __restrict__ hist, IterParams prm, int phase) {
+  // phase 0: the whole step.  A row-sharded solve splits it around an all-reduce of `sums`:
+  // phase 1 (every CTA) reduces this rank's partials into sums[0 .. nslots) and the objective's
+  // f partials into sums[nslots]; phase 2 (one CTA) takes the sums of all ranks from there.
   if (st->stop != kRunning) return;
   const int p = prm.p;
   const int nslots = kColDots * p + kTotDots;
-  step_partial_sums<T>(nrt, nct, p, colpart, totpart, dsum);
-  __shared__ bool last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1);
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  // the row ranges in order (all loads of a slot issued before the adds), in
-  // the storage type: this CTA runs alone, and GB300 adds doubles at 1/64 of
-  // the float rate, so ~25k double adds here would cost ~10 us
-  const int nranges = (int)gridDim.y;
-  for (int slot = threadIdx.x; slot < nslots; slot += blockDim.x) {
-    T buf[kStepRanges];
-#pragma unroll
-    for (int u = 0; u < kStepRanges; ++u)
-      buf[u] = (u < nranges) ? __ldcg(dsum + (size_t)u * nslots + slot) : T(0);
-    T v = buf[0];
-#pragma unroll
-    for (int u = 1; u < kStepRanges; ++u)
-      if (u < nranges) v += buf[u];
-    sums[slot] = (double)v;
-  }
-  __syncthreads();
-
   __shared__ double scratch[33];
   __shared__ double sc[8];
+  if (phase != 2) {
+    step_partial_sums<T>(nrt, nct, p, colpart, totpart, dsum);
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // the row ranges in order (all loads of a slot issued before the adds), in
+    // the storage type: this CTA runs alone, and GB300 adds doubles at 1/64 of
+    // the float rate, so ~25k double adds here would cost ~10 us
+    const int nranges = (int)gridDim.y;
+    for (int slot = threadIdx.x; slot < nslots; slot += blockDim.x) {
+      T buf[kStepRanges];
+#pragma unroll
+      for (int u = 0; u < kStepRanges; ++u)
+        buf[u] = (u < nranges) ? __ldcg(dsum + (size_t)u * nslots + slot) : T(0);
+      T v = buf[0];
+#pragma unroll
+      for (int u = 1; u < kStepRanges; ++u)
+        if (u < nranges) v += buf[u];
+      sums[slot] = (double)v;
+    }
+    __syncthreads();
+    if (phase == 1) {
+      double hs = 0.0;
+      for (int i = threadIdx.x; i < nfpart; i += blockDim.x) hs += __ldcg(fpart + i);
+      const double hpart = block_sum(hs, scratch);
+      if (threadIdx.x == 0) {
+        sums[nslots] = hpart;
+        *ticket = 0u;
+      }
+      return;
+    }
+  }
   const double* xx = sums;
   const double* xr = sums + p;
   const double* rr = sums + 2 * p;
@@ -277,8 +291,9 @@ step_size_kernel(int nrt, int nct, const T* __restrict__ colpart, const T* __res
   const double feas2 = block_sum(fsum, scratch);
   const double xx_all = block_sum(xsum, scratch);
   double hsum = 0.0;
-  for (int i = threadIdx.x; i < nfpart; i += blockDim.x) hsum += __ldcg(fpart + i);
-  const double hartree = block_sum(hsum, scratch);
+  if (phase == 0)
+    for (int i = threadIdx.x; i < nfpart; i += blockDim.x) hsum += __ldcg(fpart + i);
+  const double hartree = phase == 0 ? block_sum(hsum, scratch) : __ldcg(sums + nslots);
   const int k = st->k;
   if (threadIdx.x == 0) {
     const double ss = __ldcg(tot + 0), sy = __ldcg(tot + 1), yy = __ldcg(tot + 2);
@@ -440,14 +455,15 @@ template <typename T>
 cudaError_t launch_step_size(int nrt, int nct, const T* colpart, const T* totpart, T* dsum,
                              const double* feas_row, const double* fpart, int nfpart, double* sums,
                              unsigned int* ticket, DevState* st, double* nubuf, T* coef,
-                             double* hist, IterParams prm, cudaStream_t s) {
+                             double* hist, IterParams prm, cudaStream_t s, int phase) {
   // 32 dot slots per CTA column, about 64 row tiles (8 per warp) per CTA row
   const int groups = (kColDots * prm.p + 31) / 32 + 1;
   int ranges = (nrt + 8 * kStepWarps - 1) / (8 * kStepWarps);
   ranges = ranges < 1 ? 1 : (ranges > kStepRanges ? kStepRanges : ranges);
-  step_size_kernel<T><<<dim3(groups, ranges), kStepThreads, 0, s>>>(
-      nrt, nct, colpart, totpart, dsum, feas_row, fpart, nfpart, sums, ticket, st, nubuf, coef,
-      hist, prm);
+  const dim3 grid = phase == 2 ? dim3(1, 1) : dim3(groups, ranges);
+  step_size_kernel<T><<<grid, kStepThreads, 0, s>>>(nrt, nct, colpart, totpart, dsum, feas_row,
+                                                     fpart, nfpart, sums, ticket, st, nubuf, coef,
+                                                     hist, prm, phase);
   return cudaGetLastError();
 }
 
@@ -488,7 +504,7 @@ cudaError_t preload_update_kernels() {
                                         const DevState*, T*, T*, cudaStream_t);                    \
   template cudaError_t launch_step_size<T>(int, int, const T*, const T*, T*, const double*,       \
                                            const double*, int, double*, unsigned int*, DevState*,  \
-                                           double*, T*, double*, IterParams, cudaStream_t);        \
+                                           double*, T*, double*, IterParams, cudaStream_t, int);   \
   template cudaError_t launch_primal_update<T>(int64_t, int, T*, int64_t, const T*, const T*,      \
                                                int64_t, const T*, const DevState*, int,            \
                                                cudaStream_t);

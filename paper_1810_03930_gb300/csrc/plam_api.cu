@@ -135,6 +135,15 @@ struct plam_handle_s {
   double* kkt_part = nullptr;
   // dual-ascent multiplier (PLAM_LAMBDA_DA), p x p FP64
   double* lam = nullptr;
+  // row sharding (plam_create_sharded)
+  int sharded = 0;
+  plam_comm_t comm{};
+  int64_t g_off = 0;        // rows of G before the first local row (the stencil's lower halo plane)
+  int64_t plane = 0;        // rows of one halo plane (sharded stencil)
+  void* vext = nullptr;     // the potential with zero halo planes (sharded stencil)
+  void* halo = nullptr;     // 4 x plane x p staging: send_lo, send_hi, recv_lo, recv_hi
+  double* gath = nullptr;   // size x max(2 p^2, 3p + 7) doubles: the all-gather's receive buffer
+  void* qtmp = nullptr;     // n x p work of Problem 4's gradient (A X before the product with B)
 };
 
 namespace {
@@ -246,6 +255,13 @@ int launch_objective(plam_handle_s* h, const T* X, int64_t ldx, T* G, int64_t ld
       *err = launch_stencil_grad<T>(h->obj.nx, h->obj.ny, h->obj.nz, p, (const T*)h->obj.V, X, ldx,
                                     G, ldg, st, s);
       return 1;
+    case PLAM_OBJ_QAP:   // A X into the handle's n x p work, then (A X) B
+      *err = launch_dense_grad<T>(h->n, p, (const T*)h->obj.A, h->obj.lda, X, ldx, (T*)h->qtmp,
+                                  h->ldw, st, s);
+      if (*err == cudaSuccess)
+        *err = launch_right_multiply<T>(h->n, p, (const T*)h->qtmp, h->ldw, (const T*)h->obj.Bq,
+                                        h->obj.ldbq, G, ldg, st, s);
+      return 2;
     case PLAM_OBJ_CALLBACK:
       if (h->obj.grad(h->obj.grad_ctx, X, ldx, G, ldg, h->fpart, (void*)s) != 0) {
         *err = cudaSuccess;
@@ -258,6 +274,48 @@ int launch_objective(plam_handle_s* h, const T* X, int64_t ldx, T* G, int64_t ld
   return -1;
 }
 
+plam_status_t comm_fail(const char* what) {
+  snprintf(g_err, sizeof(g_err), "communicator callback failed: %s", what);
+  return PLAM_ERR_CUDA;
+}
+
+// Sum `count` doubles at buf over the ranks (all-gather, then the rank-order sum) in place.
+plam_status_t shard_allreduce(plam_handle_s* h, double* buf, int64_t count, cudaStream_t s,
+                              int* nk) {
+  if (h->comm.size == 1) return PLAM_OK;
+  if (h->comm.allgather(h->comm.ctx, buf, h->gath, count, (void*)s) != 0) return comm_fail("allgather");
+  CK(launch_rank_sum(h->gath, h->comm.size, count, buf, h->st, s));
+  *nk += 1;
+  return PLAM_OK;
+}
+
+// The stencil's halo planes of X: this rank's first and last planes to its neighbours, theirs
+// into the rows before X and after X + n (zeros at the global boundary: Dirichlet).
+template <typename T>
+plam_status_t shard_halo(plam_handle_s* h, T* X, int64_t ldx, cudaStream_t s) {
+  const int64_t pl = h->plane, n = h->n;
+  const size_t w = sizeof(T), pitch = (size_t)ldx * w, cnt = (size_t)pl * h->p;
+  T* buf = (T*)h->halo;
+  T *send_lo = buf, *send_hi = buf + cnt, *recv_lo = buf + 2 * cnt, *recv_hi = buf + 3 * cnt;
+  const int r = h->comm.rank, P = h->comm.size;
+  if (P > 1) {
+    CK(cudaMemcpy2DAsync(send_lo, pl * w, X, pitch, pl * w, h->p, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpy2DAsync(send_hi, pl * w, X + (n - pl), pitch, pl * w, h->p,
+                         cudaMemcpyDeviceToDevice, s));
+    if (h->comm.exchange(h->comm.ctx, send_lo, send_hi, recv_lo, recv_hi, (int64_t)cnt, (void*)s) != 0)
+      return comm_fail("exchange");
+  }
+  if (r > 0)
+    CK(cudaMemcpy2DAsync(X - pl, pitch, recv_lo, pl * w, pl * w, h->p, cudaMemcpyDeviceToDevice, s));
+  else
+    CK(cudaMemset2DAsync(X - pl, pitch, 0, pl * w, h->p, s));
+  if (r < P - 1)
+    CK(cudaMemcpy2DAsync(X + n, pitch, recv_hi, pl * w, pl * w, h->p, cudaMemcpyDeviceToDevice, s));
+  else
+    CK(cudaMemset2DAsync(X + n, pitch, 0, pl * w, h->p, s));
+  return PLAM_OK;
+}
+
 // The kernel sequence of one iteration on stream s; returns kernels launched.
 // When `ev` is given, ev[i] is recorded before kernel group i and ev[6] after
 // the last one (kernel attribution, plam_time_kernels).
@@ -266,10 +324,21 @@ plam_status_t launch_iteration(plam_handle_s* h, T* X, int64_t ldx, int variant,
                                cudaStream_t s, int* nk, cudaEvent_t* ev = nullptr) {
   const int p = (int)h->p;
   const IterParams ip = iter_params<T>(h, variant, lambda2);
-  T* G = (T*)h->G;
+  T* G = (T*)h->G + h->g_off;
   cudaError_t e;
   if (ev) CK(cudaEventRecord(ev[0], s));
-  int k = launch_objective<T>(h, X, ldx, G, h->ldw, h->st, s, &e);
+  int k = 0;
+  if (h->sharded && h->obj.kind == PLAM_OBJ_STENCIL3D) {
+    // the halo planes, then the stencil on the slab extended by them (the outputs on the
+    // halo planes themselves are not used)
+    plam_status_t hs = shard_halo<T>(h, X, ldx, s);
+    if (hs != PLAM_OK) return hs;
+    e = launch_stencil_grad<T>(h->obj.nx, h->obj.ny, h->obj.nz + 2, p, (const T*)h->vext,
+                               X - h->plane, ldx, (T*)h->G, h->ldw, h->st, s);
+    k = 1;
+  } else {
+    k = launch_objective<T>(h, X, ldx, G, h->ldw, h->st, s, &e);
+  }
   if (k == -2) return objective_fail();
   if (k < 0 || e != cudaSuccess) return cuda_fail(e, "objective gradient");
   if (ev) CK(cudaEventRecord(ev[1], s));
@@ -283,8 +352,18 @@ plam_status_t launch_iteration(plam_handle_s* h, T* X, int64_t ldx, int variant,
                                    (T*)h->part, h->st, s)));
   }
   if (ev) CK(cudaEventRecord(ev[2], s));
-  CK(launch_gram_finalize<T>(p, nch, (const T*)h->part, h->red, h->B, h->L0, (T*)h->Mt,
-                             (T*)h->L0t, h->feas_row, h->st, ip, s));
+  if (h->sharded) {
+    CK(launch_gram_finalize<T>(p, nch, (const T*)h->part, h->red, h->B, h->L0, (T*)h->Mt,
+                               (T*)h->L0t, h->feas_row, h->st, ip, s, 1));
+    plam_status_t as = shard_allreduce(h, h->red, (int64_t)2 * p * p, s, &k);
+    if (as != PLAM_OK) return as;
+    CK(launch_gram_finalize<T>(p, nch, (const T*)h->part, h->red, h->B, h->L0, (T*)h->Mt,
+                               (T*)h->L0t, h->feas_row, h->st, ip, s, 2));
+    k += 1;
+  } else {
+    CK(launch_gram_finalize<T>(p, nch, (const T*)h->part, h->red, h->B, h->L0, (T*)h->Mt,
+                               (T*)h->L0t, h->feas_row, h->st, ip, s));
+  }
   if (ev) CK(cudaEventRecord(ev[3], s));
   int nrt = h->nrt, nct = h->nct;
   if (sizeof(T) == 4 && h->use_tc && tc_update_supported(X, ldx)) {
@@ -302,10 +381,22 @@ plam_status_t launch_iteration(plam_handle_s* h, T* X, int64_t ldx, int variant,
                         (T*)h->colpart, (T*)h->totpart, s));
   }
   if (ev) CK(cudaEventRecord(ev[4], s));
-  CK(launch_step_size<T>(nrt, nct, (const T*)h->colpart, (const T*)h->totpart, (T*)h->dsum,
-                         h->feas_row,
-                         h->fpart, h->nfpart, h->sums,
-                         h->ticket, h->st, h->nubuf, (T*)h->coef, h->hist, ip, s));
+  if (h->sharded) {
+    CK(launch_step_size<T>(nrt, nct, (const T*)h->colpart, (const T*)h->totpart, (T*)h->dsum,
+                           h->feas_row, h->fpart, h->nfpart, h->sums, h->ticket, h->st, h->nubuf,
+                           (T*)h->coef, h->hist, ip, s, 1));
+    plam_status_t as = shard_allreduce(h, h->sums, (int64_t)kColDots * p + kTotDots + 1, s, &k);
+    if (as != PLAM_OK) return as;
+    CK(launch_step_size<T>(nrt, nct, (const T*)h->colpart, (const T*)h->totpart, (T*)h->dsum,
+                           h->feas_row, h->fpart, h->nfpart, h->sums, h->ticket, h->st, h->nubuf,
+                           (T*)h->coef, h->hist, ip, s, 2));
+    k += 1;
+  } else {
+    CK(launch_step_size<T>(nrt, nct, (const T*)h->colpart, (const T*)h->totpart, (T*)h->dsum,
+                           h->feas_row,
+                           h->fpart, h->nfpart, h->sums,
+                           h->ticket, h->st, h->nubuf, (T*)h->coef, h->hist, ip, s));
+  }
   if (ev) CK(cudaEventRecord(ev[5], s));
   CK(launch_primal_update<T>(h->n, p, X, ldx, (const T*)h->R[0], (const T*)h->R[1], h->ldw,
                              (const T*)h->coef, h->st, variant, s));
@@ -354,9 +445,15 @@ plam_status_t read_state(plam_handle_s* h, plam_info_t* info, int* stop) {
   return PLAM_OK;
 }
 
+// X of a sharded stencil handle carries a halo plane before and after the local rows.
+bool halo_rows_ok(const plam_handle_s* h, int64_t ldx) {
+  return h->plane == 0 || ldx >= h->n + 2 * h->plane;
+}
+
 plam_status_t step_common(plam_handle_t h, void* X, int64_t ldx, plam_info_t* info, int variant,
                           int lambda2) {
-  if (!h || !X || ldx < h->n || !aligned(X, h->esz)) return PLAM_ERR_INVALID;
+  if (!h || !X || ldx < h->n || !aligned(X, h->esz) || !halo_rows_ok(h, ldx))
+    return PLAM_ERR_INVALID;
   int nk = 0;
   plam_status_t st = dispatch_iteration(h, X, ldx, variant, lambda2, h->stream, &nk);
   if (st != PLAM_OK) return st;
@@ -379,7 +476,8 @@ void free_handle(plam_handle_s* h) {
                  h->coef, h->hist,
                  h->rho, h->blk, h->y, h->fpart, h->W, h->Z, h->info, h->feas_dev, h->Qtmp,
                  h->dotpart, h->r_halo, h->r_blk, h->r_part, h->r_red, h->r_dots, h->r_dred,
-                 h->r_bar, h->r_err, h->tc_err, h->msplit, h->kkt_part, h->lam};
+                 h->r_bar, h->r_err, h->tc_err, h->msplit, h->kkt_part, h->lam, h->vext,
+                 h->halo, h->gath, h->qtmp};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (h->st_host) cudaFreeHost(h->st_host);
@@ -405,6 +503,12 @@ plam_status_t orthonormalize_impl(plam_handle_s* h, const T* X, int64_t ldx, dou
                                                s)));
     }
     CK(launch_gram_reduce<double>(p, h->nchunks, 0, h->part64, h->B, nullptr, s));
+    if (h->sharded) {
+      int nk = 0;
+      plam_status_t as = shard_allreduce(h, h->B, (int64_t)p * p, s, &nk);   // X^T X over all rows
+      if (as != PLAM_OK) return as;
+      h->launches += nk;
+    }
     CK(launch_cholesky_inverse(p, h->B, h->W, h->Z, h->info, s));
     CK(cudaMemcpyAsync(h->info_host, h->info, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -429,6 +533,12 @@ plam_status_t orthonormalize_impl(plam_handle_s* h, const T* X, int64_t ldx, dou
     CK((launch_gram_partial<double, double>(h->n, p, Xout, ldo, (const double*)nullptr, 0,
                                              h->rows_per_chunk, h->nchunks, h->part64, nullptr, s)));
     CK(launch_gram_reduce<double>(p, h->nchunks, 0, h->part64, h->B, nullptr, s));
+    if (h->sharded) {
+      int nk = 0;
+      plam_status_t as = shard_allreduce(h, h->B, (int64_t)p * p, s, &nk);
+      if (as != PLAM_OK) return as;
+      h->launches += nk;
+    }
     CK(launch_feas(p, h->B, h->feas_row, h->feas_dev, s));
     CK(cudaMemcpyAsync(h->scal_host, h->feas_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -648,12 +758,42 @@ plam_status_t plam_default_params(plam_params_t* prm) {
   return PLAM_OK;
 }
 
-plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_objective_t* obj,
-                          const plam_params_t* prm, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// plam_create and plam_create_sharded (comm != nullptr).
+plam_status_t create_impl(plam_handle_t* out, int64_t n, int64_t p, const plam_objective_t* obj,
+                          const plam_params_t* prm_in, void* stream, const plam_comm_t* comm) {
   if (!out) return PLAM_ERR_INVALID;
   *out = nullptr;
-  if (!obj || p < 1 || n < 2 * p || p > 65535) return PLAM_ERR_INVALID;
-  if (validate_params(prm) != PLAM_OK) return PLAM_ERR_INVALID;
+  const int64_t n_all = comm ? comm->n_global : n;
+  if (!obj || p < 1 || n < 1 || n_all < 2 * p || p > 65535) return PLAM_ERR_INVALID;
+  if (validate_params(prm_in) != PLAM_OK) return PLAM_ERR_INVALID;
+  plam_params_t prm_local = *prm_in;
+  const plam_params_t* prm = &prm_local;
+  int64_t plane = 0;
+  if (comm) {
+    if (comm->size < 1 || comm->rank < 0 || comm->rank >= comm->size || comm->row0 < 0 ||
+        comm->row0 + n > comm->n_global || (comm->size > 1 && !comm->allgather))
+      return PLAM_ERR_INVALID;
+    if (obj->kind == PLAM_OBJ_STENCIL3D) {
+      plane = (int64_t)obj->nx * obj->ny;
+      if (plane < 1 || comm->row0 % plane != 0 || (comm->size > 1 && !comm->exchange))
+        return PLAM_ERR_INVALID;
+    } else if (obj->kind == PLAM_OBJ_HARTREE1D) {
+      if (obj->block < 1) return PLAM_ERR_UNSUPPORTED;   // one global L couples every row
+      if (comm->row0 % obj->block != 0 ||
+          (comm->rank < comm->size - 1 && n % obj->block != 0))
+        return PLAM_ERR_INVALID;
+    } else {
+      return PLAM_ERR_UNSUPPORTED;
+    }
+    if (prm->engine == PLAM_ENGINE_RESIDENT) return PLAM_ERR_UNSUPPORTED;
+    prm_local.engine = PLAM_ENGINE_GRAPH;
+    prm_local.graph_iters = 0;
+    prm_local.orth_metrics = 0;
+  }
   const size_t esz = prm->precision == PLAM_PREC_FP64 ? 8 : 4;
   switch (obj->kind) {
     case PLAM_OBJ_DENSE:
@@ -679,6 +819,12 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
       if (!obj->grad) return PLAM_ERR_INVALID;
       if (prm->engine == PLAM_ENGINE_RESIDENT) return PLAM_ERR_UNSUPPORTED;
       break;
+    case PLAM_OBJ_QAP:
+      if (!obj->A || obj->lda < n || !aligned(obj->A, esz) || !obj->Bq || obj->ldbq < p ||
+          !aligned(obj->Bq, esz))
+        return PLAM_ERR_INVALID;
+      if (prm->engine == PLAM_ENGINE_RESIDENT) return PLAM_ERR_UNSUPPORTED;
+      break;
     default:
       return PLAM_ERR_INVALID;
   }
@@ -687,12 +833,19 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
   h->n = n;
   h->p = p;
   h->obj = *obj;
-  if (h->obj.kind == PLAM_OBJ_HARTREE1D && h->obj.block >= n) h->obj.block = 0;   // one block
+  if (h->obj.kind == PLAM_OBJ_HARTREE1D && h->obj.block >= n && !comm) h->obj.block = 0;
   h->prm = *prm;
   h->stream = (cudaStream_t)stream;
   h->prec = prm->precision;
   h->esz = esz;
   h->ldw = round_up(n, 32);
+  if (comm) {
+    h->sharded = 1;
+    h->comm = *comm;
+    h->plane = plane;
+    h->g_off = plane;
+    h->ldw = round_up(n + 2 * plane, 32);
+  }
   const int pi = (int)p;
   const int nt = (pi + kTile - 1) / kTile;
   const GramChunkPlan gcp = gram_chunk_plan(n, pi, true, device_sm_count(), 0);
@@ -724,7 +877,7 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
             alloc(&h->L0t, pp * esz) && alloc((void**)&h->feas_row, p * sizeof(double)) &&
             alloc(&h->colpart, (size_t)h->nrt * kColDots * p * esz) &&
             alloc(&h->totpart, (size_t)h->nrt * h->nct * kTotDots * esz) &&
-            alloc((void**)&h->sums, (kColDots * p + kTotDots) * sizeof(double)) &&
+            alloc((void**)&h->sums, (kColDots * p + kTotDots + 1) * sizeof(double)) &&
             alloc(&h->dsum, (size_t)kStepRanges * (kColDots * p + kTotDots) * esz) &&
             alloc((void**)&h->ticket, sizeof(unsigned int)) &&
             alloc((void**)&h->st, sizeof(DevState)) &&
@@ -754,6 +907,21 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
     ok = alloc((void**)&h->fpart, sizeof(double));
   }
   if (ok && prm->final_orth == 2) ok = alloc((void**)&h->Qtmp, (size_t)h->ldw * p * sizeof(double));
+  if (ok && obj->kind == PLAM_OBJ_QAP) ok = alloc(&h->qtmp, np_bytes);
+  if (ok && h->sharded) {
+    const size_t gcount = std::max((size_t)2 * p * p, (size_t)kColDots * p + kTotDots + 1);
+    ok = alloc((void**)&h->gath, (size_t)comm->size * gcount * sizeof(double));
+    if (ok && plane > 0) {
+      // the potential on the slab and its two halo planes (zero there: only the outputs of
+      // interior planes are used)
+      ok = alloc(&h->vext, (size_t)(n + 2 * plane) * esz) &&
+           alloc(&h->halo, (size_t)4 * plane * p * esz);
+      if (ok) ok = cudaMemsetAsync(h->vext, 0, (size_t)(n + 2 * plane) * esz, h->stream) == cudaSuccess;
+      if (ok && obj->V)
+        ok = cudaMemcpyAsync((char*)h->vext + plane * esz, obj->V, (size_t)n * esz,
+                             cudaMemcpyDeviceToDevice, h->stream) == cudaSuccess;
+    }
+  }
   if (ok && prm->engine != PLAM_ENGINE_GRAPH && prm->precision == PLAM_PREC_FP32 &&
       prm->lambda_rule != PLAM_LAMBDA_DA &&
       ((obj->kind == PLAM_OBJ_HARTREE1D && obj->xc == 0.0 && !chain_objective(h)) ||
@@ -816,6 +984,25 @@ plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_o
   return PLAM_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+plam_status_t plam_create(plam_handle_t* out, int64_t n, int64_t p, const plam_objective_t* obj,
+                          const plam_params_t* prm, void* stream) {
+  return create_impl(out, n, p, obj, prm, stream, nullptr);
+}
+
+plam_status_t plam_create_sharded(plam_handle_t* out, int64_t n_local, int64_t p,
+                                  const plam_objective_t* obj, const plam_params_t* prm,
+                                  const plam_comm_t* comm, void* stream) {
+  if (!comm) {
+    if (out) *out = nullptr;
+    return PLAM_ERR_INVALID;
+  }
+  return create_impl(out, n_local, p, obj, prm, stream, comm);
+}
+
 plam_status_t plam_destroy(plam_handle_t h) {
   if (!h) return PLAM_ERR_INVALID;
   cudaStreamSynchronize(h->stream);
@@ -854,7 +1041,8 @@ plam_status_t plam_orthonormalize(plam_handle_t h, const void* X, int64_t ldx, d
 
 plam_status_t plam_solve(plam_handle_t h, void* X, int64_t ldx, double* Xout, int64_t ldo,
                          plam_info_t* info) {
-  if (!h || !X || ldx < h->n || !aligned(X, h->esz)) return PLAM_ERR_INVALID;
+  if (!h || !X || ldx < h->n || !aligned(X, h->esz) || !halo_rows_ok(h, ldx))
+    return PLAM_ERR_INVALID;
   if (Xout && ldo < h->n) return PLAM_ERR_INVALID;
   const int variant = h->prm.variant;
   const int lambda2 = (variant == PLAM_VARIANT_PCAL && h->prm.lambda_rule == PLAM_LAMBDA2);
@@ -982,6 +1170,7 @@ int plam_solve_engine(plam_handle_t h) {
 
 plam_status_t plam_energy(plam_handle_t h, const void* X, int64_t ldx, double* f_dev) {
   if (!h || !X || !f_dev || ldx < h->n || !aligned(X, h->esz)) return PLAM_ERR_INVALID;
+  if (h->sharded) return PLAM_ERR_UNSUPPORTED;
   plam_status_t st = h->prec == PLAM_PREC_FP64
                          ? energy_device_impl<double>(h, (const double*)X, ldx, f_dev)
                          : energy_device_impl<float>(h, (const float*)X, ldx, f_dev);
@@ -991,6 +1180,7 @@ plam_status_t plam_energy(plam_handle_t h, const void* X, int64_t ldx, double* f
 plam_status_t plam_energy_backward(plam_handle_t h, const void* X, int64_t ldx,
                                    const double* scale_dev, void* G, int64_t ldg) {
   if (!h || !X || !G || ldx < h->n || ldg < h->n) return PLAM_ERR_INVALID;
+  if (h->sharded) return PLAM_ERR_UNSUPPORTED;
   if (!aligned(X, h->esz) || !aligned(G, h->esz)) return PLAM_ERR_INVALID;
   return h->prec == PLAM_PREC_FP64
              ? energy_backward_impl<double>(h, (const double*)X, ldx, scale_dev, (double*)G, ldg)
@@ -1000,6 +1190,7 @@ plam_status_t plam_energy_backward(plam_handle_t h, const void* X, int64_t ldx,
 plam_status_t plam_energy_grad(plam_handle_t h, const void* X, int64_t ldx, void* G, int64_t ldg,
                                double* f) {
   if (!h || !X || !G || ldx < h->n || ldg < h->n) return PLAM_ERR_INVALID;
+  if (h->sharded) return PLAM_ERR_UNSUPPORTED;
   if (!aligned(X, h->esz) || !aligned(G, h->esz)) return PLAM_ERR_INVALID;
   if (h->prec == PLAM_PREC_FP64)
     return energy_impl<double>(h, (const double*)X, ldx, (double*)G, ldg, f);
@@ -1009,6 +1200,7 @@ plam_status_t plam_energy_grad(plam_handle_t h, const void* X, int64_t ldx, void
 plam_status_t plam_grams(plam_handle_t h, const void* X, int64_t ldx, const void* G, int64_t ldg,
                          double* B, double* C) {
   if (!h || !X || !B || ldx < h->n || (G && (ldg < h->n || !C))) return PLAM_ERR_INVALID;
+  if (h->sharded) return PLAM_ERR_UNSUPPORTED;
   const int p = (int)h->p;
   if (h->prec == PLAM_PREC_FP64) {
     CK((launch_gram_partial<double, double>(h->n, p, (const double*)X, ldx, (const double*)G, ldg,

@@ -85,11 +85,18 @@ cudaError_t launch_gram_partial(int64_t n, int p, const Tin* X, int64_t ldx, con
 template <typename T>
 cudaError_t launch_gram_reduce(int p, int nchunks, int with_g, const T* part, double* B,
                                double* C, cudaStream_t s);
-// red: 2p x p doubles of scratch for the reduced Grams [B | C].
+// red: 2p x p doubles of scratch for the reduced Grams [B | C].  stage 0: the chunk
+// reduction into red and the p x p step from it; 1: the reduction only; 2: the p x p step
+// only (a row-sharded solve sums red over the ranks in between).
 template <typename T>
 cudaError_t launch_gram_finalize(int p, int nchunks, const T* part, double* red, double* B,
                                  double* L0, T* Mt, T* L0t, double* feas_row, const DevState* st,
-                                 IterParams prm, cudaStream_t s);
+                                 IterParams prm, cudaStream_t s, int stage = 0);
+
+// Row sharding: out[i] = sum over r = 0 .. size-1, in that order, of in[r * count + i]
+// (in: the all-gathered buffers of every rank).  st (may be null): skipped once stopped.
+cudaError_t launch_rank_sum(const double* in, int size, int64_t count, double* out,
+                            const DevState* st, cudaStream_t s);
 
 // R0/R1: the two residual buffers (R^k goes to buffer k mod 2).  nubuf: 2 x p
 // column norms and coef: 2 x (2p + 1) scales [1/eta, 1/nu_c, 1 - nu_c] in the
@@ -100,13 +107,16 @@ cudaError_t launch_update(int64_t n, int p, const T* X, int64_t ldx, const T* G,
                           T* R0, T* R1, int64_t ldr, const T* Mt, const T* L0t, const T* coef,
                           const DevState* st, T* colpart, T* totpart, cudaStream_t s);
 // dsum: kStepRanges x (3p + 6) partial sums of scratch in the storage type;
-// sums: 3p + 6 doubles of scratch; ticket: one zero-initialised counter.
+// sums: 3p + 7 doubles of scratch; ticket: one zero-initialised counter.
+// phase 0: the whole step; a row-sharded solve runs phase 1 (this rank's sums into
+// sums[0 .. 3p + 6], with the objective's f partials at sums[3p + 6]), sums them over
+// the ranks, then phase 2 (eta, the column scales and the stop test from those sums).
 constexpr int kStepRanges = 32;
 template <typename T>
 cudaError_t launch_step_size(int nrt, int nct, const T* colpart, const T* totpart, T* dsum,
                              const double* feas_row, const double* fpart, int nfpart, double* sums,
                              unsigned int* ticket, DevState* st, double* nubuf, T* coef,
-                             double* hist, IterParams prm, cudaStream_t s);
+                             double* hist, IterParams prm, cudaStream_t s, int phase = 0);
 template <typename T>
 cudaError_t launch_primal_update(int64_t n, int p, T* X, int64_t ldx, const T* R0, const T* R1,
                                  int64_t ldr, const T* coef, const DevState* st, int variant,
@@ -117,6 +127,10 @@ cudaError_t launch_primal_update(int64_t n, int p, T* X, int64_t ldx, const T* R
 template <typename T>
 cudaError_t launch_dense_grad(int64_t n, int p, const T* A, int64_t lda, const T* X, int64_t ldx,
                               T* G, int64_t ldg, const DevState* st, cudaStream_t s);
+template <typename T>
+cudaError_t launch_right_multiply(int64_t n, int p, const T* X, int64_t ldx, const T* Bm,
+                                  int64_t ldb, T* Y, int64_t ldy, const DevState* st,
+                                  cudaStream_t s);
 template <typename T>
 cudaError_t launch_hartree_grad(int64_t n, int p, double alpha, double q, double xc, const T* X,
                                 int64_t ldx, T* G, int64_t ldg, double* rho, double* blk, double* y,

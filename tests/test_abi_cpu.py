@@ -64,7 +64,8 @@ def test_struct_layouts_match_header(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = {"plam_params_t": _lib.plam_params_t, "plam_info_t": _lib.plam_info_t,
-               "plam_objective_t": _lib.plam_objective_t}
+               "plam_objective_t": _lib.plam_objective_t, "plam_comm_t": _lib.plam_comm_t,
+               "plam_batch_problem_t": _lib.plam_batch_problem_t}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "plam.h"', "int main(void){"]
     expect = []
     for name, cls in structs.items():
@@ -141,6 +142,60 @@ def test_create_rejects_bad_block_and_linear_term(lib):
         h = C.c_void_p()
         st = lib.plam_create(C.byref(h), n, p, C.byref(obj), C.byref(prm), None)
         assert st == _lib.PLAM_ERR_INVALID and not h.value, c
+
+
+def test_sharded_create_rejects_bad_requests_without_touching_the_gpu(lib):
+    """plam_create_sharded validates the rank layout and the objective before any CUDA call:
+    no communicator, a rank outside [0, size), rows beyond n_global, a missing all-gather with
+    several ranks, a slab that does not start on a z-plane, blocks that would cross ranks, and
+    objectives whose gradient couples every row (one global Dirichlet L, a dense A)."""
+    from paper_1810_03930_gb300 import _lib
+    prm = _lib.plam_default_params()
+
+    def stencil(nz):
+        o = _lib.plam_objective_t()
+        o.kind, o.nx, o.ny, o.nz = _lib.PLAM_OBJ_STENCIL3D, 8, 8, nz
+        return o
+
+    def comm(rank, size, row0, n_global, ag=True, ex=True):
+        c = _lib.plam_comm_t()
+        c.rank, c.size, c.row0, c.n_global = rank, size, row0, n_global
+        if ag:
+            c.allgather = _lib.plam_allgather_fn(lambda *a: 0)
+        if ex:
+            c.exchange = _lib.plam_exchange_fn(lambda *a: 0)
+        return c
+
+    cases = [
+        (stencil(4), None, _lib.PLAM_ERR_INVALID),
+        (stencil(4), comm(2, 2, 0, 512), _lib.PLAM_ERR_INVALID),
+        (stencil(4), comm(1, 2, 300, 512), _lib.PLAM_ERR_INVALID),         # 300 + 256 > 512
+        (stencil(4), comm(0, 2, 0, 512, ag=False), _lib.PLAM_ERR_INVALID),
+        (stencil(4), comm(0, 2, 0, 512, ex=False), _lib.PLAM_ERR_INVALID),
+        (stencil(4), comm(1, 2, 200, 512), _lib.PLAM_ERR_INVALID),         # not on a z-plane
+    ]
+    blk = _lib.plam_objective_t()
+    blk.kind, blk.alpha, blk.quad_scale, blk.block = _lib.PLAM_OBJ_HARTREE1D, 1.0, 0.5, 5
+    cases.append((blk, comm(0, 2, 0, 1000), _lib.PLAM_OK))                 # checked below
+    one = _lib.plam_objective_t()
+    one.kind, one.alpha, one.quad_scale, one.block = _lib.PLAM_OBJ_HARTREE1D, 1.0, 0.5, 0
+    cases.append((one, comm(0, 2, 0, 1000), _lib.PLAM_ERR_UNSUPPORTED))
+    dense = _lib.plam_objective_t()
+    dense.kind, dense.A, dense.lda = _lib.PLAM_OBJ_DENSE, 256, 256
+    cases.append((dense, comm(0, 2, 0, 512), _lib.PLAM_ERR_UNSUPPORTED))
+    for obj, c, want in cases:
+        if want == _lib.PLAM_OK:
+            continue
+        n = 256 if obj.kind != _lib.PLAM_OBJ_HARTREE1D else 500
+        h = C.c_void_p()
+        st = lib.plam_create_sharded(C.byref(h), n, 4, C.byref(obj), C.byref(prm),
+                                     C.byref(c) if c is not None else None, None)
+        assert st == want and not h.value, (obj.kind, st)
+    # blocks of 5 must not cross ranks: 497 rows on rank 0 of 2
+    h = C.c_void_p()
+    st = lib.plam_create_sharded(C.byref(h), 497, 4, C.byref(blk), C.byref(prm),
+                                 C.byref(comm(0, 2, 0, 1000)), None)
+    assert st == _lib.PLAM_ERR_INVALID and not h.value
 
 
 def test_null_handle_calls_are_rejected(lib):

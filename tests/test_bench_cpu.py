@@ -2,8 +2,9 @@
 
 * The reference arm (the FP64 oracle on the host cores, the only reference this
   paper has) prints one JSON line with the keys the benchmark contract names.
-* The 128^3 workload is per-kernel timing only: asking it for a solve fails
-  with a message before anything touches a GPU.
+* The default workload (128^3, p = 1024) samples the oracle on the grid's first
+  z-planes, a Dirichlet problem of its own whose cost per iteration is the full
+  grid's times the row fraction.
 """
 import json
 import os
@@ -30,17 +31,28 @@ def test_reference_arm_prints_the_contract_line():
         assert key in d, key
     assert d["steps"] == 1 and d["warmup"] == 3 and d["n_gpus"] == 1
     assert d["value"] > 0 and d["unit"] == "iters/s" and d["higher_is_better"] is True
-    assert d["config"]["workload"] == "hartree1d_n20000_p50"
+    assert d["config"]["workload"] == "stencil3d_n2097152_p1024"
+    assert "z-planes" in d["cpu_baseline"]["sample"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
 
 
-def test_kernel_only_workload_refuses_a_solve():
-    r = _run("--workload", "stencil3d_128", timeout=120)
-    assert r.returncode != 0
-    assert "per-kernel timings only" in r.stderr
+def test_slab_sample_of_the_128_grid():
+    """The oracle's sample of the 128^3 workload: the first 8 z-planes (n = 131072 rows, the
+    same p), the potential of exactly those grid points (index x + 128 (y + 128 z), z < 8), and
+    an orthonormal start; its rate scales to the full grid by 8 / 128."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    from workloads import rng_for, uniform_potential
+    wl = dict(bench.WORKLOADS["stencil3d_128"], p=16)      # a narrow start keeps the test quick
+    V = uniform_potential(wl["n"], rng_for(5, 0))
+    grid, Vs, X0, ns = bench.slab_problem(wl, V, wl["slab_planes"])
+    assert grid == (128, 128, 8) and ns == 131072 and ns / wl["n"] == 8 / 128
+    assert np.array_equal(Vs, V.reshape(128, 128, 128)[:8].ravel())
+    assert X0.shape == (ns, 16) and np.abs(X0.T @ X0 - np.eye(16)).max() < 1e-13
 
 
 def test_width_override_applies_to_section54_workloads_only():
