@@ -14,6 +14,8 @@ Layout
                  final orthonormalisation (Section 5.3, Table "orth step")
   kernels.py     per-step reference values (Grams, multipliers, update,
                  column dots) for element-wise parity tests of single kernels
+  moptqr.py      MOptQR, the comparison solver of Sections 5.3-5.4 (Table
+                 "cost": projected gradient, Cholesky retraction, ABB step)
 
 Parity status: every function here is pinned by a `-m "not gpu"` test against
 closed forms, brute-force eigensolves, finite differences or invariants the
@@ -21,4 +23,4 @@ paper states, except the step-size sequence of the Barzilai-Borwein rules,
 whose iterates the paper never prints: "parity unpinned" for `eta` values
 beyond the invariants checked in tests/test_oracle_pins.py.
 """
-from . import objectives, plam, kernels  # noqa: F401
+from . import objectives, plam, kernels, moptqr  # noqa: F401

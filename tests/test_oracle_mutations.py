@@ -146,3 +146,19 @@ def test_problem4_gradient_without_b_is_caught(monkeypatch):
     monkeypatch.setattr(oo.QAPObjective, "grad", lambda self, X: self.A @ X)
     with pytest.raises(AssertionError):
         pins.test_gradient_finite_difference("qap")
+
+
+@pytest.mark.parametrize("wrong", ["unprojected_gradient", "column_normalisation"])
+def test_moptqr_mistakes_are_caught(monkeypatch, wrong):
+    """MOptQR's projected gradient without the projection X (G^T X), or a retraction that only
+    normalises the columns of V (no Cholesky factor): a pin fails for each."""
+    from oracle import moptqr as om
+    if wrong == "unprojected_gradient":
+        monkeypatch.setattr(om, "projected_gradient", lambda G, X: G)
+        with pytest.raises(AssertionError):
+            pins.test_moptqr_first_step_by_hand()
+    else:
+        monkeypatch.setattr(om, "cholesky_retraction",
+                            lambda V: np.asfortranarray(V / np.linalg.norm(V, axis=0)[None, :]))
+        with pytest.raises(AssertionError):
+            pins.test_moptqr_retraction_is_the_qr_factor_and_keeps_feasibility()

@@ -692,3 +692,61 @@ def test_multiplier_study_conclusion_on_problems_1_and_2():
                 if rule == closed:
                     assert all(r.converged for r in rs), (prob, variant, its)
             assert np.median(its["da"]) >= 2.5 * np.median(its[closed]), (prob, variant, its)
+
+
+# ---------------------------------------------------------------- MOptQR (Sections 5.3-5.4)
+
+
+def test_moptqr_retraction_is_the_qr_factor_and_keeps_feasibility():
+    """Table "cost"'s Cholesky retraction V L^{-T} (V^T V = L L^T) is the Q factor of V with a
+    positive diagonal of R (Householder QR, a different algorithm); the projected gradient
+    D = G - X G^T X is tangent (X^T D skew-symmetric) at a feasible X; and every MOptQR iterate
+    stays feasible to rounding."""
+    from oracle import moptqr as om
+    w = workload_dense_trace(200, 8)
+    # Problem 2's linear term makes X^T G unsymmetric, so the skew part of X^T D is not zero
+    obj = oo.QuadLinearObjective(w.A, np.random.default_rng(9).standard_normal((200, 8)))
+    X = w.X0
+    G = obj.grad(X)
+    D = om.projected_gradient(G, X)
+    S = X.T @ D
+    assert np.abs(S).max() > 1e-3 * np.abs(X.T @ G).max()
+    assert np.abs(S + S.T).max() <= 1e-13 * np.abs(X.T @ G).max()
+    V = X - 0.05 * D
+    np.testing.assert_allclose(om.cholesky_retraction(V), op.orthonormalize(V), rtol=0, atol=1e-13)
+    r = om.solve(obj, X, tol=1e-10, maxit=20)
+    assert all(h.feas <= 1e-13 for h in r.history)
+
+
+def test_moptqr_converges_to_ky_fan_optimum():
+    """Problem 3's generator (dense trace), n = 200, p = 8: MOptQR with ABB steps reaches half
+    the sum of the 8 smallest eigenvalues (Ky Fan), like PLAM and PCAL do."""
+    from oracle import moptqr as om
+    w = workload_dense_trace(200, 8)
+    obj = oo.TraceObjective(w.A)
+    fstar = 0.5 * np.linalg.eigvalsh(w.A)[:8].sum()
+    r = om.solve(obj, w.X0, tol=1e-10, maxit=5000)
+    assert r.converged and not r.diverged
+    assert abs(r.f_orth - fstar) <= 1e-10 * abs(fstar)
+    assert r.feas_orth <= 1e-13
+
+
+def test_moptqr_first_step_by_hand():
+    """One iteration written out: eta^0 = ||G||_F / ||X||_F (no penalty), V = X - D / eta^0,
+    X^1 = Q of V; and the second step size is BB1 = |<S,Y>| / <S,S> of S = X^1 - X^0,
+    Y = D^1 - D^0 (ABB, odd k)."""
+    from oracle import moptqr as om
+    w = workload_dense_trace(120, 5)
+    obj = oo.TraceObjective(w.A)
+    X0 = w.X0
+    G0 = obj.grad(X0)
+    eta0 = np.linalg.norm(G0) / np.linalg.norm(X0)
+    D0 = G0 - X0 @ (G0.T @ X0)
+    X1 = op.orthonormalize(X0 - D0 / eta0)
+    D1 = obj.grad(X1) - X1 @ (obj.grad(X1).T @ X1)
+    S, Y = X1 - X0, D1 - D0
+    eta1 = abs(np.sum(S * Y)) / np.sum(S * S)
+    r = om.solve(obj, X0, tol=0.0, maxit=2)
+    assert abs(r.history[0].eta - eta0) <= 1e-13 * eta0
+    assert abs(r.history[1].eta - eta1) <= 1e-11 * eta1
+
