@@ -87,6 +87,9 @@ def parse_args():
     ap.add_argument("--p", type=int, default=0,
                     help="block_hartree / tridiag_linear only: the width p (Section 5.4 sweeps "
                          "p = 500 ... 2500 at n = 10000); 0 keeps 1000")
+    ap.add_argument("--solver", choices=["pcal", "moptqr"], default="pcal",
+                    help="block_hartree / tridiag_linear only: PCAL, or MOptQR (the comparison "
+                         "solver of Section 5.4: a Cholesky retraction every iteration)")
     ap.add_argument("--beta", type=float, default=0.0,
                     help="block_hartree / tridiag_linear only: the penalty beta (0 keeps the "
                          "paper's PCAL default 1; from p ~ 0.18 n on, beta = 1 lets the columns "
@@ -104,6 +107,11 @@ def workload_config(args, **extra):
             raise SystemExit(f"--p must lie in [1, {wl['n'] // 2}]")
         wl["name"] = wl["name"].replace(f"_p{wl['p']}", f"_p{args.p}")
         wl["p"] = args.p
+    if getattr(args, "solver", "pcal") != "pcal":
+        if not wl.get("section54"):
+            raise SystemExit("--solver applies to the block_hartree and tridiag_linear workloads")
+        wl["variant"] = args.solver
+        wl["name"] += f"_{args.solver}"
     if getattr(args, "beta", 0.0):
         if not wl.get("section54"):
             raise SystemExit("--beta applies to the block_hartree and tridiag_linear workloads")
@@ -208,6 +216,11 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- roofline helpers
 
+def sm_count(torch):
+    """Streaming multiprocessors of the current device (152 on a GB300)."""
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -293,6 +306,7 @@ def recorded_traffic(kernel, workload):
 
 
 def golden_fstar(name):
+    name = name.replace("_moptqr", "")
     path = os.path.join(ROOT, "tests", "golden", f"{name}_optimum.json")
     try:
         return json.load(open(path))
@@ -309,7 +323,8 @@ def golden_fstar(name):
 
 def make_solver(wl, precision, torch, engine="auto", final_orth=1, maxit=3000, tensor_cores=None):
     from paper_1810_03930_gb300 import Solver
-    kw = dict(variant="pcal", lambda_rule="lambda2", beta=wl["beta"], tol=wl["tol"], maxit=maxit,
+    kw = dict(variant=wl.get("variant", "pcal"), lambda_rule="lambda2", beta=wl["beta"],
+              tol=wl["tol"], maxit=maxit,
               precision=precision, final_orth=final_orth, graph_iters=16, engine=engine,
               tensor_cores=tensor_cores or wl.get("tensor_cores", "auto"), orth_metrics=False)
     if wl["kind"] == "stencil3d":
@@ -488,10 +503,10 @@ def run_ours(args, rank, world, local):
         sol_k.close()
         t_launch = statistics.mean(ms_k) / 1e3
         achieved = flops_iter * statistics.mean(its_k) / t_launch / 1e12
-        peak = 152 * 128 * 2 * clock_mhz * 1e6 / 1e12
+        peak = sm_count(torch) * 128 * 2 * clock_mhz * 1e6 / 1e12
         roofline = {"bound": "alu", "kernel": "resident_solve_kernel", "achieved": achieved,
                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x median SM clock "
+                    "peak_source": f"derived: {sm_count(torch)} SMs x 128 FP32 FMA lanes x 2 flop x median SM clock "
                                    f"{clock_mhz:.0f} MHz",
                     "traffic": recorded_traffic("resident", wl["name"]),
                     "alg_flops_per_launch": flops_iter * statistics.mean(its_k),
@@ -506,7 +521,30 @@ def run_ours(args, rank, world, local):
     Xk = X0d.clone()
     sol_g.reset()
     kms, done = sol_g.time_kernels(Xk, 3000)
+    # the paper's categories (Fig. "OCQP-percentage"): "Func" the objective, "BLAS3" the Grams,
+    # the p x p step and the update product, "Orth" MOptQR's retraction every iteration or
+    # PCAL's one final Cholesky-QR (timed here on the last iterate), "other" PCAL's column
+    # scaling step
+    Qo = sol_g.new_matrix(dtype=torch.float64)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    sol_g.orthonormalize(Xk, Qo)
+    e1.record()
+    torch.cuda.synchronize()
+    orth_ms = e0.elapsed_time(e1)
+    del Qo
     sol_g.close()
+    moptqr = wl.get("variant") == "moptqr"
+    cat = {"func": kms["objective"] * done,
+           "blas3": (kms["gram_partial"] + kms["gram_finalize"] + kms["update"] +
+                     kms["step_size"]) * done,
+           "orth": kms["primal_update"] * done + (0.0 if moptqr else orth_ms),
+           "other": 0.0 if moptqr else kms["primal_update"] * done}
+    tot = sum(cat.values())
+    categories = {"iterations": done, "ms": cat,
+                  "share": {k: v / tot for k, v in cat.items()} if tot > 0 else None,
+                  "note": "per-iteration kernel-group times (CUDA events, plain launches) x the "
+                          "iterations of the solve; PCAL's Orth is its final Cholesky-QR"}
     kb = kernel_bytes(wl, 4)
     dom = max(kms, key=lambda k: kms[k])
     achieved_g = kb[dom] / (kms[dom] * 1e-3) / 1e9
@@ -534,7 +572,7 @@ def run_ours(args, rank, world, local):
                           "traffic": recorded_traffic(kernel_names[dom], wl["name"]),
                           "alg_flops_per_launch": kf[dom], "alg_bytes_per_launch": kb[dom],
                           "launch_ms": kms[dom]}
-    if engine == "graph":
+    if engine != "resident":
         roofline = roofline_graph
     # ---- end to end through the public API with host buffers
     Xh = torch.empty(X0d.shape, dtype=torch.float32, pin_memory=True)
@@ -556,7 +594,9 @@ def run_ours(args, rank, world, local):
                           "hartree1d": "1/4 tr(X^T L X) + alpha/4 rho^T L^-1 rho",
                           "stencil3d": "1/2 tr(X^T (L3 + Diag(V)) X), 7-point Dirichlet L3 on 64^3, "
                                        "V iid U[0,1]"}.get(wl["kind"], "1/2 tr(X^T A X)"),
-                      "n": wl["n"], "p": wl["p"], "solver": "PCAL eq.(lambda2), ABB",
+                      "n": wl["n"], "p": wl["p"],
+                      "solver": ("MOptQR (Cholesky retraction every iteration), ABB"
+                                 if wl.get("variant") == "moptqr" else "PCAL eq.(lambda2), ABB"),
                       "beta": wl["beta"], "tol_kkt_rel": wl["tol"], "final_orth": "FP64 Cholesky-QR",
                       "l2": "flushed before every step (256 MB write)",
                       "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -565,6 +605,7 @@ def run_ours(args, rank, world, local):
            "parity": parity, "objective_1e-6_solve": tight, "engine": engine,
            "roofline": roofline, "graph_engine": graph_engine,
            "graph_engine_roofline": roofline_graph, "graph_engine_kernels_ms_per_launch": kms,
+           "categories": categories,
            "e2e": e2e,
            "gpu_launches": int(launches), "clocks": clocks}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1106,11 +1147,11 @@ def run_batched(args, rank, world, local):
     # roofline: the kernel is bound by its FP32 arithmetic (A stays in L2 while a CTA works on it)
     flops = sum(i.iters * (2.0 * w.n * w.n * w.p + 8.0 * w.n * w.p * w.p) for w, i in zip(ws, infos))
     clock_mhz = clocks.get("sm_mhz") or 2070.0
-    peak = 152 * 128 * 2 * clock_mhz * 1e6 / 1e12
+    peak = sm_count(torch) * 128 * 2 * clock_mhz * 1e6 / 1e12
     achieved = flops / (ms_per_step * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": "batched_solve_kernel", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x median SM clock "
+                "peak_source": f"derived: {sm_count(torch)} SMs x 128 FP32 FMA lanes x 2 flop x median SM clock "
                                f"{clock_mhz:.0f} MHz",
                 "alg_flops_per_launch": flops, "launch_ms": ms_per_step}
     # FP64 comparator: sequential single-problem FP64 solves of a sample, scaled by cost

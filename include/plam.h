@@ -58,7 +58,11 @@ typedef enum {
   PLAM_ERR_UNSUPPORTED = 8     /* valid request that this build does not implement */
 } plam_status_t;
 
-enum { PLAM_VARIANT_PLAM = 0, PLAM_VARIANT_PCAL = 1 };
+/* MOPTQR: the comparison solver of Sections 5.3-5.4 (plam_solve only): a Riemannian gradient
+ * step on the projected gradient D = G - X G^T X with the same Barzilai-Borwein rules, then
+ * the Cholesky retraction X <- V L^{-T}, V = X - D/eta, V^T V = L L^T, every iteration
+ * (Table "cost"); the retraction's Gram, Cholesky and product run in FP64 arithmetic. */
+enum { PLAM_VARIANT_PLAM = 0, PLAM_VARIANT_PCAL = 1, PLAM_VARIANT_MOPTQR = 2 };
 /* Multiplier rule: eq. (Lambda1), eq. (lambda2) (PCAL only), or the dual
  * ascent step of Algorithm 1, Lambda^k = Lambda^{k-1} - beta ((X^k)^T X^k - I)
  * from Lambda^0 = Psi(grad f(X^0)^T X^0) (PLAM-DA / PCAL-DA, Section 5.3's
@@ -113,7 +117,8 @@ typedef int (*plam_grad_fn)(void* ctx, const void* X, int64_t ldx, void* G, int6
 enum { PLAM_ENGINE_AUTO = 0, PLAM_ENGINE_GRAPH = 1, PLAM_ENGINE_RESIDENT = 2 };
 
 typedef struct {
-  int variant;          /* PLAM_VARIANT_* used by plam_solve (plam_step/pcal_step choose their own) */
+  int variant;          /* PLAM_VARIANT_* used by plam_solve (plam_step/pcal_step choose their own;
+                           MOPTQR: plam_solve and plam_time_kernels only, not row-sharded) */
   int lambda_rule;      /* PLAM_LAMBDA1 / PLAM_LAMBDA2 / PLAM_LAMBDA_DA; PCAL default LAMBDA2;
                            PLAM uses LAMBDA1 unless DA is asked for */
   double beta;          /* penalty parameter beta > = 0 */

@@ -124,7 +124,8 @@ class Solver:
         self.precision = precision
         self.dtype = storage_dtype(precision)
         prm = plam_default_params()
-        prm.variant = PLAM_VARIANT_PCAL if variant == "pcal" else PLAM_VARIANT_PLAM
+        prm.variant = {"plam": PLAM_VARIANT_PLAM, "pcal": PLAM_VARIANT_PCAL,
+                       "moptqr": _lib.PLAM_VARIANT_MOPTQR}[variant]
         prm.lambda_rule = {"lambda1": PLAM_LAMBDA1, "lambda2": PLAM_LAMBDA2, "da": 2}[lambda_rule]
         prm.beta = float(beta)
         prm.eta_rule = _RULES[eta_rule]

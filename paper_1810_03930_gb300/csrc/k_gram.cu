@@ -246,7 +246,8 @@ gram_finalize_kernel(int p, const double* __restrict__ red, double* __restrict__
       lam = da_first ? Lrow[j] : *lp - beta * (Brow[j] - delta);
       *lp = lam;
     }
-    const double m = lam - beta * (Brow[j] - delta);
+    // MOptQR (Table "cost"): R = G - X (G^T X), i.e. the product with C^T = G^T X
+    const double m = prm.moptqr ? red[(size_t)(p + j) * p + i] : lam - beta * (Brow[j] - delta);
     Mt[j + (size_t)i * p] = (T)m;
     L0t[j + (size_t)i * p] = (T)Lrow[j];
     if (Bout) Bout[j + (size_t)i * p] = Brow[j];

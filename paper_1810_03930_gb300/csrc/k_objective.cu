@@ -212,13 +212,14 @@ hartree_grad_kernel(int64_t n, int p, double alpha, double q, double xc, double 
 //                         so that f = 1/2 <X, G> + (sum of the partials).
 
 constexpr int kChainTile = 256;
-constexpr int kChainTargetCtas = 8 * 152;
+constexpr int kChainCtasPerSm = 8;   // the row tiles x column groups aim at this many CTAs per SM
 
 ChainPlan chain_plan(int64_t n, int p, int64_t block, bool need_y) {
   ChainPlan c;
   c.tile = (need_y && block > 0) ? (int)((kChainTile / block) * block) : kChainTile;
   c.ntiles = (int)((n + c.tile - 1) / c.tile);
-  const int64_t want = (kChainTargetCtas + (int64_t)c.ntiles - 1) / c.ntiles;
+  const int64_t target = (int64_t)kChainCtasPerSm * device_sm_count();
+  const int64_t want = (target + (int64_t)c.ntiles - 1) / c.ntiles;
   const int ncg = (int)std::max<int64_t>(1, std::min<int64_t>(p, want));
   c.cw = (p + ncg - 1) / ncg;
   c.ncg = (p + c.cw - 1) / c.cw;

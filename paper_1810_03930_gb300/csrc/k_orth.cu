@@ -246,10 +246,11 @@ cholesky_inverse_smem_kernel(int p, const double* __restrict__ B, double* __rest
   }
 }
 
-template <typename T>
+template <typename T, typename To>
 __global__ void __launch_bounds__(kThreads)
 apply_rinv_kernel(int64_t n, int p, const T* __restrict__ X, int64_t ldx, const double* __restrict__ Z,
-                  double* __restrict__ Q, int64_t ldq) {
+                  To* __restrict__ Q, int64_t ldq, const DevState* __restrict__ st) {
+  if (st != nullptr && st->stop != kRunning) return;
   constexpr int KS = 16;
   const int64_t r0 = (int64_t)blockIdx.x * kTile;
   const int c0 = blockIdx.y * kTile;
@@ -314,7 +315,7 @@ apply_rinv_kernel(int64_t n, int p, const T* __restrict__ X, int64_t ldx, const 
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int64_t r = r0 + tx + 16 * u;
-      if (r < n) Q[r + (int64_t)c * ldq] = acc[u][v];
+      if (r < n) Q[r + (int64_t)c * ldq] = (To)acc[u][v];
     }
   }
 }
@@ -379,7 +380,15 @@ template <typename T>
 cudaError_t launch_apply_rinv(int64_t n, int p, const T* X, int64_t ldx, const double* Z, double* Q,
                               int64_t ldq, cudaStream_t s) {
   dim3 grid((unsigned)((n + kTile - 1) / kTile), (p + kTile - 1) / kTile);
-  apply_rinv_kernel<T><<<grid, kThreads, 0, s>>>(n, p, X, ldx, Z, Q, ldq);
+  apply_rinv_kernel<T, double><<<grid, kThreads, 0, s>>>(n, p, X, ldx, Z, Q, ldq, nullptr);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_apply_rinv_same(int64_t n, int p, const T* X, int64_t ldx, const double* Z, T* Q,
+                                   int64_t ldq, const DevState* st, cudaStream_t s) {
+  dim3 grid((unsigned)((n + kTile - 1) / kTile), (p + kTile - 1) / kTile);
+  apply_rinv_kernel<T, T><<<grid, kThreads, 0, s>>>(n, p, X, ldx, Z, Q, ldq, st);
   return cudaGetLastError();
 }
 
@@ -395,5 +404,11 @@ template cudaError_t launch_apply_rinv<float>(int64_t, int, const float*, int64_
                                               double*, int64_t, cudaStream_t);
 template cudaError_t launch_apply_rinv<double>(int64_t, int, const double*, int64_t, const double*,
                                                double*, int64_t, cudaStream_t);
+template cudaError_t launch_apply_rinv_same<float>(int64_t, int, const float*, int64_t,
+                                                   const double*, float*, int64_t, const DevState*,
+                                                   cudaStream_t);
+template cudaError_t launch_apply_rinv_same<double>(int64_t, int, const double*, int64_t,
+                                                    const double*, double*, int64_t,
+                                                    const DevState*, cudaStream_t);
 
 }  // namespace plam

@@ -471,11 +471,11 @@ template <typename T>
 cudaError_t launch_primal_update(int64_t n, int p, T* X, int64_t ldx, const T* R0, const T* R1,
                                  int64_t ldr, const T* coef, const DevState* st, int variant,
                                  cudaStream_t s) {
-  // one wave of CTAs (152 SMs x 8), grid-stride over rows: the state and scale
+  // one wave of CTAs (8 per SM), grid-stride over rows: the state and scale
   // loads at the top of each CTA are paid once, not once per 256 elements
   const int threads = 256;
   int64_t bx = (n + threads - 1) / threads;
-  const int64_t cap = (152 * 8 + p - 1) / p;
+  const int64_t cap = ((int64_t)device_sm_count() * 8 + p - 1) / p;
   if (bx > cap) bx = cap;
   if (bx < 1) bx = 1;
   dim3 grid((unsigned)bx, p);

@@ -144,6 +144,8 @@ struct plam_handle_s {
   void* halo = nullptr;     // 4 x plane x p staging: send_lo, send_hi, recv_lo, recv_hi
   double* gath = nullptr;   // size x max(2 p^2, 3p + 7) doubles: the all-gather's receive buffer
   void* qtmp = nullptr;     // n x p work of Problem 4's gradient (A X before the product with B)
+  void* xprev = nullptr;    // MOptQR: the previous iterate (S = X - X_prev), leading dimension ldw
+  void* vbuf = nullptr;     // MOptQR: the retraction's output before it is copied back to X
 };
 
 namespace {
@@ -177,7 +179,7 @@ __global__ void dot_partial_kernel(int64_t n, int p, const T* __restrict__ X, in
 
 plam_status_t validate_params(const plam_params_t* prm) {
   if (!prm) return PLAM_ERR_INVALID;
-  if (prm->variant != PLAM_VARIANT_PLAM && prm->variant != PLAM_VARIANT_PCAL) return PLAM_ERR_INVALID;
+  if (prm->variant < PLAM_VARIANT_PLAM || prm->variant > PLAM_VARIANT_MOPTQR) return PLAM_ERR_INVALID;
   if (prm->lambda_rule < PLAM_LAMBDA1 || prm->lambda_rule > PLAM_LAMBDA_DA) return PLAM_ERR_INVALID;
   if (prm->eta_rule < PLAM_ETA_ABB || prm->eta_rule > PLAM_ETA_DIFF) return PLAM_ERR_INVALID;
   if (prm->precision != PLAM_PREC_FP64 && prm->precision != PLAM_PREC_FP32) return PLAM_ERR_INVALID;
@@ -227,6 +229,13 @@ IterParams iter_params(const plam_handle_s* h, int variant, int lambda2) {
   ip.lambda_da = h->prm.lambda_rule == PLAM_LAMBDA_DA;
   ip.lam = h->lam;
   ip.refine_switch = h->use_tc ? h->prm.refine_switch : 0.0;
+  if (variant == PLAM_VARIANT_MOPTQR) {   // no penalty, no column scaling, M = C^T
+    ip.moptqr = 1;
+    ip.variant = PLAM_VARIANT_PLAM;
+    ip.lambda2 = 0;
+    ip.lambda_da = 0;
+    ip.beta = 0.0;
+  }
   return ip;
 }
 
@@ -280,11 +289,13 @@ plam_status_t comm_fail(const char* what) {
 }
 
 // Sum `count` doubles at buf over the ranks (all-gather, then the rank-order sum) in place.
+// st: the iteration's state (the sum is skipped once the run has stopped, like every kernel
+// of an iteration), or null outside the iteration (the final orthonormalisation).
 plam_status_t shard_allreduce(plam_handle_s* h, double* buf, int64_t count, cudaStream_t s,
-                              int* nk) {
+                              int* nk, const DevState* st) {
   if (h->comm.size == 1) return PLAM_OK;
   if (h->comm.allgather(h->comm.ctx, buf, h->gath, count, (void*)s) != 0) return comm_fail("allgather");
-  CK(launch_rank_sum(h->gath, h->comm.size, count, buf, h->st, s));
+  CK(launch_rank_sum(h->gath, h->comm.size, count, buf, st, s));
   *nk += 1;
   return PLAM_OK;
 }
@@ -313,6 +324,30 @@ plam_status_t shard_halo(plam_handle_s* h, T* X, int64_t ldx, cudaStream_t s) {
     CK(cudaMemcpy2DAsync(X + n, pitch, recv_hi, pl * w, pl * w, h->p, cudaMemcpyDeviceToDevice, s));
   else
     CK(cudaMemset2DAsync(X + n, pitch, 0, pl * w, h->p, s));
+  return PLAM_OK;
+}
+
+// MOptQR's retraction after the step-size kernel (Table "cost"): X_prev <- X (the
+// Barzilai-Borwein S of the next iteration), X <- V = X - D/eta (the PLAM form of the primal
+// update), then X <- V R^{-1} with V^T V = R^T R, the Gram, Cholesky and product in FP64
+// arithmetic (from a copy of V, so that X stays the converged iterate once the run stopped:
+// the kernels that write X skip then).  Returns kernels launched in *nk.
+template <typename T>
+plam_status_t moptqr_retract(plam_handle_s* h, T* X, int64_t ldx, cudaStream_t s, int* nk) {
+  const int p = (int)h->p;
+  const size_t w = sizeof(T);
+  CK(cudaMemcpy2DAsync(h->xprev, (size_t)h->ldw * w, X, (size_t)ldx * w, (size_t)h->n * w, p,
+                       cudaMemcpyDeviceToDevice, s));
+  CK(launch_primal_update<T>(h->n, p, X, ldx, (const T*)h->R[0], (const T*)h->R[1], h->ldw,
+                             (const T*)h->coef, h->st, PLAM_VARIANT_PLAM, s));
+  CK(cudaMemcpy2DAsync(h->vbuf, (size_t)h->ldw * w, X, (size_t)ldx * w, (size_t)h->n * w, p,
+                       cudaMemcpyDeviceToDevice, s));
+  CK((launch_gram_partial<T, double>(h->n, p, (const T*)h->vbuf, h->ldw, (const T*)nullptr, 0,
+                                      h->rows_per_chunk, h->nchunks, h->part64, h->st, s)));
+  CK(launch_gram_reduce<double>(p, h->nchunks, 0, h->part64, h->B, nullptr, s));
+  CK(launch_cholesky_inverse(p, h->B, h->W, h->Z, h->info, s));
+  CK(launch_apply_rinv_same<T>(h->n, p, (const T*)h->vbuf, h->ldw, h->Z, X, ldx, h->st, s));
+  *nk += 4 + cholesky_inverse_launches(p);
   return PLAM_OK;
 }
 
@@ -355,7 +390,7 @@ plam_status_t launch_iteration(plam_handle_s* h, T* X, int64_t ldx, int variant,
   if (h->sharded) {
     CK(launch_gram_finalize<T>(p, nch, (const T*)h->part, h->red, h->B, h->L0, (T*)h->Mt,
                                (T*)h->L0t, h->feas_row, h->st, ip, s, 1));
-    plam_status_t as = shard_allreduce(h, h->red, (int64_t)2 * p * p, s, &k);
+    plam_status_t as = shard_allreduce(h, h->red, (int64_t)2 * p * p, s, &k, h->st);
     if (as != PLAM_OK) return as;
     CK(launch_gram_finalize<T>(p, nch, (const T*)h->part, h->red, h->B, h->L0, (T*)h->Mt,
                                (T*)h->L0t, h->feas_row, h->st, ip, s, 2));
@@ -366,7 +401,9 @@ plam_status_t launch_iteration(plam_handle_s* h, T* X, int64_t ldx, int variant,
   }
   if (ev) CK(cudaEventRecord(ev[3], s));
   int nrt = h->nrt, nct = h->nct;
+  bool tc_upd = false;
   if (sizeof(T) == 4 && h->use_tc && tc_update_supported(X, ldx)) {
+    tc_upd = true;
     CK(launch_tc_update(h->n, p, (const float*)X, ldx, (const float*)G, h->ldw, (float*)h->R[0],
                         (float*)h->R[1], h->ldw, (const float*)h->Mt, (const float*)h->L0t, h->tcu,
                         h->msplit, (const float*)h->coef, h->st, (float*)h->colpart,
@@ -380,12 +417,19 @@ plam_status_t launch_iteration(plam_handle_s* h, T* X, int64_t ldx, int variant,
                         (const T*)h->Mt, (const T*)h->L0t, (const T*)h->coef, h->st,
                         (T*)h->colpart, (T*)h->totpart, s));
   }
+  if (ip.moptqr) {   // the update's S/Y sums assume the PLAM/PCAL step: MOptQR's own
+    CK(launch_mopt_bb<T>(h->n, p, X, ldx, (const T*)h->xprev, h->ldw, (const T*)h->R[0],
+                         (const T*)h->R[1], h->ldw, tc_upd ? 128 : kTile, tc_upd ? h->tcu.N : kTile,
+                         nrt, nct, (T*)h->totpart, h->st, s));
+    k += 1;
+  }
   if (ev) CK(cudaEventRecord(ev[4], s));
   if (h->sharded) {
     CK(launch_step_size<T>(nrt, nct, (const T*)h->colpart, (const T*)h->totpart, (T*)h->dsum,
                            h->feas_row, h->fpart, h->nfpart, h->sums, h->ticket, h->st, h->nubuf,
                            (T*)h->coef, h->hist, ip, s, 1));
-    plam_status_t as = shard_allreduce(h, h->sums, (int64_t)kColDots * p + kTotDots + 1, s, &k);
+    plam_status_t as = shard_allreduce(h, h->sums, (int64_t)kColDots * p + kTotDots + 1, s, &k,
+                                       h->st);
     if (as != PLAM_OK) return as;
     CK(launch_step_size<T>(nrt, nct, (const T*)h->colpart, (const T*)h->totpart, (T*)h->dsum,
                            h->feas_row, h->fpart, h->nfpart, h->sums, h->ticket, h->st, h->nubuf,
@@ -398,8 +442,15 @@ plam_status_t launch_iteration(plam_handle_s* h, T* X, int64_t ldx, int variant,
                            h->ticket, h->st, h->nubuf, (T*)h->coef, h->hist, ip, s));
   }
   if (ev) CK(cudaEventRecord(ev[5], s));
-  CK(launch_primal_update<T>(h->n, p, X, ldx, (const T*)h->R[0], (const T*)h->R[1], h->ldw,
-                             (const T*)h->coef, h->st, variant, s));
+  if (ip.moptqr) {
+    int nr = 0;
+    plam_status_t rs = moptqr_retract<T>(h, X, ldx, s, &nr);
+    if (rs != PLAM_OK) return rs;
+    k += nr - 1;
+  } else {
+    CK(launch_primal_update<T>(h->n, p, X, ldx, (const T*)h->R[0], (const T*)h->R[1], h->ldw,
+                               (const T*)h->coef, h->st, variant, s));
+  }
   if (ev) CK(cudaEventRecord(ev[6], s));
   *nk = k + 6;
   return PLAM_OK;
@@ -477,7 +528,7 @@ void free_handle(plam_handle_s* h) {
                  h->rho, h->blk, h->y, h->fpart, h->W, h->Z, h->info, h->feas_dev, h->Qtmp,
                  h->dotpart, h->r_halo, h->r_blk, h->r_part, h->r_red, h->r_dots, h->r_dred,
                  h->r_bar, h->r_err, h->tc_err, h->msplit, h->kkt_part, h->lam, h->vext,
-                 h->halo, h->gath, h->qtmp};
+                 h->halo, h->gath, h->qtmp, h->xprev, h->vbuf};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (h->st_host) cudaFreeHost(h->st_host);
@@ -505,7 +556,7 @@ plam_status_t orthonormalize_impl(plam_handle_s* h, const T* X, int64_t ldx, dou
     CK(launch_gram_reduce<double>(p, h->nchunks, 0, h->part64, h->B, nullptr, s));
     if (h->sharded) {
       int nk = 0;
-      plam_status_t as = shard_allreduce(h, h->B, (int64_t)p * p, s, &nk);   // X^T X over all rows
+      plam_status_t as = shard_allreduce(h, h->B, (int64_t)p * p, s, &nk, nullptr);   // all rows
       if (as != PLAM_OK) return as;
       h->launches += nk;
     }
@@ -535,7 +586,7 @@ plam_status_t orthonormalize_impl(plam_handle_s* h, const T* X, int64_t ldx, dou
     CK(launch_gram_reduce<double>(p, h->nchunks, 0, h->part64, h->B, nullptr, s));
     if (h->sharded) {
       int nk = 0;
-      plam_status_t as = shard_allreduce(h, h->B, (int64_t)p * p, s, &nk);
+      plam_status_t as = shard_allreduce(h, h->B, (int64_t)p * p, s, &nk, nullptr);
       if (as != PLAM_OK) return as;
       h->launches += nk;
     }
@@ -789,7 +840,8 @@ plam_status_t create_impl(plam_handle_t* out, int64_t n, int64_t p, const plam_o
     } else {
       return PLAM_ERR_UNSUPPORTED;
     }
-    if (prm->engine == PLAM_ENGINE_RESIDENT) return PLAM_ERR_UNSUPPORTED;
+    if (prm->engine == PLAM_ENGINE_RESIDENT || prm->variant == PLAM_VARIANT_MOPTQR)
+      return PLAM_ERR_UNSUPPORTED;
     prm_local.engine = PLAM_ENGINE_GRAPH;
     prm_local.graph_iters = 0;
     prm_local.orth_metrics = 0;
@@ -908,6 +960,7 @@ plam_status_t create_impl(plam_handle_t* out, int64_t n, int64_t p, const plam_o
   }
   if (ok && prm->final_orth == 2) ok = alloc((void**)&h->Qtmp, (size_t)h->ldw * p * sizeof(double));
   if (ok && obj->kind == PLAM_OBJ_QAP) ok = alloc(&h->qtmp, np_bytes);
+  if (ok && prm->variant == PLAM_VARIANT_MOPTQR) ok = alloc(&h->xprev, np_bytes) && alloc(&h->vbuf, np_bytes);
   if (ok && h->sharded) {
     const size_t gcount = std::max((size_t)2 * p * p, (size_t)kColDots * p + kTotDots + 1);
     ok = alloc((void**)&h->gath, (size_t)comm->size * gcount * sizeof(double));
@@ -923,7 +976,7 @@ plam_status_t create_impl(plam_handle_t* out, int64_t n, int64_t p, const plam_o
     }
   }
   if (ok && prm->engine != PLAM_ENGINE_GRAPH && prm->precision == PLAM_PREC_FP32 &&
-      prm->lambda_rule != PLAM_LAMBDA_DA &&
+      prm->lambda_rule != PLAM_LAMBDA_DA && prm->variant != PLAM_VARIANT_MOPTQR &&
       ((obj->kind == PLAM_OBJ_HARTREE1D && obj->xc == 0.0 && !chain_objective(h)) ||
        obj->kind == PLAM_OBJ_DENSE)) {
     int dev = 0, sms = 0, optin = 0, coop = 0;
@@ -1048,8 +1101,10 @@ plam_status_t plam_solve(plam_handle_t h, void* X, int64_t ldx, double* Xout, in
   const int lambda2 = (variant == PLAM_VARIANT_PCAL && h->prm.lambda_rule == PLAM_LAMBDA2);
   plam_status_t st = reset_state(h);
   if (st != PLAM_OK) return st;
-  // a user gradient runs on the host between the kernels: no graph capture
-  const int gi = h->obj.kind == PLAM_OBJ_CALLBACK ? 0 : h->prm.graph_iters;
+  // a user gradient runs on the host between the kernels, and MOptQR's retraction checks its
+  // Cholesky factorisation on the host: no graph capture
+  const int gi = (h->obj.kind == PLAM_OBJ_CALLBACK || variant == PLAM_VARIANT_MOPTQR)
+                     ? 0 : h->prm.graph_iters;
   int stop = kRunning;
   if (h->r_nblk > 0) {
     // resident engine: the whole loop in one cooperative launch
@@ -1121,10 +1176,19 @@ plam_status_t plam_solve(plam_handle_t h, void* X, int64_t ldx, double* Xout, in
       st = dispatch_iteration(h, X, ldx, variant, lambda2, h->stream, &nk);
       if (st != PLAM_OK) return st;
       h->launches += nk;
-      if ((it & 15) == 15 || it == h->prm.maxit) {
+      if ((it & 15) == 15 || it == h->prm.maxit || variant == PLAM_VARIANT_MOPTQR) {
         st = read_state(h, nullptr, &stop);
         if (st != PLAM_OK) return st;
         if (stop != kRunning) break;
+        if (variant == PLAM_VARIANT_MOPTQR) {   // the retraction's Cholesky of V^T V
+          CK(cudaMemcpyAsync(h->info_host, h->info, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+          CK(cudaStreamSynchronize(h->stream));
+          if (*h->info_host != 0) {
+            snprintf(g_err, sizeof(g_err), "MOptQR retraction: Cholesky pivot %d not positive",
+                     *h->info_host);
+            return PLAM_ERR_CHOLESKY;
+          }
+        }
       }
     }
     st = read_state(h, nullptr, &stop);
@@ -1164,7 +1228,8 @@ plam_status_t plam_solve(plam_handle_t h, void* X, int64_t ldx, double* Xout, in
 int plam_solve_engine(plam_handle_t h) {
   if (!h) return -1;
   if (h->r_nblk > 0) return PLAM_ENGINE_RESIDENT;
-  const int gi = h->obj.kind == PLAM_OBJ_CALLBACK ? 0 : h->prm.graph_iters;
+  const int gi = (h->obj.kind == PLAM_OBJ_CALLBACK || h->prm.variant == PLAM_VARIANT_MOPTQR)
+                     ? 0 : h->prm.graph_iters;
   return gi > 0 ? PLAM_ENGINE_GRAPH : 0;
 }
 

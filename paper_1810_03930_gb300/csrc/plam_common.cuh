@@ -67,7 +67,16 @@ struct IterParams {
   int lambda_da;         // 1: dual ascent Lambda^k = Lambda^{k-1} - beta (B^k - I) (PLAM-DA, PCAL-DA)
   double* lam;           // p x p FP64 multiplier carried across iterations (dual ascent only)
   double refine_switch;  // <= 0: the compensated phase never starts on its own (see DevState.refine)
+  int moptqr;            // 1: MOptQR's update matrix, M = C^T (R = G - X G^T X), no penalty
 };
+
+// MOptQR's Barzilai-Borwein sums of S = X - X_prev and Y = R^k - R^{k-1}, per tile of the
+// update kernel that ran (tile_rows x tile_cols tiles, nct tile columns): written over the
+// update's per-tile slots 0..2 of totpart (zeros at k = 0).
+template <typename T>
+cudaError_t launch_mopt_bb(int64_t n, int p, const T* X, int64_t ldx, const T* Xprev, int64_t ldxp,
+                           const T* R0, const T* R1, int64_t ldr, int tile_rows, int tile_cols,
+                           int nrt, int nct, T* totpart, const DevState* st, cudaStream_t s);
 
 // Number of per-column dot products written by the update kernel and the
 // number of whole-matrix sums (see update_kernel).
@@ -161,6 +170,11 @@ int cholesky_inverse_launches(int p);   // kernels launch_cholesky_inverse launc
 template <typename T>
 cudaError_t launch_apply_rinv(int64_t n, int p, const T* X, int64_t ldx, const double* Z,
                               double* Q, int64_t ldq, cudaStream_t s);
+// The same product written in the storage type (MOptQR's retraction X <- V R^{-1}); st (may
+// be null): skipped once the run has stopped.
+template <typename T>
+cudaError_t launch_apply_rinv_same(int64_t n, int p, const T* X, int64_t ldx, const double* Z, T* Q,
+                                   int64_t ldq, const DevState* st, cudaStream_t s);
 // out[0] = ||B - I||_F (p x p, FP64); col: p doubles of per-column sums.
 cudaError_t launch_feas(int p, const double* B, double* col, double* out, cudaStream_t s);
 
