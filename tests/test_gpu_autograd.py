@@ -290,3 +290,58 @@ def test_closed_form_multiplier_beats_dual_ascent_on_problems_1_and_2():
                         assert abs(info.iters - ref.iters) <= max(5, 0.25 * ref.iters), (
                             prob, variant, info.iters, ref.iters)
             assert np.median(its["da"]) >= 2.5 * np.median(its[closed]), (prob, variant, its)
+
+
+def test_penalty_study_conclusion_on_problem2_and_problem4():
+    """Section 5.1's penalty study (Fig. "beta") on the GPU, FP64, on the seeded instances the
+    oracle's test uses (n = 200, p = 8, ABB, relative KKT 1e-6): PLAM with a small penalty
+    (beta = 0.01 s) diverges on some Problem 2 instances (user energy in torch) and with beta = 0
+    on some Problem 4 instances (the built-in PLAM_OBJ_QAP), while PCAL converges on every
+    instance at beta = 0, 0.01 s and 10 s + 1, the last the slowest (median)."""
+    from oracle import objectives as oo2
+    from paper_1810_03930_gb300 import Solver
+    from workloads import multiplier_study_problems, orthonormal_start, paper_p4_matrices, rng_for
+    _, p2 = multiplier_study_problems()
+    n, p = 200, 8
+
+    def solve(make, variant, beta):
+        s = make(variant, beta)
+        st, info = s.solve(to_dev(s._x0, s))
+        s.close()
+        return st, info
+
+    cases2 = []
+    for A, lam, Gl, X0 in p2:
+        At = torch.as_tensor(A, device="cuda")
+        Gt = torch.as_tensor(Gl, device="cuda")
+
+        def make(variant, beta, At=At, Gt=Gt, X0=X0):
+            def energy(X):
+                return 0.5 * torch.sum(X * (At @ X)) + torch.sum(Gt * X)
+            s = Solver(n, p, "callback", energy=energy, variant=variant, beta=beta, tol=1e-6,
+                       maxit=3000, precision="fp64", final_orth=0)
+            s._x0 = X0
+            return s
+        cases2.append((make, float(np.max(np.abs(lam)))))
+    cases4 = []
+    for i in range(6):
+        A, B = paper_p4_matrices(n, p, rng_for(22, 0, sub=i))
+        X0 = orthonormal_start(n, p, rng_for(22, 1, sub=i))
+
+        def make(variant, beta, A=A, B=B, X0=X0):
+            s = Solver(n, p, "qap", A=A, B=B, variant=variant, beta=beta, tol=1e-6, maxit=3000,
+                       precision="fp64", final_orth=0)
+            s._x0 = X0
+            return s
+        cases4.append((make, oo2.QAPObjective(A, B).hess_norm_bound()))
+    div2 = sum(solve(m, "plam", 0.01 * s)[0] == 3 for m, s in cases2)
+    div4 = sum(solve(m, "plam", 0.0)[0] == 3 for m, s in cases4)
+    assert div2 >= 3 and div4 >= 1, (div2, div4)
+    for cases in (cases2, cases4):
+        med = {}
+        for name, f in (("0", lambda s: 0.0), ("0.01s", lambda s: 0.01 * s),
+                        ("10s+1", lambda s: 10 * s + 1)):
+            out = [solve(m, "pcal", f(s)) for m, s in cases]
+            assert all(st == 0 and info.converged for st, info in out), name
+            med[name] = np.median([info.iters for _, info in out])
+        assert med["10s+1"] == max(med.values()), med

@@ -750,3 +750,50 @@ def test_moptqr_first_step_by_hand():
     assert abs(r.history[0].eta - eta0) <= 1e-13 * eta0
     assert abs(r.history[1].eta - eta1) <= 1e-11 * eta1
 
+
+
+def test_penalty_study_conclusion_on_problems_1_to_4():
+    """Section 5.1's penalty study (Figs. "beta", "PCAL_beta_sensitive"), beta in {0, 0.01s, 0.1s,
+    s + 0.1, 10s + 1}, ABB, relative KKT 1e-6, 6 seeded instances each of Problems 1 (dense
+    Gaussian L, alpha = 1), 2 (Gao et al. generator with a linear term), 3 (dense trace) and 4
+    (symmetrised Gaussian A and B), n = 200, p = 8: PLAM with a small penalty diverges on some
+    instances (Problem 2 at beta = 0 and 0.01s; Problem 4 at beta = 0), PCAL converges on every
+    instance for every beta, and the largest beta is the slowest for both (medians).  Measured
+    with this oracle (5 of 6 Problem 2 runs and 2 of 6 Problem 4 runs of PLAM diverge)."""
+    from workloads import (multiplier_study_problems, paper_p4_matrices, parameter_study_problems)
+    p1, p2 = multiplier_study_problems()
+    probs = {"P1": [], "P2": [], "P3": [], "P4": []}
+    for L, X0 in p1:
+        obj = oo.DenseHartreeObjective(L, alpha=1.0, quad_scale=0.5)
+        probs["P1"].append((obj, obj.hess_norm_bound(), X0))
+    for A, lam, Gl, X0 in p2:
+        probs["P2"].append((oo.QuadLinearObjective(A, Gl), float(np.max(np.abs(lam))), X0))
+    As, X0s = parameter_study_problems()
+    for A, X0 in zip(As[:6], X0s[:6]):
+        probs["P3"].append((oo.TraceObjective(A), float(np.max(np.abs(np.linalg.eigvalsh(A)))), X0))
+    for i in range(6):
+        A, B = paper_p4_matrices(200, 8, rng_for(22, 0, sub=i))
+        obj = oo.QAPObjective(A, B)
+        probs["P4"].append((obj, obj.hess_norm_bound(), orthonormal_start(200, 8, rng_for(22, 1, sub=i))))
+    betas = {"0": lambda s: 0.0, "0.01s": lambda s: 0.01 * s, "0.1s": lambda s: 0.1 * s,
+             "s+0.1": lambda s: s + 0.1, "10s+1": lambda s: 10 * s + 1}
+
+    def run(prob, variant, b):
+        rs = [op.solve(obj, X0, variant=variant, beta=betas[b](s), tol=1e-6, maxit=3000,
+                       record=False) for obj, s, X0 in probs[prob]]
+        return rs
+
+    # PLAM with a small penalty: divergence on some instances
+    assert sum(r.diverged for r in run("P2", "plam", "0")) >= 3
+    assert sum(r.diverged for r in run("P2", "plam", "0.01s")) >= 3
+    assert sum(r.diverged for r in run("P4", "plam", "0")) >= 1
+    for prob in ("P1", "P2", "P3", "P4"):
+        med = {}
+        for b in betas:
+            rs = run(prob, "pcal", b)
+            assert all(r.converged for r in rs), (prob, b)
+            med[b] = np.median([r.iters for r in rs])
+        assert med["10s+1"] == max(med.values()), (prob, med)
+        rs = run(prob, "plam", "10s+1")
+        assert all(r.converged for r in rs)
+        assert np.median([r.iters for r in rs]) > np.median([r.iters for r in run(prob, "plam", "s+0.1")])
