@@ -163,3 +163,38 @@ def test_batched_parameter_study_reproduces_the_papers_conclusions(variant):
     assert st == 0 and info.converged and abs(info.iters - ref0) <= 0.25 * ref0, (info.iters, ref0)
     slow = batch(10 * s + 1, "abb")      # the median counts runs that reach maxit as maxit
     assert median(slow) > 1.3 * median(runs["abb"]), (median(slow), median(runs["abb"]))
+
+
+def test_full_512_problem_batch_to_kkt_1e6():
+    """The batched configuration at full size: 512 problems, n uniform in [64, 2048], p uniform
+    in [4, min(64, n/2)], PCAL with beta = 1, ABB, relative KKT 1e-6, maxit 3000, in one launch.
+    Every problem either converges or belongs to the expected set the FP32 storage cannot take
+    to 1e-6 (R24 of the design notes' readings): those whose spectral gap lambda_{p+1} - lambda_p
+    is below 1e-3 |lambda_p| (FP32 rounding of R is then a large part of the Barzilai-Borwein
+    differences Y); at most 12 of them, each with its objective within 1e-7 of Ky Fan's optimum.
+    The objectives of 32 converged problems spread over the batch (and of the non-converged
+    ones) are checked against the eigenvalue sums, and every output is orthonormal."""
+    from paper_1810_03930_gb300 import BatchSolver
+    shapes = batched_shapes(count=512, n_lo=64, n_hi=2048)
+    ws = [workload_batched_problem(b, n, p) for b, (n, p) in enumerate(shapes)]
+    bs = BatchSolver([w.A for w in ws], [w.X0 for w in ws], variant="pcal", beta=1.0, tol=1e-6,
+                     maxit=3000)
+    infos = bs.solve()
+    stalled = [b for b, i in enumerate(infos) if not i.converged]
+    assert len(stalled) <= 12, stalled
+    checked = sorted(set(range(0, 512, 16)) | set(stalled))
+    for b in checked:
+        w, info = ws[b], infos[b]
+        assert info.feas_orth <= 1e-12, (b, info.as_dict())
+        ev = np.linalg.eigvalsh(w.A)
+        fstar = 0.5 * ev[: w.p].sum()
+        f = oo.TraceObjective(w.A).value(to_host(bs.Q[b], w.n))
+        if info.converged:
+            assert info.kkt_rel < 1e-6
+            assert abs(f - fstar) <= 1e-6 * abs(fstar), (b, f, fstar)
+        else:
+            assert info.status == 2 and info.iters == 3000, (b, info.as_dict())
+            assert ev[w.p] - ev[w.p - 1] < 1e-3 * abs(ev[w.p - 1]), (b, ev[w.p - 1], ev[w.p])
+            assert abs(f - fstar) <= 1e-7 * abs(fstar), (b, f, fstar)
+    print(f"512-problem batch: {512 - len(stalled)} converged, stalled (small gaps): {stalled}")
+    bs.close()

@@ -1,0 +1,105 @@
+"""The 3D workloads at full size on the GPU, against what pins them:
+  64^3, p = 256 (n = 262144): one PCAL iteration from the seeded start against the oracle's
+    (FP32 storage, tensor-core Grams and update), entry by entry; the solve to relative KKT
+    1e-5 against the stored optimum (Ky Fan, oracle Lanczos, tests/golden);
+  128^3, p = 1024 (n = 2097152, 8.6 GB per n x p buffer): the companion instance with a
+    separable potential, whose optimum is exact (tests/golden, three tridiagonal eigensolves),
+    solved as the benchmark solves it (about 5 minutes)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import objectives as oo
+from oracle import plam as op
+from tests.gpu_helpers import ITER_FACTOR, assert_entrywise, gpu_solver, to_dev, to_host
+from workloads import stencil3d_separable_potential, workload_stencil3d
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_64cube_one_iteration_matches_oracle_entrywise():
+    w = workload_stencil3d(m=64, p=256)
+    V32 = w.V.astype(np.float32).astype(np.float64)
+    X0 = w.X0.astype(np.float32).astype(np.float64)
+    ref = op.solve(oo.Stencil3DObjective(w.m, V32), X0, variant="pcal", beta=1.0, tol=0.0, maxit=1)
+    s = gpu_solver(w, "fp32", variant="pcal", beta=1.0, tol=0.0, maxit=1, final_orth=0,
+                   tensor_cores="tf32", refine_switch=0.0, engine="graph")
+    Xd = to_dev(w.X0, s)
+    st, info = s.step(Xd)
+    assert st == 0 and info.iters == 1
+    # the step X^1 - X^0 (TF32 products: 2^-11 operands)
+    assert_entrywise(to_host(Xd, w.n) - X0, ref.X - X0, ITER_FACTOR * 4e-3, what="X^1 - X^0")
+    assert abs(info.eta - ref.history[0].eta) <= 1e-3 * ref.history[0].eta
+    s.close()
+
+
+def test_64cube_solve_reaches_stored_optimum():
+    g = json.load(open(os.path.join(GOLDEN, "stencil3d_n262144_p256_optimum.json")))
+    w = workload_stencil3d(m=64, p=256)
+    s = gpu_solver(w, "fp32", variant="pcal", beta=1.0, tol=1e-5, maxit=3000, final_orth=1,
+                   orth_metrics=False)
+    Qd = s.new_matrix(dtype=torch.float64)
+    st, info = s.solve(to_dev(w.X0, s), Qd)
+    assert st == 0 and info.converged
+    Q = to_host(Qd, w.n)
+    f = oo.Stencil3DObjective(w.m, w.V).value(Q)
+    assert abs(f - g["f_star"]) <= 1e-6 * abs(g["f_star"]), (f, g["f_star"])
+    assert op.feasibility(Q) <= 1e-12
+    s.close()
+
+
+def _stencil_energy64(Q, V, m):
+    """1/2 tr(Q^T (L3 + V) Q) in FP64 on the device, 32 columns at a time (Q: (p, n))."""
+    n = m ** 3
+    Vg = V.view(m, m, m)
+    tot = 0.0
+    for c0 in range(0, Q.shape[0], 32):
+        q = Q[c0:c0 + 32, :n].reshape(-1, m, m, m)
+        g = (6.0 + Vg) * q
+        g[:, 1:] -= q[:, :-1]
+        g[:, :-1] -= q[:, 1:]
+        g[:, :, 1:] -= q[:, :, :-1]
+        g[:, :, :-1] -= q[:, :, 1:]
+        g[:, :, :, 1:] -= q[:, :, :, :-1]
+        g[:, :, :, :-1] -= q[:, :, :, 1:]
+        tot += float((q * g).sum())
+    return 0.5 * tot
+
+
+def test_128cube_separable_solve_reaches_exact_optimum():
+    """128^3, p = 1024, FP32 storage with tensor cores (TF32, compensated once the KKT value
+    falls below 1e-3 or stalls), from the benchmark's device start, to relative KKT 1e-6 or 3000
+    iterations: an iterate comes within 1e-6 of the exact optimum and the orthonormalised output
+    ends within 1.2e-6 of it (7.9e-7 measured) with feasibility below 1e-11."""
+    from paper_1810_03930_gb300 import Solver
+    g = json.load(open(os.path.join(GOLDEN, "stencil3d_separable_n2097152_p1024_optimum.json")))
+    m, p = 128, 1024
+    n = m ** 3
+    V64 = torch.as_tensor(stencil3d_separable_potential(m)[0], device="cuda")
+    s = Solver(n, p, "stencil3d", grid=(m, m, m), V=V64.to(torch.float32), variant="pcal",
+               beta=1.0, tol=1e-6, maxit=3000, precision="fp32", final_orth=1, engine="graph",
+               orth_metrics=False)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1810039300 + 10 * 5 + 1)
+    Z = torch.randn((p, n), generator=gen, device="cuda", dtype=torch.float32)
+    Q = torch.empty((p, n), dtype=torch.float64, device="cuda")
+    s.orthonormalize(Z, Q)
+    del Z
+    X = Q.to(torch.float32)
+    st, info = s.solve(X, Q)
+    assert st in (0, 2)
+    fstar = g["f_star"]
+    hist = s.history()
+    assert np.min(np.abs(hist[:, 1] - fstar)) <= 1e-6 * abs(fstar)
+    f = _stencil_energy64(Q, V64, m)
+    assert abs(f - fstar) <= 1.2e-6 * abs(fstar), (f, fstar)
+    E = Q @ Q.T
+    E.diagonal().sub_(1.0)
+    assert float(torch.linalg.matrix_norm(E)) <= 1e-11
+    s.close()
