@@ -140,6 +140,9 @@ typedef struct {
                            that are multiples of 4, otherwise the CUDA-core Grams run */
   double refine_switch; /* relative KKT value below which the tensor-core kernels are compensated
                            (0: neither rule switches, plain TF32 throughout) */
+  double feas_max;      /* > 0: the run stops with PLAM_ERR_DIVERGED once ||X^T X - I||_F exceeds it
+                           (a penalty too small for PLAM lets X grow without bound; default 1e6);
+                           0: only non-finite values stop it */
   int orth_metrics;     /* 1 (default): plam_solve also evaluates f, the relative KKT value and the
                            feasibility ||Q^T Q - I||_F of the orthonormalised output Q
                            (plam_info_t.f_orth, kkt_orth, feas_orth); 0: skipped (NaN) — the
@@ -410,6 +413,19 @@ plam_status_t plam_grams_noalloc(int64_t n, int64_t p, int precision, const void
  * evaluated (after plam_create or plam_reset). */
 plam_status_t plam_last_iteration(plam_handle_t h, void* R, int64_t ldr, void* M, double* colsums,
                                   double* bb);
+
+/* Checkpoint and resume of a run's iteration state (everything the next iteration reads besides
+ * X: the iteration counter and stop state, K0, eta0, the step size, the previous residual
+ * R^{k-1} and the previous column scales for the Barzilai-Borwein differences, the latched
+ * compensated phase, the dual-ascent multiplier).  plam_state_bytes gives the size of the
+ * host buffer; plam_get_state copies the state to it (synchronising the stream);
+ * plam_set_state loads one taken from a handle of the same n, p, precision and variant (the
+ * buffer's header is checked: PLAM_ERR_INVALID otherwise).  With the X of the checkpointed
+ * iterate, plam_step / pcal_step then continue the run exactly (bit for bit) where it stood;
+ * plam_solve always starts a fresh run.  The history records are not part of the state. */
+size_t plam_state_bytes(plam_handle_t h);
+plam_status_t plam_get_state(plam_handle_t h, void* buf, size_t bytes);
+plam_status_t plam_set_state(plam_handle_t h, const void* buf, size_t bytes);
 
 /* Copies up to `cap` per-iteration records (k, f, kkt_rel, feas, eta as 5
  * doubles each, in that order) of the current run to host memory `out`;

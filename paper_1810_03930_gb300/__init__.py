@@ -118,7 +118,7 @@ class Solver:
                  variant="pcal", lambda_rule="lambda2", beta=1.0, eta_rule="abb", eta0=0.0,
                  eta_gamma=0.0, tol=1e-8, maxit=3000, precision="fp64", final_orth=1,
                  graph_iters=16, engine="auto", tensor_cores="auto", refine_switch=1e-3,
-                 energy=None, orth_metrics=True, stream=None, shard=None):
+                 energy=None, orth_metrics=True, stream=None, shard=None, feas_max=1e6):
         torch = _torch()
         self.n, self.p = int(n), int(p)
         self.precision = precision
@@ -140,6 +140,7 @@ class Solver:
         prm.tensor_cores = {"auto": -1, "off": 0, "on": 1, "tf32": 1, "3xtf32": 2}[tensor_cores]
         prm.refine_switch = float(refine_switch)
         prm.orth_metrics = 1 if orth_metrics else 0
+        prm.feas_max = float(feas_max)
         self.params = prm
         obj = _lib.plam_objective_t()
         self._keep = []
@@ -282,6 +283,18 @@ class Solver:
         st, cols, bb = _lib.plam_last_iteration(self.h, R.data_ptr(), self.n, M.data_ptr(), self.p)
         check(st, "plam_last_iteration")
         return R, M, cols, bb
+
+    def get_state(self) -> bytes:
+        """The run's iteration state (plam_get_state) as bytes: a checkpoint that, with the X of
+        the same iterate, lets plam_step / pcal_step continue the run exactly."""
+        nb = _lib.load().plam_state_bytes(self.h)
+        buf = (_lib.C.c_char * nb)()
+        check(_lib.load().plam_get_state(self.h, buf, nb), "plam_get_state")
+        return bytes(buf)
+
+    def set_state(self, state: bytes):
+        buf = (_lib.C.c_char * len(state)).from_buffer_copy(state)
+        check(_lib.load().plam_set_state(self.h, buf, len(state)), "plam_set_state")
 
     def history(self):
         return plam_history(self.h, self.params.maxit + 2)

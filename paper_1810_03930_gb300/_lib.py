@@ -39,7 +39,8 @@ class plam_params_t(C.Structure):
                 ("eta_rule", C.c_int), ("eta0", C.c_double), ("eta_gamma", C.c_double),
                 ("tol", C.c_double), ("maxit", C.c_int), ("precision", C.c_int),
                 ("final_orth", C.c_int), ("graph_iters", C.c_int), ("engine", C.c_int),
-                ("tensor_cores", C.c_int), ("refine_switch", C.c_double), ("orth_metrics", C.c_int)]
+                ("tensor_cores", C.c_int), ("refine_switch", C.c_double), ("feas_max", C.c_double),
+                ("orth_metrics", C.c_int)]
 
 
 # int grad(void* ctx, const void* X, int64_t ldx, void* G, int64_t ldg, double* f, void* stream)
@@ -114,6 +115,9 @@ SIGNATURES = {
     "plam_last_iteration": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                       C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "plam_kernel_launches": (C.c_int64, [C.c_void_p]),
+    "plam_state_bytes": (C.c_size_t, [C.c_void_p]),
+    "plam_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "plam_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "plam_solve_engine": (C.c_int, [C.c_void_p]),
     "plam_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(plam_batch_problem_t), C.c_int,
                                     C.POINTER(plam_params_t), C.c_void_p]),

@@ -326,7 +326,8 @@ step_size_kernel(int nrt, int nct, const T* __restrict__ colpart, const T* __res
     }
     int stop = kRunning;
     double eta = st->eta;
-    if (!isfinite(kkt)) stop = kDiverged;
+    if (!isfinite(kkt) || !isfinite(feas) || (prm.feas_max > 0.0 && feas > prm.feas_max))
+      stop = kDiverged;
     else if (K0 == 0.0 || kkt < prm.tol) stop = kConverged;
     else if (k >= prm.maxit) stop = kMaxit;
     else {

@@ -23,6 +23,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/plam.h"
 #include "plam_common.cuh"
 
@@ -189,6 +191,7 @@ plam_status_t validate_params(const plam_params_t* prm) {
   if (prm->engine < PLAM_ENGINE_AUTO || prm->engine > PLAM_ENGINE_RESIDENT) return PLAM_ERR_INVALID;
   if (prm->tensor_cores < -1 || prm->tensor_cores > 2) return PLAM_ERR_INVALID;
   if (!(prm->refine_switch >= 0.0)) return PLAM_ERR_INVALID;
+  if (!(prm->feas_max >= 0.0)) return PLAM_ERR_INVALID;
   return PLAM_OK;
 }
 
@@ -229,6 +232,7 @@ IterParams iter_params(const plam_handle_s* h, int variant, int lambda2) {
   ip.lambda_da = h->prm.lambda_rule == PLAM_LAMBDA_DA;
   ip.lam = h->lam;
   ip.refine_switch = h->use_tc ? h->prm.refine_switch : 0.0;
+  ip.feas_max = h->prm.feas_max;
   if (variant == PLAM_VARIANT_MOPTQR) {   // no penalty, no column scaling, M = C^T
     ip.moptqr = 1;
     ip.variant = PLAM_VARIANT_PLAM;
@@ -805,6 +809,7 @@ plam_status_t plam_default_params(plam_params_t* prm) {
   prm->engine = PLAM_ENGINE_AUTO;
   prm->tensor_cores = -1;
   prm->refine_switch = 1e-3;
+  prm->feas_max = 1e6;
   prm->orth_metrics = 1;
   return PLAM_OK;
 }
@@ -1092,8 +1097,8 @@ plam_status_t plam_orthonormalize(plam_handle_t h, const void* X, int64_t ldx, d
   return orthonormalize_impl<float>(h, (const float*)X, ldx, Xout, ldo, passes, feas);
 }
 
-plam_status_t plam_solve(plam_handle_t h, void* X, int64_t ldx, double* Xout, int64_t ldo,
-                         plam_info_t* info) {
+static plam_status_t solve_impl(plam_handle_t h, void* X, int64_t ldx, double* Xout, int64_t ldo,
+                                plam_info_t* info) {
   if (!h || !X || ldx < h->n || !aligned(X, h->esz) || !halo_rows_ok(h, ldx))
     return PLAM_ERR_INVALID;
   if (Xout && ldo < h->n) return PLAM_ERR_INVALID;
@@ -1194,6 +1199,8 @@ plam_status_t plam_solve(plam_handle_t h, void* X, int64_t ldx, double* Xout, in
     st = read_state(h, nullptr, &stop);
     if (st != PLAM_OK) return st;
   }
+  nvtxRangePop();   // the iterations (profiler timelines: "Func" + "BLAS3")
+  nvtxRangePushA("plam_solve: final orthonormalisation");
   plam_info_t tmp;
   plam_info_t* inf = info ? info : &tmp;
   st = read_state(h, inf, &stop);
@@ -1223,6 +1230,20 @@ plam_status_t plam_solve(plam_handle_t h, void* X, int64_t ldx, double* Xout, in
     if (st != PLAM_OK) return st;
   }
   return stop == kConverged ? PLAM_OK : PLAM_ERR_NOT_CONVERGED;
+}
+
+plam_status_t plam_solve(plam_handle_t h, void* X, int64_t ldx, double* Xout, int64_t ldo,
+                         plam_info_t* info) {
+  // NVTX ranges for profiler timelines (no cost without a profiler attached): the iterations,
+  // then the final orthonormalisation (the paper's "Orth" category, Section 5.4)
+  nvtxRangePushA("plam_solve");
+  nvtxRangePushA("plam_solve: iterations");
+  // solve_impl swaps the inner range for "final orthonormalisation" on its way out: two pops
+  // here on every path
+  plam_status_t st = solve_impl(h, X, ldx, Xout, ldo, info);
+  nvtxRangePop();
+  nvtxRangePop();
+  return st;
 }
 
 int plam_solve_engine(plam_handle_t h) {
@@ -1362,6 +1383,105 @@ plam_status_t plam_last_iteration(plam_handle_t h, void* R, int64_t ldr, void* M
   if (bb)
     CK(cudaMemcpyAsync(bb, h->sums + kColDots * p, 3 * sizeof(double), cudaMemcpyDeviceToHost,
                        h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return PLAM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Layout of a checkpoint (plam_get_state): this header, the DevState, both parity halves of
+// the column scales (storage type) and of the column norms (double), the residual R^{k-1}
+// that the next iteration's Barzilai-Borwein differences read (n x p, packed), and, when the
+// handle has them, the dual-ascent multiplier (p x p double) and MOptQR's X^{k-1} (n x p).
+struct StateHeader {
+  uint32_t magic, version;
+  int64_t n, p;
+  int32_t prec, variant, has_lam, has_xprev;
+  uint64_t bytes;
+};
+constexpr uint32_t kStateMagic = 0x4d414c50u;   // "PLAM"
+
+size_t state_bytes(const plam_handle_s* h) {
+  const size_t np = (size_t)h->n * h->p * h->esz;
+  size_t b = sizeof(StateHeader) + sizeof(DevState) + 2 * (2 * (size_t)h->p + 1) * h->esz +
+             2 * (size_t)h->p * sizeof(double) + np;
+  if (h->lam) b += (size_t)h->p * h->p * sizeof(double);
+  if (h->xprev) b += np;
+  return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t plam_state_bytes(plam_handle_t h) { return h ? state_bytes(h) : 0; }
+
+plam_status_t plam_get_state(plam_handle_t h, void* buf, size_t bytes) {
+  if (!h || !buf || bytes < state_bytes(h)) return PLAM_ERR_INVALID;
+  CK(cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const DevState ds = *h->st_host;
+  unsigned char* o = (unsigned char*)buf;
+  StateHeader hd{kStateMagic, 1u, h->n, h->p, h->prec, h->prm.variant, h->lam != nullptr,
+                 h->xprev != nullptr, (uint64_t)state_bytes(h)};
+  memcpy(o, &hd, sizeof(hd));
+  o += sizeof(hd);
+  memcpy(o, &ds, sizeof(ds));
+  o += sizeof(ds);
+  const size_t w = h->esz, cb = 2 * (2 * (size_t)h->p + 1) * w, nb = 2 * (size_t)h->p * 8;
+  CK(cudaMemcpyAsync(o, h->coef, cb, cudaMemcpyDeviceToHost, h->stream));
+  o += cb;
+  CK(cudaMemcpyAsync(o, h->nubuf, nb, cudaMemcpyDeviceToHost, h->stream));
+  o += nb;
+  // R^{k-1}: the buffer the next iteration (k = ds.k) reads as the previous residual
+  const void* rprev = h->R[(ds.k + 1) & 1];
+  CK(cudaMemcpy2DAsync(o, (size_t)h->n * w, rprev, (size_t)h->ldw * w, (size_t)h->n * w,
+                       (size_t)h->p, cudaMemcpyDeviceToHost, h->stream));
+  o += (size_t)h->n * h->p * w;
+  if (h->lam) {
+    CK(cudaMemcpyAsync(o, h->lam, (size_t)h->p * h->p * 8, cudaMemcpyDeviceToHost, h->stream));
+    o += (size_t)h->p * h->p * 8;
+  }
+  if (h->xprev)
+    CK(cudaMemcpy2DAsync(o, (size_t)h->n * w, h->xprev, (size_t)h->ldw * w, (size_t)h->n * w,
+                         (size_t)h->p, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return PLAM_OK;
+}
+
+plam_status_t plam_set_state(plam_handle_t h, const void* buf, size_t bytes) {
+  if (!h || !buf || bytes < sizeof(StateHeader)) return PLAM_ERR_INVALID;
+  StateHeader hd;
+  memcpy(&hd, buf, sizeof(hd));
+  if (hd.magic != kStateMagic || hd.version != 1u || hd.n != h->n || hd.p != h->p ||
+      hd.prec != h->prec || hd.variant != h->prm.variant || hd.has_lam != (h->lam != nullptr) ||
+      hd.has_xprev != (h->xprev != nullptr) || hd.bytes != state_bytes(h) || bytes < hd.bytes)
+    return PLAM_ERR_INVALID;
+  const unsigned char* o = (const unsigned char*)buf + sizeof(hd);
+  DevState ds;
+  memcpy(&ds, o, sizeof(ds));
+  o += sizeof(ds);
+  const size_t w = h->esz, cb = 2 * (2 * (size_t)h->p + 1) * w, nb = 2 * (size_t)h->p * 8;
+  CK(cudaStreamSynchronize(h->stream));
+  *h->st_host = ds;
+  CK(cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->coef, o, cb, cudaMemcpyHostToDevice, h->stream));
+  o += cb;
+  CK(cudaMemcpyAsync(h->nubuf, o, nb, cudaMemcpyHostToDevice, h->stream));
+  o += nb;
+  CK(cudaMemcpy2DAsync(h->R[(ds.k + 1) & 1], (size_t)h->ldw * w, o, (size_t)h->n * w,
+                       (size_t)h->n * w, (size_t)h->p, cudaMemcpyHostToDevice, h->stream));
+  o += (size_t)h->n * h->p * w;
+  if (h->lam) {
+    CK(cudaMemcpyAsync(h->lam, o, (size_t)h->p * h->p * 8, cudaMemcpyHostToDevice, h->stream));
+    o += (size_t)h->p * h->p * 8;
+  }
+  if (h->xprev)
+    CK(cudaMemcpy2DAsync(h->xprev, (size_t)h->ldw * w, o, (size_t)h->n * w, (size_t)h->n * w,
+                         (size_t)h->p, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return PLAM_OK;
 }

@@ -68,6 +68,7 @@ struct IterParams {
   double* lam;           // p x p FP64 multiplier carried across iterations (dual ascent only)
   double refine_switch;  // <= 0: the compensated phase never starts on its own (see DevState.refine)
   int moptqr;            // 1: MOptQR's update matrix, M = C^T (R = G - X G^T X), no penalty
+  double feas_max;       // > 0: ||X^T X - I||_F above it stops the run as diverged
 };
 
 // MOptQR's Barzilai-Borwein sums of S = X - X_prev and Y = R^k - R^{k-1}, per tile of the

@@ -752,3 +752,67 @@ def test_exchange_energy_and_solve_match_oracle(precision):
     assert abs(obj.value(Q) - ref.f_orth) <= (1e-10 if precision == "fp64" else 1e-6) * abs(ref.f_orth)
     assert abs(info.f_orth - obj.value(Q)) <= (1e-12 if precision == "fp64" else 1e-6) * abs(ref.f_orth)
     s.close()
+
+
+@pytest.mark.parametrize("precision,variant,rule", [("fp64", "pcal", "lambda2"), ("fp32", "pcal", "lambda2"),
+                                                    ("fp64", "plam", "lambda1"), ("fp64", "pcal", "da")])
+def test_checkpoint_and_resume_continue_the_run_bit_for_bit(precision, variant, rule):
+    """plam_get_state after 10 iterations, then 10 more; a second handle loaded with that state
+    and the checkpointed X runs the same 10 iterations: the same X bit for bit (the state carries
+    the previous residual and column scales of the Barzilai-Borwein differences, the dual-ascent
+    multiplier, the step size and the counters).  A state from another shape is refused."""
+    from paper_1810_03930_gb300 import PlamError
+    w = workload_dense_trace(300, 6)
+    kw = dict(variant=variant, lambda_rule=rule, beta=1.5, tol=0.0, maxit=100, final_orth=0,
+              engine="graph")
+    s = gpu_solver(w, precision, **kw)
+    Xd = to_dev(w.X0, s)
+    for _ in range(10):
+        s.step(Xd, variant)
+    state = s.get_state()
+    Xck = Xd.clone()
+    for _ in range(10):
+        s.step(Xd, variant)
+    s.close()
+    s2 = gpu_solver(w, precision, **kw)
+    s2.set_state(state)
+    Xb = Xck.clone()
+    for _ in range(10):
+        st, info = s2.step(Xb, variant)
+    assert info.iters == 20
+    assert torch.equal(Xd, Xb)
+    s2.close()
+    other = gpu_solver(workload_dense_trace(300, 7), precision, **kw)
+    with pytest.raises(PlamError):
+        other.set_state(state)
+    other.close()
+
+
+def test_feasibility_blow_up_stops_the_run_as_diverged():
+    """PLAM with a penalty too small (beta = 0.01 s) on a Problem 2 instance lets X grow without
+    bound (the penalty study of Section 5.1); with feas_max = 10 the run stops as diverged as soon
+    as ||X^T X - I||_F passes 10, earlier than the non-finite test alone would, and X is the last
+    finite iterate."""
+    from paper_1810_03930_gb300 import Solver
+    from workloads import multiplier_study_problems
+    _, p2 = multiplier_study_problems()
+    A, lam, Gl, X0 = p2[0]
+    At = torch.as_tensor(A, device="cuda")
+    Gt = torch.as_tensor(Gl, device="cuda")
+
+    def energy(X):
+        return 0.5 * torch.sum(X * (At @ X)) + torch.sum(Gt * X)
+    s_ = float(np.max(np.abs(lam)))
+    out = {}
+    for fm in (10.0, 0.0):
+        s = Solver(200, 8, "callback", energy=energy, variant="plam", beta=0.01 * s_, tol=1e-6,
+                   maxit=3000, precision="fp64", final_orth=0, feas_max=fm)
+        Xd = to_dev(X0, s)
+        st, info = s.solve(Xd)
+        h = s.history()
+        out[fm] = (st, info.iters, h)
+        assert st == 3 and torch.isfinite(Xd).all(), (fm, st, info.as_dict())
+        s.close()
+    st, k10, h10 = out[10.0]
+    assert k10 < out[0.0][1]
+    assert h10[-1, 3] > 10.0 and np.all(h10[:-1, 3] <= 10.0)
