@@ -162,3 +162,47 @@ def test_moptqr_mistakes_are_caught(monkeypatch, wrong):
                             lambda V: np.asfortranarray(V / np.linalg.norm(V, axis=0)[None, :]))
         with pytest.raises(AssertionError):
             pins.test_moptqr_retraction_is_the_qr_factor_and_keeps_feasibility()
+
+
+@pytest.mark.parametrize("wrong", ["update_transposed_m", "update_sign", "update_k_uses_m",
+                                   "bb_reversed_s", "bb_s_from_r", "primal_times_eta",
+                                   "primal_row_norm", "chol_lower"])
+def test_single_step_definition_mistakes_are_caught(monkeypatch, wrong):
+    """A mistake in one of the single-step definitions the GPU kernels are checked against
+    (oracle.kernels) fails that definition's pin."""
+    import oracle.kernels as ok
+    if wrong == "update_transposed_m":
+        monkeypatch.setattr(ok, "update", lambda X, G, M, L0: (G - X @ M.T, G - X @ L0))
+        pin = pins.test_update_residual_lies_outside_the_range_of_x
+    elif wrong == "update_sign":
+        monkeypatch.setattr(ok, "update", lambda X, G, M, L0: (G + X @ M, G - X @ L0))
+        pin = pins.test_update_residual_lies_outside_the_range_of_x
+    elif wrong == "update_k_uses_m":
+        monkeypatch.setattr(ok, "update", lambda X, G, M, L0: (G - X @ M, G - X @ M))
+        pin = pins.test_update_residual_lies_outside_the_range_of_x
+    elif wrong == "bb_reversed_s":
+        def bad(X, R, Xp, Rp):
+            S, Y = Xp - X, R - Rp
+            return float(np.sum(S * S)), float(np.sum(S * Y)), float(np.sum(Y * Y))
+        monkeypatch.setattr(ok, "bb_dots", bad)
+        pin = pins.test_bb_dots_along_one_direction
+    elif wrong == "bb_s_from_r":
+        def bad(X, R, Xp, Rp):
+            S, Y = X - Xp, R - Rp
+            return float(np.sum(S * S)), float(np.sum(Y * Y)), float(np.sum(Y * Y))
+        monkeypatch.setattr(ok, "bb_dots", bad)
+        pin = pins.test_bb_dots_along_one_direction
+    elif wrong == "primal_times_eta":
+        monkeypatch.setattr(ok, "primal_update", lambda X, R, eta, variant="pcal": X - R * eta)
+        pin = pins.test_primal_update_lands_on_a_chosen_target
+    elif wrong == "primal_row_norm":
+        def bad(X, R, eta, variant="pcal"):
+            V = X - R / eta
+            return V if variant == "plam" else V / np.linalg.norm(V, axis=1)[:, None]
+        monkeypatch.setattr(ok, "primal_update", bad)
+        pin = pins.test_primal_update_lands_on_a_chosen_target
+    else:
+        monkeypatch.setattr(ok, "cholesky_qr_factor", lambda X: np.linalg.cholesky(X.T @ X))
+        pin = pins.test_cholesky_qr_factor_recovers_a_planted_triangle
+    with pytest.raises(AssertionError):
+        pin()

@@ -797,3 +797,78 @@ def test_penalty_study_conclusion_on_problems_1_to_4():
         rs = run(prob, "plam", "10s+1")
         assert all(r.converged for r in rs)
         assert np.median([r.iters for r in rs]) > np.median([r.iters for r in run(prob, "plam", "s+0.1")])
+
+
+# ---------------------------------------------------------------- single-step definitions
+
+
+def _orthonormal_block(n, k, seed):
+    """An n x k matrix with orthonormal columns (Householder QR of a seeded Gaussian)."""
+    Z = np.random.default_rng(seed).standard_normal((n, k))
+    return np.linalg.qr(Z)[0]
+
+
+def test_update_residual_lies_outside_the_range_of_x():
+    """R = G - X M with X orthonormal and M = X^T G (not symmetric) is G's component orthogonal
+    to range(X): X^T R = 0 and ||R||^2 = ||G||^2 - ||X^T G||^2 (Pythagoras).  K = G - X Psi(C)
+    leaves the skew part: X^T K = (C - C^T)/2.  A transposed M or a sign flip breaks either."""
+    X = _orthonormal_block(40, 5, 11)
+    G = np.random.default_rng(12).standard_normal((40, 5))
+    C = X.T @ G
+    assert np.linalg.norm(C - C.T) > 0.5
+    R, K = ok.update(X, G, C, 0.5 * (C + C.T))
+    assert np.abs(X.T @ R).max() <= 1e-13
+    assert math.isclose(np.sum(R * R), np.sum(G * G) - np.sum(C * C), rel_tol=1e-12)
+    np.testing.assert_allclose(X.T @ K, 0.5 * (C - C.T), atol=1e-13)
+
+
+def test_column_dots_of_orthogonal_pieces():
+    """X = Q diag(a), R = Q diag(b) + W diag(c) with [Q | W] orthonormal: the column dots are
+    a^2, a b and b^2 + c^2 exactly (up to rounding)."""
+    Q2 = _orthonormal_block(30, 8, 13)
+    Q, W = Q2[:, :4], Q2[:, 4:]
+    a = np.array([1.0, 2.0, 0.5, 3.0])
+    b = np.array([-1.0, 0.25, 2.0, 0.0])
+    c = np.array([0.5, 1.5, 0.0, 2.0])
+    xx, xr, rr = ok.column_dots(Q * a, Q * b + W * c)
+    np.testing.assert_allclose(xx, a * a, rtol=1e-13)
+    np.testing.assert_allclose(xr, a * b, rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(rr, b * b + c * c, rtol=1e-13)
+
+
+def test_bb_dots_along_one_direction():
+    """X = X_prev + t D and R = R_prev + c D: <S,S> = t^2 |D|^2, <S,Y> = t c |D|^2,
+    <Y,Y> = c^2 |D|^2 with S = X - X_prev, Y = R - R_prev (Section 5.1); a reversed difference
+    flips the sign of <S,Y>."""
+    rng = np.random.default_rng(14)
+    Xp, Rp = rng.standard_normal((25, 3)), rng.standard_normal((25, 3))
+    D = _orthonormal_block(25, 3, 15) * np.array([1.0, 2.0, 2.0])      # |D|_F^2 = 9
+    t, c = 0.75, -1.5
+    ss, sy, yy = ok.bb_dots(Xp + t * D, Rp + c * D, Xp, Rp)
+    assert math.isclose(ss, t * t * 9.0, rel_tol=1e-12)
+    assert math.isclose(sy, t * c * 9.0, rel_tol=1e-12)
+    assert math.isclose(yy, c * c * 9.0, rel_tol=1e-12)
+
+
+def test_primal_update_lands_on_a_chosen_target():
+    """PLAM: R = eta (X - Y) gives X - R/eta = Y (eq. PLAM-main).  PCAL: R = eta (X - Y diag(s))
+    with Y of unit columns and s > 0 gives Y after the column normalisation (Algorithm 3)."""
+    rng = np.random.default_rng(16)
+    X = rng.standard_normal((20, 4))
+    Y = rng.standard_normal((20, 4))
+    eta = 3.5
+    np.testing.assert_allclose(ok.primal_update(X, eta * (X - Y), eta, variant="plam"), Y,
+                               rtol=1e-13, atol=1e-14)
+    Yu = Y / np.linalg.norm(Y, axis=0)
+    s = np.array([0.5, 2.0, 7.0, 1.0])
+    np.testing.assert_allclose(ok.primal_update(X, eta * (X - Yu * s), eta, variant="pcal"), Yu,
+                               rtol=1e-12, atol=1e-13)
+
+
+def test_cholesky_qr_factor_recovers_a_planted_triangle():
+    """X = Q R0 with Q orthonormal and R0 upper triangular with a positive diagonal: R0 is the
+    unique Cholesky factor of X^T X, so the factor is R0 (Section 5.3's Cholesky-QR)."""
+    Q = _orthonormal_block(50, 6, 17)
+    R0 = np.triu(np.random.default_rng(18).standard_normal((6, 6)))
+    R0[np.diag_indices(6)] = np.abs(R0[np.diag_indices(6)]) + 0.5
+    np.testing.assert_allclose(ok.cholesky_qr_factor(Q @ R0), R0, rtol=1e-12, atol=1e-13)
