@@ -80,10 +80,14 @@ def parse_args():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--slab-planes", type=int, default=0,
+                    help="stencil3d_128 only: z-planes of the oracle's bounded sample (the "
+                         "cpu_baseline and the reference arm); 0 keeps 8")
     ap.add_argument("--kernel-iters", type=int, default=0,
                     help="only time the kernel groups of this many iterations (graph engine's "
                          "kernels launched one by one) and print them; a short, profiler-sized run")
-    ap.add_argument("--tensor-cores", choices=["auto", "off", "tf32", "3xtf32"], default="auto")
+    ap.add_argument("--tensor-cores", choices=["auto", "off", "tf32", "3xtf32", "tf32-single",
+                                               "3xtf32-single"], default="auto")
     ap.add_argument("--p", type=int, default=0,
                     help="block_hartree / tridiag_linear only: the width p (Section 5.4 sweeps "
                          "p = 500 ... 2500 at n = 10000); 0 keeps 1000")
@@ -119,6 +123,12 @@ def workload_config(args, **extra):
             raise SystemExit("--beta must be positive")
         wl["beta"] = args.beta
         wl["name"] += f"_beta{args.beta:g}"
+    if getattr(args, "slab_planes", 0):
+        if not wl.get("slab_planes"):
+            raise SystemExit("--slab-planes applies to the stencil3d_128 workload")
+        if not 1 <= args.slab_planes <= wl["m"]:
+            raise SystemExit(f"--slab-planes must lie in [1, {wl['m']}]")
+        wl["slab_planes"] = args.slab_planes
     return wl
 
 

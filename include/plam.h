@@ -115,6 +115,9 @@ typedef int (*plam_grad_fn)(void* ctx, const void* X, int64_t ldx, void* G, int6
  * DENSE, and the rows per SM must fit; otherwise PLAM_ERR_UNSUPPORTED).
  * AUTO: RESIDENT when it applies, else GRAPH. */
 enum { PLAM_ENGINE_AUTO = 0, PLAM_ENGINE_GRAPH = 1, PLAM_ENGINE_RESIDENT = 2 };
+/* Flag or-ed into plam_params_t.tensor_cores (with 1 or 2): the tensor-core Grams use one CTA
+   per 128-column tile for every p instead of CTA pairs for p >= 256. */
+enum { PLAM_TC_SINGLE_CTA = 8 };
 
 typedef struct {
   int variant;          /* PLAM_VARIANT_* used by plam_solve (plam_step/pcal_step choose their own;
@@ -136,8 +139,10 @@ typedef struct {
                            (hi*hi + hi*lo + lo*hi) once the relative KKT value is below refine_switch
                            or has not halved its best value for 100 iterations (TF32 rounding can
                            floor it above refine_switch); 2 always 3xTF32; -1 auto (= 1 when
-                           p >= 128).  Needs 16-byte aligned X and G with leading dimensions
-                           that are multiples of 4, otherwise the CUDA-core Grams run */
+                           p >= 128).  For p >= 256 the Grams run on CTA pairs (256 x 256
+                           tiles); 1 or 2 or-ed with PLAM_TC_SINGLE_CTA keeps one CTA per
+                           128-column tile.  Needs 16-byte aligned X and G with leading
+                           dimensions that are multiples of 4, otherwise the CUDA-core Grams run */
   double refine_switch; /* relative KKT value below which the tensor-core kernels are compensated
                            (0: neither rule switches, plain TF32 throughout) */
   double feas_max;      /* > 0: the run stops with PLAM_ERR_DIVERGED once ||X^T X - I||_F exceeds it
@@ -337,7 +342,8 @@ typedef struct {
 typedef struct plam_batch_s* plam_batch_t;
 
 /* prm: precision must be PLAM_PREC_FP32; variant, lambda_rule, beta, eta rule,
- * tol and maxit apply to every problem.  The problem array is copied; A, X and
+ * tol and maxit apply to every problem (the other fields, feas_max among them, are
+ * not used: a problem stops as diverged only on non-finite values).  The problem array is copied; A, X and
  * Q stay owned by the caller and must outlive the batch.  The workspace (three
  * n x p float buffers per problem) is allocated here. */
 plam_status_t plam_batch_create(plam_batch_t* b, const plam_batch_problem_t* probs, int count,

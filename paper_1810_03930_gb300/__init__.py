@@ -137,7 +137,9 @@ class Solver:
         prm.final_orth = int(final_orth)
         prm.graph_iters = int(graph_iters)
         prm.engine = {"auto": 0, "graph": 1, "resident": 2}[engine]
-        prm.tensor_cores = {"auto": -1, "off": 0, "on": 1, "tf32": 1, "3xtf32": 2}[tensor_cores]
+        prm.tensor_cores = {"auto": -1, "off": 0, "on": 1, "tf32": 1, "3xtf32": 2,
+                            "tf32-single": 1 | _lib.PLAM_TC_SINGLE_CTA,
+                            "3xtf32-single": 2 | _lib.PLAM_TC_SINGLE_CTA}[tensor_cores]
         prm.refine_switch = float(refine_switch)
         prm.orth_metrics = 1 if orth_metrics else 0
         prm.feas_max = float(feas_max)

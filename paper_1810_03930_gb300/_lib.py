@@ -27,6 +27,7 @@ STATUS_NAMES = {0: "PLAM_OK", 1: "PLAM_ERR_INVALID", 2: "PLAM_ERR_NOT_CONVERGED"
                 6: "PLAM_ERR_CUDA", 7: "PLAM_ERR_NOMEM", 8: "PLAM_ERR_UNSUPPORTED"}
 
 PLAM_VARIANT_PLAM, PLAM_VARIANT_PCAL, PLAM_VARIANT_MOPTQR = 0, 1, 2
+PLAM_TC_SINGLE_CTA = 8
 PLAM_LAMBDA1, PLAM_LAMBDA2, PLAM_LAMBDA_DA = 0, 1, 2
 PLAM_ETA_ABB, PLAM_ETA_BB1, PLAM_ETA_BB2, PLAM_ETA_CONST, PLAM_ETA_DIFF = 0, 1, 2, 3, 4
 PLAM_PREC_FP64, PLAM_PREC_FP32 = 0, 1

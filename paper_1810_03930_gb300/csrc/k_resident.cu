@@ -625,7 +625,8 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_solve_kernel(Resident
         nrec = min(nrec + 1, prm.hist_cap);
         int s = kRunning;
         double e2 = eta;
-        if (!isfinite(kkt)) s = kDiverged;
+        if (!isfinite(kkt) || !isfinite(feas) || (prm.feas_max > 0.0 && feas > prm.feas_max))
+          s = kDiverged;
         else if (K0 == 0.0 || kkt < prm.tol) s = kConverged;
         else if (k >= prm.maxit) s = kMaxit;
         else {

@@ -70,34 +70,6 @@ __device__ __forceinline__ void tc_tile(const TcGramArgs& a, int tile, int& mb, 
   }
 }
 
-// The tensor cores read an FP32 operand as TF32 by dropping its low 13 bits
-// (a biased, round-toward-zero conversion).  Converter warps rewrite each
-// staged tile first: hi = round-to-nearest TF32 (in place, unbiased), and in
-// compensated mode lo = TF32(x - hi) into a second buffer, so that
-// hi*hi + hi*lo + lo*hi carries about 2^-21 relative error per product.
-__device__ __forceinline__ void convert_tile(float* tile, float* lo, int nfloat4, int tid, int nthr,
-                                             bool split) {
-  float4* t4 = reinterpret_cast<float4*>(tile);
-  float4* l4 = reinterpret_cast<float4*>(lo);
-  for (int i = tid; i < nfloat4; i += nthr) {
-    const float4 x = t4[i];
-    float4 h;
-    h.x = __uint_as_float(tf32_rna(x.x));
-    h.y = __uint_as_float(tf32_rna(x.y));
-    h.z = __uint_as_float(tf32_rna(x.z));
-    h.w = __uint_as_float(tf32_rna(x.w));
-    t4[i] = h;
-    if (split) {
-      float4 l;
-      l.x = __uint_as_float(tf32_rna(x.x - h.x));
-      l.y = __uint_as_float(tf32_rna(x.y - h.y));
-      l.z = __uint_as_float(tf32_rna(x.z - h.z));
-      l.w = __uint_as_float(tf32_rna(x.w - h.w));
-      l4[i] = l;
-    }
-  }
-}
-
 constexpr int kTcConvThreads = 192;  // warps 2, 3 and 8-11
 constexpr int kTcThreads = 384;      // warps 0-11
 constexpr int kTcSegSplit = 1;       // stages per accumulation segment in compensated mode
@@ -357,7 +329,9 @@ static bool encode_map(CUtensorMap* m, const float* ptr, int64_t n, int p, int64
                         (uint32_t)cols, true);
 }
 
-void tc_gram_plan(int64_t n, int p, int with_g, TcGramPlan* pl) {
+void tc_gram_plan(int64_t n, int p, int with_g, TcGramPlan* pl, int allow_pair) {
+  if (allow_pair && tc_gram2_plan(n, p, with_g, pl)) return;
+  pl->pair = 0;
   pl->N = p >= 128 ? 128 : ((p + 15) / 16) * 16;
   pl->nmb = (p + kTcM - 1) / kTcM;
   pl->nnb = (p + pl->N - 1) / pl->N;
@@ -395,6 +369,8 @@ bool tc_gram_supported(const void* X, int64_t ldx, const void* G, int64_t ldg) {
 cudaError_t launch_tc_gram(int64_t n, int p, const float* X, int64_t ldx, const float* G,
                            int64_t ldg, const TcGramPlan& pl, float* part, int* err,
                            const DevState* st, double refine_switch, int force3, cudaStream_t s) {
+  if (pl.pair)
+    return launch_tc_gram2(n, p, X, ldx, G, ldg, pl, part, err, st, refine_switch, force3, s);
   CUtensorMap mA, mXB, mGB;
   if (!encode_map(&mA, X, n, p, ldx, kTcM) || !encode_map(&mXB, X, n, p, ldx, pl.N))
     return cudaErrorInvalidValue;
@@ -417,7 +393,8 @@ cudaError_t launch_tc_gram(int64_t n, int p, const float* X, int64_t ldx, const 
 
 cudaError_t preload_tc_kernels() {
   cudaFuncAttributes at;
-  return cudaFuncGetAttributes(&at, tc_gram_kernel);
+  cudaError_t e = cudaFuncGetAttributes(&at, tc_gram_kernel);
+  return e != cudaSuccess ? e : preload_tc_gram2();
 }
 
 }  // namespace plam

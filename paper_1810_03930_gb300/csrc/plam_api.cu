@@ -179,6 +179,11 @@ __global__ void dot_partial_kernel(int64_t n, int p, const T* __restrict__ X, in
   }
 }
 
+// tensor_cores = 2 (or 2 | PLAM_TC_SINGLE_CTA): compensated 3xTF32 from the first iteration.
+inline int tc_always3(const plam_params_t& prm) {
+  return prm.tensor_cores >= 0 && (prm.tensor_cores & 3) == 2;
+}
+
 plam_status_t validate_params(const plam_params_t* prm) {
   if (!prm) return PLAM_ERR_INVALID;
   if (prm->variant < PLAM_VARIANT_PLAM || prm->variant > PLAM_VARIANT_MOPTQR) return PLAM_ERR_INVALID;
@@ -189,7 +194,11 @@ plam_status_t validate_params(const plam_params_t* prm) {
   if (!(prm->tol >= 0.0) || prm->maxit < 0) return PLAM_ERR_INVALID;
   if (prm->final_orth < 0 || prm->final_orth > 2 || prm->graph_iters < 0) return PLAM_ERR_INVALID;
   if (prm->engine < PLAM_ENGINE_AUTO || prm->engine > PLAM_ENGINE_RESIDENT) return PLAM_ERR_INVALID;
-  if (prm->tensor_cores < -1 || prm->tensor_cores > 2) return PLAM_ERR_INVALID;
+  {
+    const int tc = prm->tensor_cores;
+    if (!(tc >= -1 && tc <= 2) && tc != (1 | PLAM_TC_SINGLE_CTA) && tc != (2 | PLAM_TC_SINGLE_CTA))
+      return PLAM_ERR_INVALID;
+  }
   if (!(prm->refine_switch >= 0.0)) return PLAM_ERR_INVALID;
   if (!(prm->feas_max >= 0.0)) return PLAM_ERR_INVALID;
   return PLAM_OK;
@@ -384,7 +393,7 @@ plam_status_t launch_iteration(plam_handle_s* h, T* X, int64_t ldx, int variant,
   int nch = h->nchunks;
   if (sizeof(T) == 4 && h->use_tc && tc_gram_supported(X, ldx, G, h->ldw)) {
     CK(launch_tc_gram(h->n, p, (const float*)X, ldx, (const float*)G, h->ldw, h->tc, (float*)h->part,
-                      h->tc_err, h->st, h->prm.refine_switch, h->prm.tensor_cores == 2, s));
+                      h->tc_err, h->st, h->prm.refine_switch, tc_always3(h->prm), s));
     nch = h->tc.nchunks;
   } else {
     CK((launch_gram_partial<T, T>(h->n, p, X, ldx, G, h->ldw, h->rows_per_chunk, h->nchunks,
@@ -412,7 +421,7 @@ plam_status_t launch_iteration(plam_handle_s* h, T* X, int64_t ldx, int variant,
                         (float*)h->R[1], h->ldw, (const float*)h->Mt, (const float*)h->L0t, h->tcu,
                         h->msplit, (const float*)h->coef, h->st, (float*)h->colpart,
                         (float*)h->totpart, h->tc_err, h->prm.refine_switch,
-                        h->prm.tensor_cores == 2, s));
+                        tc_always3(h->prm), s));
     nrt = h->tcu.nrt;
     nct = h->tcu.nct;
     k += 1;   // the TF32 split of M and Psi(C)
@@ -913,7 +922,8 @@ plam_status_t create_impl(plam_handle_t* out, int64_t n, int64_t p, const plam_o
   h->hist_cap = prm->maxit + 2;
   if (prm->precision == PLAM_PREC_FP32 &&
       (prm->tensor_cores >= 1 || (prm->tensor_cores == -1 && p >= 128))) {
-    tc_gram_plan(n, (int)p, 1, &h->tc);
+    tc_gram_plan(n, (int)p, 1, &h->tc, !(prm->tensor_cores >= 0 &&
+                                         (prm->tensor_cores & PLAM_TC_SINGLE_CTA)));
     tc_update_plan(n, (int)p, &h->tcu);
     h->use_tc = 1;
   }
@@ -1296,11 +1306,11 @@ plam_status_t plam_grams(plam_handle_t h, const void* X, int64_t ldx, const void
                                   h->stream));
   } else if (h->use_tc && tc_gram_supported(X, ldx, G, ldg)) {
     TcGramPlan pl = h->tc;
-    if (!G) tc_gram_plan(h->n, p, 0, &pl);
+    if (!G) tc_gram_plan(h->n, p, 0, &pl, pl.pair);
     if (pl.nchunks > h->tc.nchunks) pl = h->tc;   // the workspace is sized for the with-G plan
     CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream));
     CK(launch_tc_gram(h->n, p, (const float*)X, ldx, (const float*)G, ldg, pl, (float*)h->part,
-                      h->tc_err, nullptr, 0.0, h->prm.tensor_cores == 2, h->stream));
+                      h->tc_err, nullptr, 0.0, tc_always3(h->prm), h->stream));
     CK(launch_gram_reduce<float>(p, pl.nchunks, G != nullptr, (const float*)h->part, B, C,
                                  h->stream));
     CK(cudaMemcpyAsync(h->info_host, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));

@@ -244,12 +244,19 @@ cudaError_t preload_resident_kernels();
 // Tensor-core (tcgen05, kind::tf32) Grams: split-K partials in the layout of
 // launch_gram_partial (float), reduced by launch_gram_finalize / _reduce.
 struct TcGramPlan {
+  int pair;              // 1: CTA-pair kernel (256 x 256 tiles, p >= 256); 0: one CTA per tile
   int N, nmb, nnb, nbt, ntiles;
   int64_t rows_per_chunk;
   int nchunks;
   size_t smem;
 };
-void tc_gram_plan(int64_t n, int p, int with_g, TcGramPlan* pl);
+// allow_pair = 0 keeps one CTA per 128 x N tile for every p.
+void tc_gram_plan(int64_t n, int p, int with_g, TcGramPlan* pl, int allow_pair = 1);
+bool tc_gram2_plan(int64_t n, int p, int with_g, TcGramPlan* pl);
+cudaError_t launch_tc_gram2(int64_t n, int p, const float* X, int64_t ldx, const float* G,
+                            int64_t ldg, const TcGramPlan& pl, float* part, int* err,
+                            const DevState* st, double refine_switch, int force3, cudaStream_t s);
+cudaError_t preload_tc_gram2();
 bool tc_gram_supported(const void* X, int64_t ldx, const void* G, int64_t ldg);
 // st / refine_switch: compensated 3xTF32 once st->refine is latched (st may be
 // null); force3 = 1 always uses it.

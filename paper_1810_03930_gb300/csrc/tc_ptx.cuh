@@ -112,6 +112,34 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
   return r;
 }
 
+// The tensor cores read an FP32 operand as TF32 by dropping its low 13 bits
+// (a biased, round-toward-zero conversion).  Converter warps rewrite each
+// staged tile first: hi = round-to-nearest TF32 (in place, unbiased), and in
+// compensated mode lo = TF32(x - hi) into a second buffer, so that
+// hi*hi + hi*lo + lo*hi carries about 2^-21 relative error per product.
+__device__ __forceinline__ void convert_tile(float* tile, float* lo, int nfloat4, int tid, int nthr,
+                                             bool split) {
+  float4* t4 = reinterpret_cast<float4*>(tile);
+  float4* l4 = reinterpret_cast<float4*>(lo);
+  for (int i = tid; i < nfloat4; i += nthr) {
+    const float4 x = t4[i];
+    float4 h;
+    h.x = __uint_as_float(tf32_rna(x.x));
+    h.y = __uint_as_float(tf32_rna(x.y));
+    h.z = __uint_as_float(tf32_rna(x.z));
+    h.w = __uint_as_float(tf32_rna(x.w));
+    t4[i] = h;
+    if (split) {
+      float4 l;
+      l.x = __uint_as_float(tf32_rna(x.x - h.x));
+      l.y = __uint_as_float(tf32_rna(x.y - h.y));
+      l.z = __uint_as_float(tf32_rna(x.z - h.z));
+      l.w = __uint_as_float(tf32_rna(x.w - h.w));
+      l4[i] = l;
+    }
+  }
+}
+
 // 16 consecutive 32-bit columns of the calling thread's TMEM lane, without the wait.
 __device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
@@ -131,6 +159,113 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16
       "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
       "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
       "r"(r[15])
+      : "memory");
+}
+
+// 32 consecutive 32-bit columns of the calling thread's TMEM lane, without the wait.
+__device__ __forceinline__ void tmem_ld32_nw(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+}
+
+// ---- CTA pairs (a cluster of two CTAs whose tensor cores run one MMA together)
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// The shared::cluster address of the same shared-memory offset in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+
+// Arrive (release, cluster scope) on an mbarrier given by its shared::cluster address.
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t caddr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr)
+               : "memory");
+}
+
+// One poll (acquire, cluster scope) of a local mbarrier that the peer CTA arrives on.
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait (acquire, cluster scope) on a local mbarrier that the peer CTA arrives on;
+// false (and *err raised) when the limit expires or *err is already raised.
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, int* err) {
+  for (long long i = 0; i < kTcSpin; ++i) {
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    if ((i & 1023) == 1023 && *(volatile int*)err != 0) return false;
+  }
+  atomicExch(err, 1);
+  return false;
+}
+
+// The same wait taken by a whole warp, with one outcome for all its lanes.
+__device__ __forceinline__ bool mbar_wait_cluster_warp(uint64_t* bar, uint32_t parity, int* err) {
+  const bool ok = mbar_wait_cluster(bar, parity, err);
+  return __all_sync(0xffffffffu, ok) != 0;
+}
+
+// Every thread of both CTAs of the cluster (release / acquire), reached from divergent code
+// (the non-aligned forms of the CTA barrier and of the cluster barrier).
+__device__ __forceinline__ void cta_sync_divergent() {
+  asm volatile("barrier.sync 0;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_sync_divergent() {
+  asm volatile(
+      "barrier.cluster.arrive.release;\n\t"
+      "barrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// Every thread of both CTAs of the cluster (release / acquire).
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile(
+      "barrier.cluster.arrive.release.aligned;\n\t"
+      "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// One kind::tf32 MMA of the CTA pair, issued by the even CTA: D (M = 256: lanes of both CTAs'
+// TMEM) += A (128 rows from each CTA's shared memory) x B (N / 2 columns from each CTA's
+// shared memory); the descriptors address the same offsets in both CTAs.
+__device__ __forceinline__ void mma_tf32_pair(uint32_t tmem_d, uint64_t a, uint64_t b,
+                                              uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Arrive on the mbarrier at the same offset in every CTA of `mask` once the pair MMAs issued
+// so far have completed.
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(smem_addr(bar)),
+      "h"(mask)
       : "memory");
 }
 

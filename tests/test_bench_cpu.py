@@ -20,7 +20,7 @@ def _run(*args, timeout=300):
 
 
 def test_reference_arm_prints_the_contract_line():
-    r = _run("--impl", "reference", "--steps", "1", "--warmup", "3")
+    r = _run("--impl", "reference", "--steps", "1", "--warmup", "3", "--slab-planes", "1")
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
@@ -32,7 +32,7 @@ def test_reference_arm_prints_the_contract_line():
     assert d["steps"] == 1 and d["warmup"] == 3 and d["n_gpus"] == 1
     assert d["value"] > 0 and d["unit"] == "iters/s" and d["higher_is_better"] is True
     assert d["config"]["workload"] == "stencil3d_n2097152_p1024"
-    assert "z-planes" in d["cpu_baseline"]["sample"]
+    assert "the first 1 of the 128 z-planes (n = 16384" in d["cpu_baseline"]["sample"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     e2e = d["e2e"]

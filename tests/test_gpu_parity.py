@@ -191,8 +191,10 @@ def test_first_twenty_step_sizes_match_oracle_every_rule(variant, rule):
     obj = oo.TraceObjective(w.A)
     ref = op.solve(obj, w.X0, variant=variant, beta=1.0, eta_rule=rule, tol=0.0, maxit=20)
     eta_ref = np.array([h.eta for h in ref.history[:20]])
+    # feas_max = 0: no feasibility blow-up stop (a safeguard of this library that the paper and
+    # the oracle do not have), so a diverging rule runs until its values stop being finite
     s = gpu_solver(w, "fp64", variant=variant, beta=1.0, eta_rule=rule, tol=0.0, maxit=20,
-                   final_orth=0)
+                   final_orth=0, feas_max=0.0)
     Xd = to_dev(w.X0, s)
     st, info = s.solve(Xd)
     hist = s.history()
