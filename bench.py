@@ -278,7 +278,8 @@ def kernel_bytes(wl, w, nchunks_unused=None):
 
 KERNEL_SOURCES = {
     "resident": ["k_resident.cu"], "tc_update": ["k_tc_update.cu", "tc_ptx.cuh"],
-    "tc_gram": ["k_tc_gram.cu", "tc_ptx.cuh"], "stencil_grad": ["k_objective.cu"],
+    "tc_gram": ["k_tc_gram.cu", "tc_ptx.cuh"], "tc_gram2": ["k_tc_gram2.cu", "tc_ptx.cuh"],
+    "stencil_grad": ["k_objective.cu"],
     "hartree_grad": ["k_objective.cu"], "dense_grad": ["k_objective.cu"],
     "chain_grad": ["k_objective.cu"],
     "update": ["k_update.cu"], "primal_update": ["k_update.cu"], "step_size": ["k_update.cu"],
@@ -297,6 +298,12 @@ def csrc_hash(kernel=None):
     for fn in names:
         h.update(open(os.path.join(cdir, fn), "rb").read())
     return h.hexdigest()[:16]
+
+
+def tc_gram_name(p, tensor_cores="auto"):
+    """The tensor-core Gram kernel the library runs at width p: CTA pairs (256 x 256 tiles) from
+    p = 256 on, one CTA per 128-column tile below (or with a "-single" tensor_cores mode)."""
+    return "tc_gram2" if p >= 256 and not str(tensor_cores).endswith("-single") else "tc_gram"
 
 
 def recorded_traffic(kernel, workload):
@@ -562,7 +569,7 @@ def run_ours(args, rank, world, local):
     kernel_names = {"objective": "chain_grad" if wl.get("section54") else
                     {"hartree1d": "hartree_grad", "stencil3d": "stencil_grad"}.get(
                         wl["kind"], "dense_grad"),
-                    "gram_partial": "tc_gram" if tc else "gram_partial",
+                    "gram_partial": tc_gram_name(wl["p"]) if tc else "gram_partial",
                     "gram_finalize": "gram_finalize", "update": "tc_update" if tc else "update",
                     "step_size": "step_size", "primal_update": "primal_update"}
     roofline_graph = {"bound": "hbm", "kernel": kernel_names[dom], "achieved": achieved_g,
@@ -889,7 +896,8 @@ def run_stencil128(args, rank, world, local):
     kf = kernel_flops(wl)
     kb = kernel_bytes(wl, 4)
     dom = max(kms, key=lambda k: kms[k])
-    names = {"objective": "stencil_grad", "gram_partial": "tc_gram", "gram_finalize": "gram_finalize",
+    names = {"objective": "stencil_grad", "gram_partial": tc_gram_name(p),
+             "gram_finalize": "gram_finalize",
              "update": "tc_update", "step_size": "step_size", "primal_update": "primal_update"}
     if dom in kf:
         ach = kf[dom] / (kms[dom] * 1e-3) / 1e12

@@ -17,7 +17,8 @@
 //                          stage in both CTAs
 //   warps 2-7            : converters (both CTAs): round-to-nearest TF32 (and the
 //                          TF32 remainder when compensated), then one arrival per
-//                          warp on the even CTA's conversion barrier
+//                          warp on the even CTA's conversion barrier (CTA-scope
+//                          release: no cluster-wide fence per stage)
 //   warps 8-15           : accumulator warps (both CTAs): add each finished
 //                          accumulation segment of their TMEM lanes into a
 //                          running total held in registers (128 columns per
@@ -90,7 +91,7 @@ __device__ __forceinline__ void tc2_teardown(uint64_t* done, uint64_t* full, con
   tc_fence_before();
   cta_sync_divergent();
   if (threadIdx.x == 0) {
-    for (long long t2 = 0; t2 < kTcSpin && !mbar_try_wait_cluster(done, 0); ++t2) {
+    for (long long t2 = 0; t2 < kTcSpin && !mbar_try_wait(done, 0); ++t2) {
     }
     for (int kt = counters[1]; kt < counters[0]; ++kt) {
       const int s = kt % nst;
@@ -180,7 +181,7 @@ tc_gram2_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
         for (int kt = 0; kt < KT; ++kt) {
           const int s = kt % nst;
           const uint32_t ph = (uint32_t)(kt / nst) & 1u;
-          if (!mbar_wait_cluster(&empty[s], ph ^ 1u, a.err)) break;
+          if (!mbar_wait(&empty[s], ph ^ 1u, a.err)) break;
           unsigned char* sa = base + s * STAGE;
           mbar_arrive_expect_tx(&full[s], HALF);
           const int x = (int)(r0 + (int64_t)kt * kTc2K);
@@ -199,12 +200,12 @@ tc_gram2_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
           const bool last = (kt % segk) == segk - 1 || kt == KT - 1;
           const int r = seg & 1;
           if (first && seg >= 2) {   // both CTAs' accumulator warps have added region r
-            if (!mbar_wait_cluster(&acc_empty[r], (uint32_t)((seg >> 1) - 1) & 1u, a.err)) break;
+            if (!mbar_wait(&acc_empty[r], (uint32_t)((seg >> 1) - 1) & 1u, a.err)) break;
             tc_fence_after();
           }
           const int s = kt % nst;
           const uint32_t ph = (uint32_t)(kt / nst) & 1u;
-          if (!mbar_wait_cluster(&conv[s], ph, a.err)) break;
+          if (!mbar_wait(&conv[s], ph, a.err)) break;
           tc_fence_after();
           const uint32_t d = tmem + (uint32_t)(r * 256);
           const uint32_t sa = smem_addr(base + s * STAGE);
@@ -237,7 +238,7 @@ tc_gram2_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
                      (int)(HALF / 16), tid, 192, split);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive_cluster(conv_leader + (uint32_t)(s * 8));
+        if (lane == 0) mbar_arrive_remote(conv_leader + (uint32_t)(s * 8));
       }
     }
     tc2_teardown(done, full, counters, nst, tmem, warp);
@@ -254,7 +255,7 @@ tc_gram2_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
     bool ok = true;
     for (int seg = 0; seg < nseg; ++seg) {
       const int r = seg & 1;
-      if (!mbar_wait_cluster_warp(&acc_full[r], (uint32_t)(seg >> 1) & 1u, a.err)) {
+      if (!mbar_wait_warp(&acc_full[r], (uint32_t)(seg >> 1) & 1u, a.err)) {
         ok = false;
         break;
       }
@@ -271,7 +272,7 @@ tc_gram2_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive_cluster(acc_empty_leader + (uint32_t)(r * 8));
+      if (lane == 0) mbar_arrive_remote(acc_empty_leader + (uint32_t)(r * 8));
     }
     if (ok) {
       const int gi = mb * 256 + (int)rank * kTc2Cols + q * 32 + lane;

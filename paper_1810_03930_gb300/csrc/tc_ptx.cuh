@@ -192,40 +192,12 @@ __device__ __forceinline__ uint32_t mapa_shared(uint32_t saddr, uint32_t rank) {
   return r;
 }
 
-// Arrive (release, cluster scope) on an mbarrier given by its shared::cluster address.
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t caddr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr)
-               : "memory");
-}
-
-// One poll (acquire, cluster scope) of a local mbarrier that the peer CTA arrives on.
-__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait (acquire, cluster scope) on a local mbarrier that the peer CTA arrives on;
-// false (and *err raised) when the limit expires or *err is already raised.
-__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, int* err) {
-  for (long long i = 0; i < kTcSpin; ++i) {
-    if (mbar_try_wait_cluster(bar, parity)) return true;
-    if ((i & 1023) == 1023 && *(volatile int*)err != 0) return false;
-  }
-  atomicExch(err, 1);
-  return false;
-}
-
-// The same wait taken by a whole warp, with one outcome for all its lanes.
-__device__ __forceinline__ bool mbar_wait_cluster_warp(uint64_t* bar, uint32_t parity, int* err) {
-  const bool ok = mbar_wait_cluster(bar, parity, err);
-  return __all_sync(0xffffffffu, ok) != 0;
+// Arrive on an mbarrier given by its shared::cluster address (possibly in the peer CTA), with
+// the default CTA-scope release: what it publishes is this CTA's own shared memory, read after
+// the arrival by this CTA's own tensor core (through an MMA that the peer issues only once it
+// has seen the arrival), so no cluster-scope fence is needed on the per-stage path.
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t caddr) {
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
 }
 
 // Every thread of both CTAs of the cluster (release / acquire), reached from divergent code
