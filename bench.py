@@ -80,6 +80,9 @@ def parse_args():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--grams-only", type=int, nargs=2, metavar=("N", "P"), default=None,
+                    help="only time the tensor-core Grams X^T [X | G] of one FP32 handle on seeded "
+                         "N x P Gaussian matrices (with --tensor-cores); a profiler-sized run")
     ap.add_argument("--slab-planes", type=int, default=0,
                     help="stencil3d_128 only: z-planes of the oracle's bounded sample (the "
                          "cpu_baseline and the reference arm); 0 keeps 8")
@@ -1057,6 +1060,33 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def run_grams_only(args):
+    """Milliseconds of plam_grams (the tensor-core Gram kernel, its chunk reduction and the
+    handle's synchronisation) on seeded N x P Gaussian X and G, after three untimed calls."""
+    import torch
+    from paper_1810_03930_gb300 import Solver
+    n, p = args.grams_only
+    tc = args.tensor_cores if args.tensor_cores not in ("auto", "off") else "3xtf32"
+    s = Solver(n, p, "hartree1d", precision="fp32", tensor_cores=tc)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(STENCIL128_SEED)
+    X = torch.randn((p, n), generator=gen, device="cuda") / n ** 0.5
+    G = torch.randn((p, n), generator=gen, device="cuda")
+    for _ in range(3):
+        s.grams(X, G)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(5):
+        s.grams(X, G)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"grams_only": {"n": n, "p": p, "tensor_cores": tc,
+                                     "kernel": tc_gram_name(p, tc),
+                                     "ms_per_call": e0.elapsed_time(e1) / 5}}), flush=True)
+    s.close()
+
+
 def run_kernel_iters(args):
     """Per-kernel-group milliseconds of the first --kernel-iters iterations (mixed path); for the
     batched workload, one launch capped at --kernel-iters iterations per problem."""
@@ -1265,6 +1295,10 @@ def main():
     rank, world, local = dist_env()
     if args.workload == "batched" and args.impl == "ours" and args.kernel_iters == 0:
         run_batched(args, rank, world, local)
+        return
+    if args.grams_only:
+        if rank == 0:
+            run_grams_only(args)
         return
     if args.kernel_iters > 0:
         if rank == 0:

@@ -115,8 +115,8 @@ typedef int (*plam_grad_fn)(void* ctx, const void* X, int64_t ldx, void* G, int6
  * DENSE, and the rows per SM must fit; otherwise PLAM_ERR_UNSUPPORTED).
  * AUTO: RESIDENT when it applies, else GRAPH. */
 enum { PLAM_ENGINE_AUTO = 0, PLAM_ENGINE_GRAPH = 1, PLAM_ENGINE_RESIDENT = 2 };
-/* Flag or-ed into plam_params_t.tensor_cores (with 1 or 2): the tensor-core Grams use one CTA
-   per 128-column tile for every p instead of CTA pairs for p >= 256. */
+/* Flag or-ed into plam_params_t.tensor_cores (with 1 or 2): the tensor-core Grams and update
+   use one CTA per tile for every p instead of CTA pairs for p >= 256. */
 enum { PLAM_TC_SINGLE_CTA = 8 };
 
 typedef struct {
@@ -139,9 +139,9 @@ typedef struct {
                            (hi*hi + hi*lo + lo*hi) once the relative KKT value is below refine_switch
                            or has not halved its best value for 100 iterations (TF32 rounding can
                            floor it above refine_switch); 2 always 3xTF32; -1 auto (= 1 when
-                           p >= 128).  For p >= 256 the Grams run on CTA pairs (256 x 256
-                           tiles); 1 or 2 or-ed with PLAM_TC_SINGLE_CTA keeps one CTA per
-                           128-column tile.  Needs 16-byte aligned X and G with leading
+                           p >= 128).  For p >= 256 the Grams (256 x 256 tiles) and the update
+                           (256-row tiles) run on CTA pairs; 1 or 2 or-ed with PLAM_TC_SINGLE_CTA
+                           keeps one CTA per tile.  Needs 16-byte aligned X and G with leading
                            dimensions that are multiples of 4, otherwise the CUDA-core Grams run */
   double refine_switch; /* relative KKT value below which the tensor-core kernels are compensated
                            (0: neither rule switches, plain TF32 throughout) */

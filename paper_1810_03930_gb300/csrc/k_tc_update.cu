@@ -54,7 +54,7 @@ constexpr int kUpM = 128;          // rows of X per tile (TMEM lanes)
 constexpr int kUpK = 32;           // inner indices per stage
 constexpr int kUpThreads = 448;    // 14 warps
 constexpr int kUpConvThreads = 128;
-constexpr int kUpMaxStages = 4;
+constexpr int kUpMaxStages = 6;
 constexpr int kUpChunk = 16;       // epilogue columns per ring slot
 constexpr int kUpAux = 256;        // barriers, TMEM address, flags
 
@@ -129,6 +129,14 @@ __device__ __forceinline__ int conv_tid(int warp, int lane) {
   return (warp < 8 ? warp - 2 : warp - 6) * 32 + lane;
 }
 
+// kPair = false: one CTA per 128-row x N-column tile.  kPair = true: a cluster of two CTAs
+// per 256-row x N-column tile (tcgen05 cta_group::2, M = 256): each CTA stages and transposes
+// its own 128 rows of X and N / 2 columns of M, E (and M lo), the even CTA issues the pair's
+// MMAs and its commits release stages and accumulators in both CTAs, and each CTA's epilogue
+// finishes its own 128 rows exactly as a single CTA does.  Per multiply-add this halves the
+// bytes of the M / E operands each SM loads and reads, and a quarter of all its shared-memory
+// traffic per stage.
+template <bool kPair>
 __global__ void __launch_bounds__(kUpThreads, 1)
 tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapMh,
                  const __grid_constant__ CUtensorMap mapMl, const __grid_constant__ CUtensorMap mapEh,
@@ -141,8 +149,9 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   unsigned char* base = smem_raw + pad;
   const bool split = a.force3 || (a.refine_switch > 0.0 && a.st->refine);
   const int N = a.N;
-  const uint32_t A = kUpM * kUpK * 4, BT = (uint32_t)N * kUpK * 4;
-  const uint32_t STAGE = up_stage_bytes(N, split);
+  const int NB = kPair ? N / 2 : N;                  // columns of M / E staged by this CTA
+  const uint32_t A = kUpM * kUpK * 4, BT = (uint32_t)NB * kUpK * 4;
+  const uint32_t STAGE = up_stage_bytes(NB, split);
   int nst = (int)(a.pipe_bytes / STAGE);
   if (nst > kUpMaxStages) nst = kUpMaxStages;
   const uint32_t oAh = 0, oAl = A, oRaw = split ? A : 0;
@@ -166,19 +175,26 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
                                                         //  ring slot 0, into slot 1]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int KT = (a.p + kUpK - 1) / kUpK;
-  const int ntl = (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  // tiles of this CTA (of its pair): rows rtile * kRows .. + kRows - 1, columns ctile * N ..;
+  // this CTA's own rows start at rtile * kRows + rank * kUpM
+  constexpr int kRows = kPair ? 2 * kUpM : kUpM;
+  const uint32_t rank = kPair ? cluster_ctarank() : 0u;
+  const int unit = kPair ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int nunits = kPair ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+  const int ntl = (a.ntiles - unit + nunits - 1) / nunits;
+  const int nrt128 = (int)((a.n + kUpM - 1) / kUpM);   // 128-row tiles of the partial dots
   const uint32_t ncols = tmem_cols_for(4 * N);
   const int kst = a.st->k;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kUpMaxStages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&conv[s], kUpConvThreads);
+      mbar_init(&conv[s], kPair ? 8 : 4);   // one arrival per converter warp (of both CTAs)
       mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 256);
+      mbar_init(&tempty[b], kPair ? 16 : 8);   // one arrival per epilogue warp (of both CTAs)
       mbar_init(&epfull[b], 1);
     }
     mbar_init(done, 1);
@@ -186,14 +202,26 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 2) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_addr(tmem_slot)),
-                 "r"(ncols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if constexpr (kPair) {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_addr(tmem_slot)),
+                   "r"(ncols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_addr(tmem_slot)),
+                   "r"(ncols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
   tc_fence_before();
-  __syncthreads();
+  if constexpr (kPair) {
+    cluster_sync_all();   // both CTAs' barriers initialised and TMEM allocated
+  } else {
+    __syncthreads();
+  }
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -203,8 +231,9 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       int gs = 0;
       bool ok = true;
       for (int lt = 0; lt < ntl && ok; ++lt) {
-        const int tile = (int)blockIdx.x + lt * (int)gridDim.x;
-        const int r0 = (tile / a.nct) * kUpM, c0 = (tile % a.nct) * N;
+        const int tile = unit + lt * nunits;
+        const int r0 = (tile / a.nct) * kRows + (int)rank * kUpM;
+        const int c0 = (tile % a.nct) * N + (int)rank * NB;
         for (int kt = 0; kt < KT; ++kt, ++gs) {
           const int s = gs % nst;
           if (!mbar_wait(&empty[s], ((uint32_t)(gs / nst) & 1u) ^ 1u, a.err)) { ok = false; break; }
@@ -220,9 +249,9 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      // ---- MMA issuer
-      const uint32_t idesc = idesc_tf32(kUpM, N);
+    if (lane == 0 && rank == 0) {
+      // ---- MMA issuer (the even CTA of a pair)
+      const uint32_t idesc = idesc_tf32(kPair ? 2 * kUpM : kUpM, N);
       int gs = 0;
       bool ok = true;
       for (int lt = 0; lt < ntl && ok; ++lt) {
@@ -243,18 +272,32 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
 #pragma unroll
           for (int k = 0; k < kUpK / 8; ++k) {
             const uint32_t acc = (kt | k) != 0 ? 1u : 0u;
-            mma_tf32(d1, ah + 2 * k, mh + 2 * k, idesc, acc);
-            mma_tf32(d2, ah + 2 * k, eh + 2 * k, idesc, acc);
-            if (split) {
-              mma_tf32(d1, ah + 2 * k, ml + 2 * k, idesc, 1);
-              mma_tf32(d1, al + 2 * k, mh + 2 * k, idesc, 1);
+            if constexpr (kPair) {
+              mma_tf32_pair(d1, ah + 2 * k, mh + 2 * k, idesc, acc);
+              mma_tf32_pair(d2, ah + 2 * k, eh + 2 * k, idesc, acc);
+              if (split) {
+                mma_tf32_pair(d1, ah + 2 * k, ml + 2 * k, idesc, 1);
+                mma_tf32_pair(d1, al + 2 * k, mh + 2 * k, idesc, 1);
+              }
+            } else {
+              mma_tf32(d1, ah + 2 * k, mh + 2 * k, idesc, acc);
+              mma_tf32(d2, ah + 2 * k, eh + 2 * k, idesc, acc);
+              if (split) {
+                mma_tf32(d1, ah + 2 * k, ml + 2 * k, idesc, 1);
+                mma_tf32(d1, al + 2 * k, mh + 2 * k, idesc, 1);
+              }
             }
           }
-          mma_commit(&empty[s]);
+          if constexpr (kPair) mma_commit_pair(&empty[s], (uint16_t)3);
+          else mma_commit(&empty[s]);
         }
-        if (ok) mma_commit(&tfull[b]);
+        if (ok) {
+          if constexpr (kPair) mma_commit_pair(&tfull[b], (uint16_t)3);
+          else mma_commit(&tfull[b]);
+        }
       }
-      mma_commit(done);
+      if constexpr (kPair) mma_commit_pair(done, (uint16_t)3);
+      else mma_commit(done);
     }
   } else if (warp == 2 || warp == 3 || warp == 8 || warp == 9) {
     // ---- converters: landed X slice [32 columns][128 rows] -> K-major SW128 rows
@@ -302,8 +345,12 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
           }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&conv[s]))
-                     : "memory");
+        __syncwarp();
+        if (lane == 0) {
+          if constexpr (kPair) mbar_arrive_remote(mapa_shared(smem_addr(&conv[s]), 0));
+          else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&conv[s]))
+                            : "memory");
+        }
       }
       if (abort) break;
     }
@@ -330,8 +377,9 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     auto issue_seq = [&](int g) {
       const int lt2 = g / nch, jj = g - lt2 * nch;
       if (lt2 >= ntl) return;
-      const int tile2 = (int)blockIdx.x + lt2 * (int)gridDim.x;
-      const int r0c = (tile2 / a.nct) * kUpM, cc = (tile2 % a.nct) * N + jj * kUpChunk;
+      const int tile2 = unit + lt2 * nunits;
+      const int r0c = (tile2 / a.nct) * kRows + (int)rank * kUpM;
+      const int cc = (tile2 % a.nct) * N + jj * kUpChunk;
       unsigned char* sl = ring + (g & 1) * 3 * EPC;
       mbar_arrive_expect_tx(&epfull[g & 1], ep_bytes);
       tma_load_2d(sl, &mapXe, &epfull[g & 1], r0c, cc);
@@ -342,8 +390,9 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     if (leader) issue_seq(e);
     bool aborted = false;
     for (int lt = 0; lt < ntl; ++lt) {
-      const int tile = (int)blockIdx.x + lt * (int)gridDim.x;
-      const int rb = tile / a.nct, ctl = tile % a.nct;
+      const int tile = unit + lt * nunits;
+      const int rb = (tile / a.nct) * (kRows / kUpM) + (int)rank;   // this CTA's 128-row tile
+      const int ctl = tile % a.nct;
       const int r0 = rb * kUpM, c0 = ctl * N;
       const int b = lt & 1;
       if (!mbar_wait_warp(&tfull[b], (uint32_t)(lt >> 1) & 1u, a.err) && lane == 0) flags[0] = 1;
@@ -417,8 +466,12 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       }
       // the accumulators of buffer b are read: the MMA may reuse them
       tc_fence_before();
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&tempty[b]))
-                   : "memory");
+      __syncwarp();
+      if (lane == 0) {
+        if constexpr (kPair) mbar_arrive_remote(mapa_shared(smem_addr(&tempty[b]), 0));
+        else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&tempty[b]))
+                          : "memory");
+      }
       float tot[kTotDots] = {ss, sy, yy, kk, gg, xg};
 #pragma unroll
       for (int d = 0; d < kTotDots; ++d) {
@@ -431,7 +484,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       }
       named_bar(4, 256);
       const bool stop_all = *(volatile int*)&flags[0] != 0;
-      if (!stop_all) {
+      if (!stop_all && rb < nrt128) {
         for (int jj = ea; jj < N; jj += 256) {
           const int col = c0 + jj;
           if (col < a.p) {
@@ -456,7 +509,8 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   tc_fence_before();
   __syncthreads();
   if (threadIdx.x == 0) {
-    // every issued MMA has completed and every issued copy has landed (bounded waits)
+    // every issued MMA has completed and every issued copy has landed (bounded waits; in a
+    // pair the even CTA's final commit arrives in both CTAs)
     for (long long i = 0; i < kTcSpin && !mbar_try_wait(done, 0); ++i) {
     }
     const int gs_issued = flags[2];
@@ -473,10 +527,21 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     }
   }
   __syncthreads();
+  if constexpr (kPair) {
+    tc_fence_before();
+    cluster_sync_all();   // the peer no longer reads this CTA's shared memory or arrives here
+  }
   if (warp == 2) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols)
-                 : "memory");
+    if constexpr (kPair) {
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"(ncols)
+                   : "memory");
+    } else {
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"(ncols)
+                   : "memory");
+    }
   }
 }
 
@@ -503,24 +568,56 @@ __global__ void tc_split_m_kernel(int p, const float* __restrict__ Mt, const flo
 
 // ---------------------------------------------------------------- host side
 
-void tc_update_plan(int64_t n, int p, TcUpdatePlan* pl) {
+void tc_update_plan(int64_t n, int p, TcUpdatePlan* pl, int allow_pair) {
   pl->N = p >= 128 ? 128 : ((p + 15) / 16) * 16;
   pl->nct = (p + pl->N - 1) / pl->N;
   pl->nrt = (int)((n + kUpM - 1) / kUpM);
   pl->ldm = ((p + 31) / 32) * 32;
+  pl->pair = 0;
+  pl->ncl = 0;
   // stage buffers: what is left after the epilogue ring and the reduction scratch,
-  // at most four stages of either mode
-  const size_t fixed = 1024 + up_ring_bytes() + up_red_bytes(pl->N) + kUpAux;
-  const size_t avail = 232448 - fixed;
-  size_t pipe = 0;
-  for (int split = 0; split < 2; ++split) {
-    const size_t st = up_stage_bytes(pl->N, split != 0);
-    size_t k = avail / st;
-    if (k > (size_t)kUpMaxStages) k = kUpMaxStages;
-    if (k * st > pipe) pipe = k * st;
+  // at most kUpMaxStages stages of either mode (a pair stages N / 2 columns of M and E)
+  auto size_pipe = [&](int nb) {
+    const size_t fixed = 1024 + up_ring_bytes() + up_red_bytes(pl->N) + kUpAux;
+    const size_t avail = 232448 - fixed;
+    size_t pipe = 0;
+    for (int split = 0; split < 2; ++split) {
+      const size_t st = up_stage_bytes(nb, split != 0);
+      size_t k = avail / st;
+      if (k > (size_t)kUpMaxStages) k = kUpMaxStages;
+      if (k * st > pipe) pipe = k * st;
+    }
+    pl->pipe_bytes = (uint32_t)pipe;
+    pl->smem = fixed + pipe;
+  };
+  if (allow_pair && p >= 256) {
+    size_pipe(pl->N / 2);
+    int ncl = 0;
+    cudaFuncAttributes at;
+    if (cudaFuncGetAttributes(&at, tc_update_kernel<true>) == cudaSuccess &&
+        cudaFuncSetAttribute(tc_update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)pl->smem) == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 2;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(2, 1, 1);
+      cfg.blockDim = dim3(kUpThreads, 1, 1);
+      cfg.dynamicSmemBytes = pl->smem;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      if (cudaOccupancyMaxActiveClusters(&ncl, tc_update_kernel<true>, &cfg) != cudaSuccess) ncl = 0;
+    }
+    cudaGetLastError();
+    if (ncl >= 1) {
+      pl->pair = 1;
+      pl->ncl = ncl;
+      return;
+    }
   }
-  pl->pipe_bytes = (uint32_t)pipe;
-  pl->smem = fixed + pipe;
+  size_pipe(pl->N);
 }
 
 bool tc_update_supported(const void* X, int64_t ldx) {
@@ -541,34 +638,60 @@ cudaError_t launch_tc_update(int64_t n, int p, const float* X, int64_t ldx, cons
     if (e != cudaSuccess) return e;
   }
   const size_t plane = (size_t)pl.ldm * p;
+  const uint32_t nb = pl.pair ? (uint32_t)pl.N / 2 : (uint32_t)pl.N;   // M / E columns per CTA
   CUtensorMap mX, mMh, mMl, mEh, mXe, mGe, mR0e, mR1e;
   if (!encode_map_f32(&mX, X, (uint64_t)n, (uint64_t)p, (uint64_t)ldx, kUpM, kUpK, false) ||
-      !encode_map_f32(&mMh, msplit, p, p, pl.ldm, kUpK, pl.N, true) ||
-      !encode_map_f32(&mMl, msplit + plane, p, p, pl.ldm, kUpK, pl.N, true) ||
-      !encode_map_f32(&mEh, msplit + 2 * plane, p, p, pl.ldm, kUpK, pl.N, true) ||
+      !encode_map_f32(&mMh, msplit, p, p, pl.ldm, kUpK, nb, true) ||
+      !encode_map_f32(&mMl, msplit + plane, p, p, pl.ldm, kUpK, nb, true) ||
+      !encode_map_f32(&mEh, msplit + 2 * plane, p, p, pl.ldm, kUpK, nb, true) ||
       !encode_map_f32(&mXe, X, (uint64_t)n, (uint64_t)p, (uint64_t)ldx, kUpM, kUpChunk, false) ||
       !encode_map_f32(&mGe, G, (uint64_t)n, (uint64_t)p, (uint64_t)ldg, kUpM, kUpChunk, false) ||
       !encode_map_f32(&mR0e, R0, (uint64_t)n, (uint64_t)p, (uint64_t)ldr, kUpM, kUpChunk, false) ||
       !encode_map_f32(&mR1e, R1, (uint64_t)n, (uint64_t)p, (uint64_t)ldr, kUpM, kUpChunk, false))
     return cudaErrorInvalidValue;
   TcUpdateArgs a;
-  a.n = n; a.p = p; a.N = pl.N; a.nct = pl.nct; a.ntiles = pl.nrt * pl.nct;
+  a.n = n; a.p = p; a.N = pl.N; a.nct = pl.nct;
+  a.ntiles = (pl.pair ? (pl.nrt + 1) / 2 : pl.nrt) * pl.nct;
   a.R0 = R0; a.R1 = R1; a.ldr = ldr;
   a.coef = coef; a.st = st; a.colpart = colpart; a.totpart = totpart; a.err = err;
   a.pipe_bytes = pl.pipe_bytes; a.refine_switch = refine_switch; a.force3 = force3;
   a.mdiag = msplit + 3 * plane;
-  cudaError_t e = cudaFuncSetAttribute(tc_update_kernel,
+  if (pl.pair) {
+    cudaError_t e = cudaFuncSetAttribute(tc_update_kernel<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+    if (e != cudaSuccess) return e;
+    const int units = pl.ncl < a.ntiles ? pl.ncl : a.ntiles;   // persistent: one pass of clusters
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(2 * units), 1, 1);
+    cfg.blockDim = dim3(kUpThreads, 1, 1);
+    cfg.dynamicSmemBytes = pl.smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, tc_update_kernel<true>, mX, mMh, mMl, mEh, mXe, mGe, mR0e, mR1e, a);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
+  cudaError_t e = cudaFuncSetAttribute(tc_update_kernel<false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
   if (e != cudaSuccess) return e;
   int grid = device_sm_count();
   if (grid > a.ntiles) grid = a.ntiles;
-  tc_update_kernel<<<grid, kUpThreads, pl.smem, s>>>(mX, mMh, mMl, mEh, mXe, mGe, mR0e, mR1e, a);
+  tc_update_kernel<false><<<grid, kUpThreads, pl.smem, s>>>(mX, mMh, mMl, mEh, mXe, mGe, mR0e,
+                                                            mR1e, a);
   return cudaGetLastError();
 }
 
 cudaError_t preload_tc_update_kernels() {
   cudaFuncAttributes at;
-  cudaError_t e = cudaFuncGetAttributes(&at, tc_update_kernel);
+  cudaError_t e = cudaFuncGetAttributes(&at, tc_update_kernel<false>);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncGetAttributes(&at, tc_update_kernel<true>);
   if (e != cudaSuccess) return e;
   return cudaFuncGetAttributes(&at, tc_split_m_kernel);
 }

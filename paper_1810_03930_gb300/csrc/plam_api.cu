@@ -924,7 +924,8 @@ plam_status_t create_impl(plam_handle_t* out, int64_t n, int64_t p, const plam_o
       (prm->tensor_cores >= 1 || (prm->tensor_cores == -1 && p >= 128))) {
     tc_gram_plan(n, (int)p, 1, &h->tc, !(prm->tensor_cores >= 0 &&
                                          (prm->tensor_cores & PLAM_TC_SINGLE_CTA)));
-    tc_update_plan(n, (int)p, &h->tcu);
+    tc_update_plan(n, (int)p, &h->tcu, !(prm->tensor_cores >= 0 &&
+                                         (prm->tensor_cores & PLAM_TC_SINGLE_CTA)));
     h->use_tc = 1;
   }
   const int part_chunks = h->use_tc && h->tc.nchunks > h->nchunks ? h->tc.nchunks : h->nchunks;

@@ -272,11 +272,14 @@ int device_sm_count();   // SMs of the current device
 // nrt x nct x 6 partials, nrt = ceil(n / 128), nct = ceil(p / N)).
 // msplit: 4 x ldm x p floats of scratch for the TF32 parts of M and Psi(C).
 struct TcUpdatePlan {
-  int N, nct, nrt, ldm;
+  int pair;              // 1: CTA pairs on 256-row tiles (p >= 256); 0: one CTA per 128-row tile
+  int N, nct, nrt, ldm;  // nrt: 128-row tiles of the partial dots (either kernel)
+  int ncl;               // pair: clusters of two that fit at once
   uint32_t pipe_bytes;
   size_t smem;
 };
-void tc_update_plan(int64_t n, int p, TcUpdatePlan* pl);
+// allow_pair = 0 keeps one CTA per 128-row tile for every p.
+void tc_update_plan(int64_t n, int p, TcUpdatePlan* pl, int allow_pair = 1);
 bool tc_update_supported(const void* X, int64_t ldx);
 cudaError_t launch_tc_update(int64_t n, int p, const float* X, int64_t ldx, const float* G,
                              int64_t ldg, float* R0, float* R1, int64_t ldr, const float* Mt,

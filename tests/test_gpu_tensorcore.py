@@ -149,16 +149,19 @@ def _dense_case(n, p, seed):
     return w, X0
 
 
-@pytest.mark.parametrize("n,p", [(3001, 130), (2048, 256), (1000, 40), (777, 1)])
+@pytest.mark.parametrize("n,p", [(3001, 130), (2048, 256), (2900, 300), (1000, 40), (777, 1)])
 @pytest.mark.parametrize("variant", ["plam", "pcal"])
-@pytest.mark.parametrize("tc,tol", [("3xtf32", 2e-5), ("tf32", 4e-3)])
+@pytest.mark.parametrize("tc,tol", [("3xtf32", 2e-5), ("tf32", 4e-3), ("3xtf32-single", 2e-5)])
 def test_tensor_core_update_three_iterations(n, p, variant, tc, tol):
     """Three FP32 iterations with the tcgen05 update GEMM R = G - X M (eq. S1) and its epilogue
     dots (column norms for PCAL's closed form, the Barzilai-Borwein sums of Section 5.1, the KKT
     residual of Section 3.3) against the FP64 oracle: the steps X^3 - X^0 and the step sizes
     eta^0..2 agree to the accuracy of the operand rounding (TF32: 2^-11; compensated 3xTF32: FP32
-    level), the relative KKT values to TF32 level (its correction term X E is plain TF32).  Row blocks of 128 with a ragged tail, column tiles of 128
-    with a ragged tail (p = 130), a single column (p = 1)."""
+    level), the relative KKT values to TF32 level (its correction term X E is plain TF32).  Row
+    blocks of 128 with a ragged tail, column tiles of 128 with a ragged tail (p = 130), a single
+    column (p = 1); from p = 256 on CTA pairs take 256-row tiles (n = 2900: 23 row blocks, so
+    the second CTA of the last pair lies past n; p = 300: the second CTA's half of the last
+    column tile lies past p), and "-single" keeps one CTA per tile."""
     from oracle import objectives as oo
     from oracle import plam as op
     from tests.gpu_helpers import ITER_FACTOR, assert_entrywise, gpu_solver, to_host
@@ -198,7 +201,7 @@ def test_tensor_core_update_replaces_the_cuda_core_update():
 
 
 @pytest.mark.parametrize("m,p", [(30, 256), (34, 130)])
-@pytest.mark.parametrize("tc,tol", [("3xtf32", 2e-5), ("tf32", 4e-3)])
+@pytest.mark.parametrize("tc,tol", [("3xtf32", 2e-5), ("tf32", 4e-3), ("tf32-single", 4e-3)])
 def test_tensor_core_update_persistent_tiles(m, p, tc, tol):
     """The persistent update kernel walks several 128 x 128 tiles per CTA (27000 or 39304 rows:
     hundreds of tiles on 152 SMs), alternating its two tensor-memory accumulator buffers and the
