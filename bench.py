@@ -52,9 +52,12 @@ WORKLOADS = {
     # (tests/golden), the FP64 path over its first iterations (extrapolated) and the oracle on
     # the grid's first 8 z-planes (cpu_baseline).  The start is the Q factor of a seeded
     # Gaussian generated on the device (a host FP64 start would take 17 GB).
+    # the separable companion (exact optimum) runs PCAL with the Lambda1 multiplier: with
+    # eq. (lambda2) one large ABB step collapses its columns onto one direction, which PCAL's
+    # column normalisation cannot undo (see the tests of the 128^3 solve)
     "stencil3d_128": dict(kind="stencil3d", m=128, n=2097152, p=1024, beta=1.0, tol=1e-5,
                           tol_separable=1e-6, maxit=3000, name="stencil3d_n2097152_p1024",
-                          fp64_iters=1, slab_planes=8),
+                          fp64_iters=1, slab_planes=8, separable=dict(lambda_rule="lambda1")),
     # Section 5.4's parallel workloads at n = 10000, p = 1000, PCAL with beta = 1 (the paper's
     # default): Problem 1 with L = Diag(L_1, ..., L_2000) of 5 x 5 Dirichlet blocks (alpha = 1),
     # and Problem 2 with the tridiagonal A and a random linear term; FP32 storage with
@@ -343,7 +346,8 @@ def golden_fstar(name):
 
 def make_solver(wl, precision, torch, engine="auto", final_orth=1, maxit=3000, tensor_cores=None):
     from paper_1810_03930_gb300 import Solver
-    kw = dict(variant=wl.get("variant", "pcal"), lambda_rule="lambda2", beta=wl["beta"],
+    kw = dict(variant=wl.get("variant", "pcal"), lambda_rule=wl.get("lambda_rule", "lambda2"),
+              beta=wl["beta"],
               tol=wl["tol"], maxit=maxit,
               precision=precision, final_orth=final_orth, graph_iters=16, engine=engine,
               tensor_cores=tensor_cores or wl.get("tensor_cores", "auto"), orth_metrics=False)
@@ -697,6 +701,40 @@ def timed_solve_e2e(sol, Xh, Xw, Q, Qh, torch):
     return ev[1].elapsed_time(ev[2]) / 1e3, ev[0].elapsed_time(ev[3]) / 1e3, st, info
 
 
+def companion_parity(sol_p, wls, Xh, Xw, Q, Vs64, m, torch):
+    """One solve of the separable companion and its objective against the exact optimum.  A
+    solve whose final Cholesky-QR fails (the iterate lost rank in a transient blow-up of the
+    ABB steps, which PCAL cannot undo) is reported with its history instead of ending the run."""
+    from paper_1810_03930_gb300._lib import PlamError
+    g = golden_fstar("stencil3d_separable_n2097152_p1024")
+    fstar = g["f_star"] if g else None
+    out = {"tol_kkt_rel": wls["tol"], "variant": wls.get("variant", "pcal"), "beta": wls["beta"],
+           "lambda_rule": wls.get("lambda_rule", "lambda2"),
+           "potential": "V = v_x(x) + v_y(y) + v_z(z), v_k iid U[0, 1/3] (exact optimum from "
+                        "three tridiagonal eigensolves)"}
+    try:
+        t_sep, _, st_p, info_p = timed_solve_e2e(sol_p, Xh, Xw, Q, None, torch)
+    except PlamError as e:
+        hist = sol_p.history()
+        out.update({"status": "failed", "error": str(e), "iters": int(hist[-1][0]),
+                    "kkt_rel_last": float(hist[-1][2]), "feas_last": float(hist[-1][3]),
+                    "feas_max": float(max(h[3] for h in hist))})
+        return out
+    out.update(result_parity(Q, Vs64, m, info_p, torch, fstar))
+    out.update({"time_s": t_sep, "status": {0: "converged", 2: "maxit"}.get(st_p, str(st_p))})
+    if fstar is not None:
+        # the first iterate whose objective is within 1e-6 of f* (the device's f of the iterate
+        # X^k, which PCAL keeps at unit column norms: the orthonormalisation moves f only at
+        # second order), and the time to it at the solve's mean rate
+        hist = sol_p.history()
+        ok = [int(h[0]) for h in hist if abs(h[1] - fstar) <= 1e-6 * abs(fstar)]
+        if ok:
+            k6 = ok[0]
+            out["objective_1e-6"] = {"iteration": k6, "time_s_est": t_sep * k6 / max(1, info_p.iters),
+                                     "kkt_rel_there": float(hist[k6][2])}
+    return out
+
+
 def result_parity(Q, V64, m, info, torch, fstar=None):
     n = m ** 3
     f = stencil_energy64(Q, V64, m, torch)
@@ -853,26 +891,9 @@ def run_stencil128(args, rank, world, local):
     del Qh
     # ---- the companion instance with a separable potential: exact optimum (tests/golden)
     Vs64 = torch.as_tensor(stencil3d_separable_potential(m)[0], device="cuda")
-    wls = dict(wl, V=Vs64.to(torch.float32), tol=wl["tol_separable"])
+    wls = dict(wl, V=Vs64.to(torch.float32), tol=wl["tol_separable"], **wl.get("separable", {}))
     sol_p = make_solver(wls, "fp32", torch, engine="graph", maxit=wl["maxit"])
-    t_sep, _, st_p, info_p = timed_solve_e2e(sol_p, Xh, Xw, Q, None, torch)
-    g = golden_fstar("stencil3d_separable_n2097152_p1024")
-    fstar = g["f_star"] if g else None
-    parity_sep = result_parity(Q, Vs64, m, info_p, torch, fstar)
-    parity_sep.update({"tol_kkt_rel": wls["tol"], "time_s": t_sep,
-                       "status": {0: "converged", 2: "maxit"}.get(st_p, str(st_p)),
-                       "potential": "V = v_x(x) + v_y(y) + v_z(z), v_k iid U[0, 1/3] (exact optimum "
-                                    "from three tridiagonal eigensolves)"})
-    if fstar is not None:
-        # the first iterate whose objective is within 1e-6 of f* (the device's f of the iterate
-        # X^k, which PCAL keeps at unit column norms: the orthonormalisation moves f only at
-        # second order), and the time to it at the solve's mean rate
-        hist = sol_p.history()
-        ok = [int(h[0]) for h in hist if abs(h[1] - fstar) <= 1e-6 * abs(fstar)]
-        if ok:
-            k6 = ok[0]
-            parity_sep["objective_1e-6"] = {"iteration": k6, "time_s_est": t_sep * k6 / max(1, info_p.iters),
-                                            "kkt_rel_there": float(hist[k6][2])}
+    parity_sep = companion_parity(sol_p, wls, Xh, Xw, Q, Vs64, m, torch)
     sol_p.close()
     del Xh, Q, Vs64
     torch.cuda.empty_cache()
