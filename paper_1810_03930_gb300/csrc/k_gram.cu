@@ -30,6 +30,8 @@
 //   Lambda^k = Lambda^{k-1} - beta (B^k - I), Lambda^0 = Psi(C^0), M = Lambda^k - beta (B - I)
 //   feas_row_i = sum_j (B_ij - delta_ij)^2
 // M is symmetric, so column i of M is row i.
+#include <type_traits>
+
 #include "plam_device.cuh"
 
 namespace plam {
@@ -150,6 +152,104 @@ gram_partial_kernel(int64_t n, int p, const Tin* __restrict__ X, int64_t ldx, co
   }
 }
 
+// The FP64 Gram X^T X of a float X (the final orthonormalisation's, and MOptQR's retraction's)
+// without FP64 multiplies: GB300 executes FP64 at 1/64 of the FP32 rate, so each product is
+// formed exactly in FP32 arithmetic, x y = h + r with h = fl(x y), r = fma(x, y, -h)
+// (TwoProduct), and summed as in Ogita, Rump and Oishi's Dot2: (s, q) = TwoSum(s, h) (exact),
+// with the TwoSum errors q and the product errors r in two separate float sums (added together
+// they lose r against the much larger q, and the product errors of squares are not centred: a
+// diagonal of X^T X then drifts low by a few u^2, u = 2^-24).  Every kExactFlush rows a thread
+// adds its three float sums into double totals, so a segment of 64 products carries an error of
+// order u^2 of its magnitude, and the segments are added in FP64.  Same tiles, stages and partial
+// layout as gram_partial_kernel (B only: G is not used).
+constexpr int kExactFlush = 64;   // rows per float segment of the exact Gram
+
+__global__ void __launch_bounds__(kThreads, 1)
+gram_partial_exact_kernel(int64_t n, int p, const float* __restrict__ X, int64_t ldx,
+                          int64_t rows_per_chunk, double* __restrict__ part,
+                          const DevState* __restrict__ st) {
+  if (st != nullptr && st->stop != kRunning) return;
+  const int nt = (p + kTile - 1) / kTile;
+  int ti, tj, isg;
+  decode_tile(blockIdx.x, nt, ti, tj, isg);
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk;
+  const int64_t r1 = min(n, r0 + rows_per_chunk);
+  const int i0 = ti * kTile, j0 = tj * kTile;
+
+  __shared__ float As[kTile][kKStep + 1];
+  __shared__ float Bs[kTile][kKStep + 1];
+
+  const int t = threadIdx.x;
+  const int tx = t & 15, ty = t >> 4;
+  const int kk = t & (kKStep - 1);
+  const int cb = t / kKStep;
+  float hs[4][4], he[4][4], hr[4][4];
+  double tot[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) { hs[u][v] = 0.f; he[u][v] = 0.f; hr[u][v] = 0.f; tot[u][v] = 0.0; }
+  int since = 0;
+
+  for (int64_t k0 = r0; k0 < r1; k0 += kKStep) {
+    const int64_t row = k0 + kk;
+    const bool rok = row < r1;
+#pragma unroll
+    for (int s = 0; s < kTile / 8; ++s) {
+      const int c = cb + 8 * s;
+      const int ci = i0 + c, cj = j0 + c;
+      As[c][kk] = (rok && ci < p) ? X[row + (int64_t)ci * ldx] : 0.f;
+      Bs[c][kk] = (rok && cj < p) ? X[row + (int64_t)cj * ldx] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int q = 0; q < kKStep; ++q) {
+      float a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { a[u] = As[tx + 16 * u][q]; b[u] = Bs[ty + 16 * u][q]; }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const float h = __fmul_rn(a[u], b[v]);
+          const float r = __fmaf_rn(a[u], b[v], -h);          // x y - h, exact
+          const float sn = __fadd_rn(hs[u][v], h);            // TwoSum(s, h)
+          const float bv = __fsub_rn(sn, hs[u][v]);
+          const float q2 = __fadd_rn(__fsub_rn(hs[u][v], __fsub_rn(sn, bv)), __fsub_rn(h, bv));
+          hs[u][v] = sn;
+          he[u][v] = __fadd_rn(he[u][v], q2);
+          hr[u][v] = __fadd_rn(hr[u][v], r);
+        }
+    }
+    __syncthreads();
+    since += kKStep;
+    if (since >= kExactFlush) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          tot[u][v] += (double)hs[u][v] + ((double)he[u][v] + (double)hr[u][v]);
+          hs[u][v] = 0.f;
+          he[u][v] = 0.f;
+          hr[u][v] = 0.f;
+        }
+      since = 0;
+    }
+  }
+  const size_t cstride = (size_t)2 * p * p;
+  double* out = part + (size_t)blockIdx.y * cstride;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + tx + 16 * u;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int j = j0 + ty + 16 * v;
+      if (i < p && j < p)
+        out[(size_t)j * p + i] = tot[u][v] + ((double)hs[u][v] + ((double)he[u][v] + (double)hr[u][v]));
+    }
+  }
+}
+
 template <typename T>
 __global__ void gram_reduce_kernel(int p, int nchunks, int with_g, const T* __restrict__ part,
                                    double* __restrict__ B, double* __restrict__ C) {
@@ -265,6 +365,12 @@ cudaError_t launch_gram_partial(int64_t n, int p, const Tin* X, int64_t ldx, con
   const int nt = (p + kTile - 1) / kTile;
   const int tiles = nt * (nt + 1) / 2 + (G ? nt * nt : 0);
   dim3 grid(tiles, nchunks);
+  if constexpr (std::is_same<Tin, float>::value && std::is_same<T, double>::value) {
+    if (G == nullptr) {   // the FP64 Gram of a float X: exact products, compensated FP32 sums
+      gram_partial_exact_kernel<<<grid, kThreads, 0, s>>>(n, p, X, ldx, rows_per_chunk, part, st);
+      return cudaGetLastError();
+    }
+  }
   gram_partial_kernel<Tin, T><<<grid, kThreads, 0, s>>>(n, p, X, ldx, G, ldg, rows_per_chunk, part,
                                                           st);
   return cudaGetLastError();
@@ -307,6 +413,7 @@ cudaError_t preload_gram_kernels() {
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_partial_kernel<float, float>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_partial_kernel<float, double>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_partial_kernel<double, double>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_partial_exact_kernel);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_reduce_kernel<float>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_reduce_kernel<double>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_finalize_kernel<float>);

@@ -12,6 +12,8 @@
 // apply_rinv_kernel: Q = X Z over 64 x 64 output tiles, double arithmetic
 // (float inputs are converted exactly), Z upper triangular so column c only
 // needs rows k <= c.
+#include <type_traits>
+
 #include "plam_device.cuh"
 
 namespace plam {
@@ -320,6 +322,119 @@ apply_rinv_kernel(int64_t n, int p, const T* __restrict__ X, int64_t ldx, const 
   }
 }
 
+// Q = X Z for a float X without FP64 multiplies (GB300 executes FP64 at 1/64 of the FP32 rate):
+// each entry of Z is split into float parts z = z_hi + z_lo (z_lo = fl(z - z_hi), so the pair
+// carries z to about 2^-48), x z_hi is formed exactly (TwoProduct: h + r), x z_lo in FP32 (a
+// term 2^-24 smaller), and the sum runs as Dot2 (TwoSum of h into s; the TwoSum errors and the
+// product terms r + x z_lo in two separate float sums, see the exact Gram), added into double
+// totals every 64 terms.  Same tiles and triangular skipping as apply_rinv_kernel.
+template <typename To>
+__global__ void __launch_bounds__(kThreads, 1)
+apply_rinv_exact_kernel(int64_t n, int p, const float* __restrict__ X, int64_t ldx,
+                        const double* __restrict__ Z, To* __restrict__ Q, int64_t ldq,
+                        const DevState* __restrict__ st) {
+  if (st != nullptr && st->stop != kRunning) return;
+  constexpr int KS = 16;
+  constexpr int kFlushK = 64;
+  const int64_t r0 = (int64_t)blockIdx.x * kTile;
+  const int c0 = blockIdx.y * kTile;
+  __shared__ float Xs[KS][kTile];
+  __shared__ float Zh[kTile][KS + 1];
+  __shared__ float Zl[kTile][KS + 1];
+  const int t = threadIdx.x;
+  const int tx = t & 15, ty = t >> 4;
+  float hs[4][4], he[4][4], hr[4][4];
+  double tot[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) { hs[u][v] = 0.f; he[u][v] = 0.f; hr[u][v] = 0.f; tot[u][v] = 0.0; }
+  const int kend = min(p, c0 + kTile);
+  int since = 0;
+  for (int k0 = 0; k0 < kend; k0 += KS) {
+    {
+      const int r = t & (kTile - 1);
+      const int64_t row = r0 + r;
+#pragma unroll
+      for (int s = 0; s < KS / 4; ++s) {
+        const int q = (t >> 6) + 4 * s;
+        const int col = k0 + q;
+        Xs[q][r] = (row < n && col < p) ? X[row + (int64_t)col * ldx] : 0.f;
+      }
+    }
+    {
+      const int q = t & (KS - 1);
+      const int kr = k0 + q;
+#pragma unroll
+      for (int s = 0; s < kTile * KS / kThreads; ++s) {
+        const int c = t / KS + (kThreads / KS) * s;
+        const int cc = c0 + c;
+        const double z = (kr < p && cc < p && kr <= cc) ? Z[kr + (size_t)cc * p] : 0.0;
+        const float zh = (float)z;
+        Zh[c][q] = zh;
+        Zl[c][q] = (float)(z - (double)zh);
+      }
+    }
+    __syncthreads();
+    bool live[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) live[v] = c0 + 16 * v + 15 >= k0;
+#pragma unroll 2
+    for (int q = 0; q < KS; ++q) {
+      float a[4], bh[4], bl[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = Xs[q][tx + 16 * u];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        bh[v] = live[v] ? Zh[ty + 16 * v][q] : 0.f;
+        bl[v] = live[v] ? Zl[ty + 16 * v][q] : 0.f;
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        if (!live[v]) continue;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float h = __fmul_rn(a[u], bh[v]);
+          const float r = __fmaf_rn(a[u], bh[v], -h);          // x z_hi - h, exact
+          const float m = __fmul_rn(a[u], bl[v]);
+          const float sn = __fadd_rn(hs[u][v], h);             // TwoSum(s, h)
+          const float bv = __fsub_rn(sn, hs[u][v]);
+          const float q2 = __fadd_rn(__fsub_rn(hs[u][v], __fsub_rn(sn, bv)), __fsub_rn(h, bv));
+          hs[u][v] = sn;
+          he[u][v] = __fadd_rn(he[u][v], q2);
+          hr[u][v] = __fadd_rn(hr[u][v], __fadd_rn(r, m));
+        }
+      }
+    }
+    __syncthreads();
+    since += KS;
+    if (since >= kFlushK) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          tot[u][v] += (double)hs[u][v] + ((double)he[u][v] + (double)hr[u][v]);
+          hs[u][v] = 0.f;
+          he[u][v] = 0.f;
+          hr[u][v] = 0.f;
+        }
+      since = 0;
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int c = c0 + ty + 16 * v;
+    if (c >= p) continue;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t r = r0 + tx + 16 * u;
+      if (r < n)
+        Q[r + (int64_t)c * ldq] =
+            (To)(tot[u][v] + ((double)hs[u][v] + ((double)he[u][v] + (double)hr[u][v])));
+    }
+  }
+}
+
 // ||B - I||_F: one CTA per column (coalesced), then the column sums in order.
 __global__ void feas_col_kernel(int p, const double* __restrict__ B, double* __restrict__ col) {
   __shared__ double scratch[33];
@@ -380,7 +495,10 @@ template <typename T>
 cudaError_t launch_apply_rinv(int64_t n, int p, const T* X, int64_t ldx, const double* Z, double* Q,
                               int64_t ldq, cudaStream_t s) {
   dim3 grid((unsigned)((n + kTile - 1) / kTile), (p + kTile - 1) / kTile);
-  apply_rinv_kernel<T, double><<<grid, kThreads, 0, s>>>(n, p, X, ldx, Z, Q, ldq, nullptr);
+  if constexpr (std::is_same<T, float>::value)
+    apply_rinv_exact_kernel<double><<<grid, kThreads, 0, s>>>(n, p, X, ldx, Z, Q, ldq, nullptr);
+  else
+    apply_rinv_kernel<T, double><<<grid, kThreads, 0, s>>>(n, p, X, ldx, Z, Q, ldq, nullptr);
   return cudaGetLastError();
 }
 
@@ -388,7 +506,10 @@ template <typename T>
 cudaError_t launch_apply_rinv_same(int64_t n, int p, const T* X, int64_t ldx, const double* Z, T* Q,
                                    int64_t ldq, const DevState* st, cudaStream_t s) {
   dim3 grid((unsigned)((n + kTile - 1) / kTile), (p + kTile - 1) / kTile);
-  apply_rinv_kernel<T, T><<<grid, kThreads, 0, s>>>(n, p, X, ldx, Z, Q, ldq, st);
+  if constexpr (std::is_same<T, float>::value)
+    apply_rinv_exact_kernel<float><<<grid, kThreads, 0, s>>>(n, p, X, ldx, Z, Q, ldq, st);
+  else
+    apply_rinv_kernel<T, T><<<grid, kThreads, 0, s>>>(n, p, X, ldx, Z, Q, ldq, st);
   return cudaGetLastError();
 }
 
