@@ -164,10 +164,15 @@ gram_partial_kernel(int64_t n, int p, const Tin* __restrict__ X, int64_t ldx, co
 // layout as gram_partial_kernel (B only: G is not used).
 constexpr int kExactFlush = 64;   // rows per float segment of the exact Gram
 
+// Tin = double (the feasibility report of a double Q): each entry is split into float parts
+// q = q_hi + q_lo (about 48 bits), q_hi q_hi' is formed exactly and the cross terms
+// q_hi q_lo' + q_lo q_hi' in FP32 (q_lo q_lo' is below 2^-48 of the product and dropped).
+template <typename Tin>
 __global__ void __launch_bounds__(kThreads, 1)
-gram_partial_exact_kernel(int64_t n, int p, const float* __restrict__ X, int64_t ldx,
+gram_partial_exact_kernel(int64_t n, int p, const Tin* __restrict__ X, int64_t ldx,
                           int64_t rows_per_chunk, double* __restrict__ part,
                           const DevState* __restrict__ st) {
+  constexpr bool kSplit = std::is_same<Tin, double>::value;
   if (st != nullptr && st->stop != kRunning) return;
   const int nt = (p + kTile - 1) / kTile;
   int ti, tj, isg;
@@ -178,6 +183,8 @@ gram_partial_exact_kernel(int64_t n, int p, const float* __restrict__ X, int64_t
 
   __shared__ float As[kTile][kKStep + 1];
   __shared__ float Bs[kTile][kKStep + 1];
+  __shared__ float Al[kSplit ? kTile : 1][kKStep + 1];
+  __shared__ float Bl[kSplit ? kTile : 1][kKStep + 1];
 
   const int t = threadIdx.x;
   const int tx = t & 15, ty = t >> 4;
@@ -198,21 +205,39 @@ gram_partial_exact_kernel(int64_t n, int p, const float* __restrict__ X, int64_t
     for (int s = 0; s < kTile / 8; ++s) {
       const int c = cb + 8 * s;
       const int ci = i0 + c, cj = j0 + c;
-      As[c][kk] = (rok && ci < p) ? X[row + (int64_t)ci * ldx] : 0.f;
-      Bs[c][kk] = (rok && cj < p) ? X[row + (int64_t)cj * ldx] : 0.f;
+      if constexpr (kSplit) {
+        const double xa = (rok && ci < p) ? X[row + (int64_t)ci * ldx] : 0.0;
+        const double xb = (rok && cj < p) ? X[row + (int64_t)cj * ldx] : 0.0;
+        const float ha = (float)xa, hb = (float)xb;
+        As[c][kk] = ha;
+        Bs[c][kk] = hb;
+        Al[c][kk] = (float)(xa - (double)ha);
+        Bl[c][kk] = (float)(xb - (double)hb);
+      } else {
+        As[c][kk] = (rok && ci < p) ? X[row + (int64_t)ci * ldx] : 0.f;
+        Bs[c][kk] = (rok && cj < p) ? X[row + (int64_t)cj * ldx] : 0.f;
+      }
     }
     __syncthreads();
 #pragma unroll 2
     for (int q = 0; q < kKStep; ++q) {
-      float a[4], b[4];
+      float a[4], b[4], al[4], bl[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) { a[u] = As[tx + 16 * u][q]; b[u] = Bs[ty + 16 * u][q]; }
+      for (int u = 0; u < 4; ++u) {
+        a[u] = As[tx + 16 * u][q];
+        b[u] = Bs[ty + 16 * u][q];
+        if constexpr (kSplit) {
+          al[u] = Al[tx + 16 * u][q];
+          bl[u] = Bl[ty + 16 * u][q];
+        }
+      }
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const float h = __fmul_rn(a[u], b[v]);
-          const float r = __fmaf_rn(a[u], b[v], -h);          // x y - h, exact
+          float r = __fmaf_rn(a[u], b[v], -h);                // x y - h, exact
+          if constexpr (kSplit) r = __fadd_rn(r, __fmaf_rn(al[u], b[v], __fmul_rn(a[u], bl[v])));
           const float sn = __fadd_rn(hs[u][v], h);            // TwoSum(s, h)
           const float bv = __fsub_rn(sn, hs[u][v]);
           const float q2 = __fadd_rn(__fsub_rn(hs[u][v], __fsub_rn(sn, bv)), __fsub_rn(h, bv));
@@ -367,12 +392,22 @@ cudaError_t launch_gram_partial(int64_t n, int p, const Tin* X, int64_t ldx, con
   dim3 grid(tiles, nchunks);
   if constexpr (std::is_same<Tin, float>::value && std::is_same<T, double>::value) {
     if (G == nullptr) {   // the FP64 Gram of a float X: exact products, compensated FP32 sums
-      gram_partial_exact_kernel<<<grid, kThreads, 0, s>>>(n, p, X, ldx, rows_per_chunk, part, st);
+      gram_partial_exact_kernel<float><<<grid, kThreads, 0, s>>>(n, p, X, ldx, rows_per_chunk, part,
+                                                                 st);
       return cudaGetLastError();
     }
   }
   gram_partial_kernel<Tin, T><<<grid, kThreads, 0, s>>>(n, p, X, ldx, G, ldg, rows_per_chunk, part,
                                                           st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_report(int64_t n, int p, const double* Q, int64_t ldq,
+                               int64_t rows_per_chunk, int nchunks, double* part, cudaStream_t s) {
+  const int nt = (p + kTile - 1) / kTile;
+  dim3 grid(nt * (nt + 1) / 2, nchunks);
+  gram_partial_exact_kernel<double><<<grid, kThreads, 0, s>>>(n, p, Q, ldq, rows_per_chunk, part,
+                                                              nullptr);
   return cudaGetLastError();
 }
 
@@ -413,7 +448,8 @@ cudaError_t preload_gram_kernels() {
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_partial_kernel<float, float>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_partial_kernel<float, double>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_partial_kernel<double, double>);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_partial_exact_kernel);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_partial_exact_kernel<float>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_partial_exact_kernel<double>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_reduce_kernel<float>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_reduce_kernel<double>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_finalize_kernel<float>);

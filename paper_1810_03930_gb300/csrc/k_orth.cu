@@ -26,9 +26,9 @@ namespace plam {
 //   chol_row_kernel     the row panel R[j, k] = R_jj^{-T} W[j, k] = Z_jj^T W[j, k], k >= j1
 //   chol_update_kernel  the trailing upper triangle W[i, k] -= R[j, i]^T R[j, k],
 //                       j1 <= i <= k, on upper-triangle tiles
-// then Z = R^{-1} by block rows from the bottom (rinv_row_kernel):
-//   Z[b, c] = -Z_bb sum_{b < l <= c} R[b, l] Z[l, c]   (block rows below b are final).
-// Only the upper triangle of W is read; Z is zero below its diagonal.
+// then Z = R^{-1} from the inverted 32 x 32 diagonal blocks by recursive doubling
+// (rinv_pair_t_kernel, rinv_pair_z_kernel, below).  Only the upper triangle of W is read; Z is
+// zero below its diagonal on return.
 
 constexpr int kCB = 32;
 
@@ -136,54 +136,6 @@ chol_update_kernel(int p, int j0, double* __restrict__ W, const int* __restrict_
   }
 }
 
-__global__ void __launch_bounds__(256)
-rinv_row_kernel(int p, int bi, const double* __restrict__ W, double* __restrict__ Z,
-                const int* __restrict__ info) {
-  __shared__ double Rs[kCB][kCB + 1];
-  __shared__ double Zs[kCB][kCB + 1];
-  __shared__ double Ts[kCB][kCB + 1];
-  if (*(volatile const int*)info != 0) return;
-  const int bk = bi + 1 + (int)blockIdx.x;
-  const int i0 = bi * kCB, ni = min(kCB, p - i0);
-  const int k0 = bk * kCB, nk = min(kCB, p - k0);
-  const int t = threadIdx.x, a = t & 31;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int bl = bi + 1; bl <= bk; ++bl) {
-    const int l0 = bl * kCB, nl = min(kCB, p - l0);
-    __syncthreads();
-    for (int e = t; e < kCB * kCB; e += 256) {
-      const int x = e & 31, y = e >> 5;
-      Rs[x][y] = (x < ni && y < nl) ? W[(i0 + x) + (size_t)(l0 + y) * p] : 0.0;
-      Zs[x][y] = (x < nl && y < nk) ? Z[(l0 + x) + (size_t)(k0 + y) * p] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int b = (t >> 5) + 8 * v;
-      double sum = acc[v];
-      for (int l = 0; l < kCB; ++l) sum += Rs[a][l] * Zs[l][b];
-      acc[v] = sum;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int v = 0; v < 4; ++v) Ts[a][(t >> 5) + 8 * v] = acc[v];
-  for (int e = t; e < kCB * kCB; e += 256) {
-    const int x = e & 31, y = e >> 5;
-    Rs[x][y] = (x < ni && y < ni) ? Z[(i0 + x) + (size_t)(i0 + y) * p] : 0.0;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const int b = (t >> 5) + 8 * v;
-    if (a < ni && b < nk) {
-      double sum = 0.0;
-      for (int m = a; m < ni; ++m) sum += Rs[a][m] * Ts[m][b];
-      Z[(i0 + a) + (size_t)(k0 + b) * p] = -sum;
-    }
-  }
-}
-
 // The same factorisation and inverse for p <= kCholSmemMaxP with R and Z in
 // shared memory: the trailing update indexes (a, b) of the remaining square
 // directly (no square root per element), the pivot reciprocals are formed once,
@@ -245,6 +197,115 @@ cholesky_inverse_smem_kernel(int p, const double* __restrict__ B, double* __rest
   for (int e = t; e < p * p; e += nt) {
     W[e] = Ws[e];
     Z[e] = Zs[e];
+  }
+}
+
+// ---- Z = R^{-1} by recursive doubling (the blocked path, p > kCholSmemMaxP):
+// once the diagonal super-blocks of size s are inverted (the 32 x 32 ones by chol_diag_kernel),
+// each pair of adjacent super-blocks A = [2qs, (2q+1)s), C = [(2q+1)s, (2q+2)s) gets its
+// off-diagonal block from
+//     T = R_AC Z_CC,      Z_AC = -Z_AA T,
+// and the pairs of one level are independent: log2(p / 32) levels of two batched launches
+// instead of p / 32 dependent block rows.  T is kept transposed in the (otherwise unused)
+// lower triangle of Z, which a last pass sets back to zero.  32 x 32 output tiles of 256
+// threads (4 entries each), FP64, the triangular factors' zero parts skipped.
+__device__ __forceinline__ bool rinv_pair(int p, int s, int q, int& a0, int& na, int& c0, int& nc) {
+  a0 = 2 * q * s;
+  c0 = a0 + s;
+  if (c0 >= p) return false;
+  na = s;
+  nc = min(s, p - c0);
+  return true;
+}
+
+// T^T (rows C, columns A of Z) = (R_AC Z_CC)^T; grid (tiles of A, tiles of C, pairs).
+__global__ void __launch_bounds__(256)
+rinv_pair_t_kernel(int p, int s, const double* __restrict__ W, double* __restrict__ Z,
+                   const int* __restrict__ info) {
+  __shared__ double Rs[kCB][kCB + 1];
+  __shared__ double Zs[kCB][kCB + 1];
+  if (*(volatile const int*)info != 0) return;
+  int a0, na, c0, nc;
+  if (!rinv_pair(p, s, (int)blockIdx.z, a0, na, c0, nc)) return;
+  const int ti = (int)blockIdx.x * kCB, tj = (int)blockIdx.y * kCB;
+  if (ti >= na || tj >= nc) return;
+  const int t = threadIdx.x, a = t & 31;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  // k runs over C up to the tile's last column (Z_CC is upper triangular)
+  const int kend = min(nc, tj + kCB);
+  for (int k0 = 0; k0 < kend; k0 += kCB) {
+    __syncthreads();
+    for (int e = t; e < kCB * kCB; e += 256) {
+      const int x = e & 31, y = e >> 5;
+      const int gi = a0 + ti + x, gk = c0 + k0 + y;
+      Rs[x][y] = (ti + x < na && k0 + y < nc) ? W[gi + (size_t)gk * p] : 0.0;
+      const int lk = k0 + x, lj = tj + y;                       // Z_CC (lk, lj)
+      Zs[x][y] = (lk < nc && lj < nc && lk <= lj) ? Z[(c0 + lk) + (size_t)(c0 + lj) * p] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int b = (t >> 5) + 8 * v;
+      double sum = acc[v];
+#pragma unroll 8
+      for (int k = 0; k < kCB; ++k) sum = fma(Rs[a][k], Zs[k][b], sum);
+      acc[v] = sum;
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int b = (t >> 5) + 8 * v;
+    if (ti + a < na && tj + b < nc)
+      Z[(c0 + tj + b) + (size_t)(a0 + ti + a) * p] = acc[v];   // T(i, j) at Z[j, i]
+  }
+}
+
+// Z_AC = -Z_AA T with T(k, j) read from Z[j, k]; grid (tiles of A, tiles of C, pairs).
+__global__ void __launch_bounds__(256)
+rinv_pair_z_kernel(int p, int s, double* __restrict__ Z, const int* __restrict__ info) {
+  __shared__ double As[kCB][kCB + 1];
+  __shared__ double Ts[kCB][kCB + 1];
+  if (*(volatile const int*)info != 0) return;
+  int a0, na, c0, nc;
+  if (!rinv_pair(p, s, (int)blockIdx.z, a0, na, c0, nc)) return;
+  const int ti = (int)blockIdx.x * kCB, tj = (int)blockIdx.y * kCB;
+  if (ti >= na || tj >= nc) return;
+  const int t = threadIdx.x, a = t & 31;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  // k runs over A from the tile's first row (Z_AA is upper triangular)
+  for (int k0 = ti; k0 < na; k0 += kCB) {
+    __syncthreads();
+    for (int e = t; e < kCB * kCB; e += 256) {
+      const int x = e & 31, y = e >> 5;
+      const int li = ti + x, lk = k0 + y;                       // Z_AA (li, lk)
+      As[x][y] = (li < na && lk < na && li <= lk) ? Z[(a0 + li) + (size_t)(a0 + lk) * p] : 0.0;
+      const int kk = k0 + x, lj = tj + y;                       // T(kk, lj) = Z[c0 + lj, a0 + kk]
+      Ts[x][y] = (kk < na && lj < nc) ? Z[(c0 + lj) + (size_t)(a0 + kk) * p] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int b = (t >> 5) + 8 * v;
+      double sum = acc[v];
+#pragma unroll 8
+      for (int k = 0; k < kCB; ++k) sum = fma(As[a][k], Ts[k][b], sum);
+      acc[v] = sum;
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int b = (t >> 5) + 8 * v;
+    if (ti + a < na && tj + b < nc) Z[(a0 + ti + a) + (size_t)(c0 + tj + b) * p] = -acc[v];
+  }
+}
+
+// The strictly lower triangle of Z back to zero (it held the transposed T blocks).
+__global__ void zero_lower_kernel(int p, double* __restrict__ Z) {
+  const size_t total = (size_t)p * p;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % p), c = (int)(e / p);
+    if (r > c) Z[e] = 0.0;
   }
 }
 
@@ -480,15 +541,27 @@ cudaError_t launch_cholesky_inverse(int p, const double* B, double* W, double* Z
       chol_update_kernel<<<dim3(rest, rest), 256, 0, s>>>(p, j0, W, info);
     }
   }
-  for (int bi = nbt - 2; bi >= 0; --bi)
-    rinv_row_kernel<<<nbt - 1 - bi, 256, 0, s>>>(p, bi, W, Z, info);
+  for (int sz = kCB; sz < p; sz *= 2) {
+    const int pairs = (p + 2 * sz - 1) / (2 * sz);
+    const dim3 grid((unsigned)((sz + kCB - 1) / kCB), (unsigned)((sz + kCB - 1) / kCB),
+                    (unsigned)pairs);
+    rinv_pair_t_kernel<<<grid, 256, 0, s>>>(p, sz, W, Z, info);
+    rinv_pair_z_kernel<<<grid, 256, 0, s>>>(p, sz, Z, info);
+  }
+  {
+    int blocks = (int)(((size_t)p * p + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    zero_lower_kernel<<<blocks, 256, 0, s>>>(p, Z);
+  }
   return cudaGetLastError();
 }
 
 int cholesky_inverse_launches(int p) {
   if (p <= kCholSmemMaxP) return 1;
   const int nbt = (p + kCB - 1) / kCB;
-  return nbt + 2 * (nbt - 1) + (nbt - 1);
+  int levels = 0;
+  for (int sz = kCB; sz < p; sz *= 2) ++levels;
+  return nbt + 2 * (nbt - 1) + 2 * levels + 1;
 }
 
 template <typename T>

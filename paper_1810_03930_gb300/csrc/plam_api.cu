@@ -594,8 +594,7 @@ plam_status_t orthonormalize_impl(plam_handle_s* h, const T* X, int64_t ldx, dou
     h->launches += 1;
   }
   if (feas) {
-    CK((launch_gram_partial<double, double>(h->n, p, Xout, ldo, (const double*)nullptr, 0,
-                                             h->rows_per_chunk, h->nchunks, h->part64, nullptr, s)));
+    CK(launch_gram_report(h->n, p, Xout, ldo, h->rows_per_chunk, h->nchunks, h->part64, s));
     CK(launch_gram_reduce<double>(p, h->nchunks, 0, h->part64, h->B, nullptr, s));
     if (h->sharded) {
       int nk = 0;

@@ -318,6 +318,10 @@ cudaError_t preload_batched_kernels();
 
 // Force the module load of every kernel (lazy loading must not happen inside
 // a stream capture).
+// Q^T Q of a double Q for the feasibility report: entries split into float pairs (about 48
+// bits), exact FP32 products and compensated sums; partials in the layout of launch_gram_partial.
+cudaError_t launch_gram_report(int64_t n, int p, const double* Q, int64_t ldq,
+                               int64_t rows_per_chunk, int nchunks, double* part, cudaStream_t s);
 cudaError_t preload_gram_kernels();
 cudaError_t preload_update_kernels();
 cudaError_t preload_objective_kernels();
