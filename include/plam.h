@@ -152,6 +152,10 @@ typedef struct {
                            feasibility ||Q^T Q - I||_F of the orthonormalised output Q
                            (plam_info_t.f_orth, kkt_orth, feas_orth); 0: skipped (NaN) — the
                            feasibility alone is one more FP64 Gram of Q, n p^2 / 2 multiply-adds */
+  double eta_min;       /* > 0: lower bound of every step-size parameter eta^k (eta0 included); 0: 1e-10 eta0.
+                           The convergence analysis asks eta^k in an interval [eta_low, eta_up];
+                           a lower bound caps the step 1/eta^k that the BB rules may take */
+  double eta_max;       /* > 0: upper bound of eta^k; 0: 1e10 eta0.  eta_min <= eta_max when both > 0 */
 } plam_params_t;
 
 typedef struct {
@@ -342,8 +346,9 @@ typedef struct {
 typedef struct plam_batch_s* plam_batch_t;
 
 /* prm: precision must be PLAM_PREC_FP32; variant, lambda_rule, beta, eta rule,
- * tol and maxit apply to every problem (the other fields, feas_max among them, are
- * not used: a problem stops as diverged only on non-finite values).  The problem array is copied; A, X and
+ * eta_min, eta_max, tol and maxit apply to every problem (the other fields,
+ * feas_max among them, are not used: a problem stops as diverged only on
+ * non-finite values).  The problem array is copied; A, X and
  * Q stay owned by the caller and must outlive the batch.  The workspace (three
  * n x p float buffers per problem) is allocated here. */
 plam_status_t plam_batch_create(plam_batch_t* b, const plam_batch_problem_t* probs, int count,

@@ -39,14 +39,17 @@ def cholesky_retraction(V):
 
 
 def solve(obj, X0, eta_rule="abb", eta0=None, tol=1e-8, maxit=3000, gamma=None,
-          clamp=(1e-10, 1e10), record=True) -> SolveResult:
+          clamp=(1e-10, 1e10), eta_min=None, eta_max=None, record=True) -> SolveResult:
     """Run MOptQR from X0 (n-by-p, orthonormal)."""
     X = np.array(X0, dtype=np.float64, order="F", copy=True)
     G = obj.grad(X)
     K0 = fro(kkt_residual(G, X))
     if eta0 is None:
         eta0 = default_eta0(G, X, 0.0)
-    lo, hi = clamp[0] * eta0, clamp[1] * eta0
+    # [eta_min, eta_max] when given (the interval the convergence analysis assumes for eta^k),
+    # else relative to eta0
+    lo = eta_min if eta_min else clamp[0] * eta0
+    hi = eta_max if eta_max else clamp[1] * eta0
     hist = []
     X_prev = D_prev = None
     eta = eta0

@@ -25,8 +25,10 @@ Readings where the paper is silent or ambiguous (each listed in the design notes
     with (the PCAL multiplier when PCAL uses eq. lambda2).
   * ABB: k counts from 0; k = 0 uses eta0; odd k uses BB1, even k >= 2 BB2.
   * eta0 (no history at k = 0) defaults to ||G^0||_F / ||X^0||_F + beta.
-  * Safeguards: if <S,S> = 0 or <S,Y> = 0 the previous eta is kept; eta is
-    clamped to [1e-10 eta0, 1e10 eta0].
+  * Safeguards: if <S,S> = 0 or <S,Y> = 0 the previous eta is kept; every eta,
+    eta0 included, is clamped to [eta_min, eta_max] (the interval of the step-size
+    condition of the convergence analysis) when they are given, else to
+    [1e-10 eta0, 1e10 eta0].
   * If the initial KKT residual is exactly zero the start is returned as converged.
   * A non-finite KKT value, step size or iterate stops the run as diverged; X
     is then the last finite iterate.
@@ -154,7 +156,8 @@ class SolveResult:
 
 
 def solve(obj, X0, variant="pcal", beta=1.0, lambda_rule="lambda2", eta_rule="abb",
-          eta0=None, tol=1e-8, maxit=3000, gamma=None, clamp=(1e-10, 1e10),
+          eta0=None, tol=1e-8, maxit=3000, gamma=None, clamp=(1e-10, 1e10), eta_min=None,
+          eta_max=None,
           record=True, callback=None) -> SolveResult:
     """Run PLAM (variant='plam') or PCAL (variant='pcal') from X0 (n-by-p, FP64)."""
     if variant not in ("plam", "pcal"):
@@ -166,7 +169,10 @@ def solve(obj, X0, variant="pcal", beta=1.0, lambda_rule="lambda2", eta_rule="ab
     K0 = fro(kkt_residual(G, X))
     if eta0 is None:
         eta0 = default_eta0(G, X, beta)
-    lo, hi = clamp[0] * eta0, clamp[1] * eta0
+    # [eta_min, eta_max] when given (the interval the convergence analysis assumes for eta^k),
+    # else relative to eta0
+    lo = eta_min if eta_min else clamp[0] * eta0
+    hi = eta_max if eta_max else clamp[1] * eta0
     hist = []
     X_prev = R_prev = None
     Lam_prev = None

@@ -118,7 +118,8 @@ class Solver:
                  variant="pcal", lambda_rule="lambda2", beta=1.0, eta_rule="abb", eta0=0.0,
                  eta_gamma=0.0, tol=1e-8, maxit=3000, precision="fp64", final_orth=1,
                  graph_iters=16, engine="auto", tensor_cores="auto", refine_switch=1e-3,
-                 energy=None, orth_metrics=True, stream=None, shard=None, feas_max=1e6):
+                 energy=None, orth_metrics=True, stream=None, shard=None, feas_max=1e6,
+                 eta_min=0.0, eta_max=0.0):
         torch = _torch()
         self.n, self.p = int(n), int(p)
         self.precision = precision
@@ -143,6 +144,8 @@ class Solver:
         prm.refine_switch = float(refine_switch)
         prm.orth_metrics = 1 if orth_metrics else 0
         prm.feas_max = float(feas_max)
+        prm.eta_min = float(eta_min)
+        prm.eta_max = float(eta_max)
         self.params = prm
         obj = _lib.plam_objective_t()
         self._keep = []
@@ -319,7 +322,8 @@ class BatchSolver:
     (or (p, ld) device tensors from colmajor_to_device).  FP32 storage; FP64 outputs Q_b."""
 
     def __init__(self, As, X0s, *, variant="pcal", lambda_rule="lambda2", beta=1.0, eta_rule="abb",
-                 eta0=0.0, eta_gamma=0.0, tol=1e-6, maxit=3000, orthonormalize=True, stream=None):
+                 eta0=0.0, eta_gamma=0.0, tol=1e-6, maxit=3000, orthonormalize=True, stream=None,
+                 eta_min=0.0, eta_max=0.0):
         torch = _torch()
         prm = plam_default_params()
         prm.variant = PLAM_VARIANT_PCAL if variant == "pcal" else PLAM_VARIANT_PLAM
@@ -327,6 +331,7 @@ class BatchSolver:
         prm.beta, prm.eta_rule = float(beta), _RULES[eta_rule]
         prm.eta0, prm.eta_gamma = float(eta0), float(eta_gamma)
         prm.tol, prm.maxit = float(tol), int(maxit)
+        prm.eta_min, prm.eta_max = float(eta_min), float(eta_max)
         prm.precision = PLAM_PREC_FP32
         self.A, self.X, self.Q, probs = [], [], [], []
         for A, X0 in zip(As, X0s):

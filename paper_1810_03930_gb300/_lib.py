@@ -41,7 +41,7 @@ class plam_params_t(C.Structure):
                 ("tol", C.c_double), ("maxit", C.c_int), ("precision", C.c_int),
                 ("final_orth", C.c_int), ("graph_iters", C.c_int), ("engine", C.c_int),
                 ("tensor_cores", C.c_int), ("refine_switch", C.c_double), ("feas_max", C.c_double),
-                ("orth_metrics", C.c_int)]
+                ("orth_metrics", C.c_int), ("eta_min", C.c_double), ("eta_max", C.c_double)]
 
 
 # int grad(void* ctx, const void* X, int64_t ldx, void* G, int64_t ldg, double* f, void* stream)

@@ -392,7 +392,7 @@ __device__ void batch_solve_one(const BatchDesc& q, const BatchParams& prm, plam
           e = prm.eta_rule == 1 ? bb1 : prm.eta_rule == 2 ? bb2 : ((k & 1) ? bb1 : bb2);
         }
         if (!isfinite(e)) st = kDiverged;
-        else e = fmin(fmax(e, 1e-10 * eta0), 1e10 * eta0);
+        else e = eta_clamp(e, eta0, prm.eta_min, prm.eta_max);
       }
       eta = e;
       S.sc[0] = e;

@@ -639,7 +639,7 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_solve_kernel(Resident
             e2 = (prm.eta_rule == 1) ? bb1 : (prm.eta_rule == 2) ? bb2 : ((k & 1) ? bb1 : bb2);
           }
           if (!isfinite(e2)) s = kDiverged;
-          else e2 = fmin(fmax(e2, 1e-10 * eta0), 1e10 * eta0);
+          else e2 = eta_clamp(e2, eta0, prm.eta_min, prm.eta_max);
         }
         sc[0] = e2;
         sc[1] = (double)s;

@@ -348,7 +348,7 @@ step_size_kernel(int nrt, int nct, const T* __restrict__ colpart, const T* __res
         else eta = (k & 1) ? bb1 : bb2;              // alternating BB
       }
       if (!isfinite(eta)) stop = kDiverged;
-      else eta = fmin(fmax(eta, 1e-10 * eta0), 1e10 * eta0);
+      else eta = eta_clamp(eta, eta0, prm.eta_min, prm.eta_max);
     }
     sc[0] = eta;
     sc[1] = (double)stop;

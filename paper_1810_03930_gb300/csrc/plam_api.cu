@@ -201,6 +201,10 @@ plam_status_t validate_params(const plam_params_t* prm) {
   }
   if (!(prm->refine_switch >= 0.0)) return PLAM_ERR_INVALID;
   if (!(prm->feas_max >= 0.0)) return PLAM_ERR_INVALID;
+  if (!(prm->eta_min >= 0.0) || !(prm->eta_max >= 0.0) || !std::isfinite(prm->eta_min) ||
+      !std::isfinite(prm->eta_max) ||
+      (prm->eta_min > 0.0 && prm->eta_max > 0.0 && prm->eta_min > prm->eta_max))
+    return PLAM_ERR_INVALID;
   return PLAM_OK;
 }
 
@@ -242,6 +246,8 @@ IterParams iter_params(const plam_handle_s* h, int variant, int lambda2) {
   ip.lam = h->lam;
   ip.refine_switch = h->use_tc ? h->prm.refine_switch : 0.0;
   ip.feas_max = h->prm.feas_max;
+  ip.eta_min = h->prm.eta_min;
+  ip.eta_max = h->prm.eta_max;
   if (variant == PLAM_VARIANT_MOPTQR) {   // no penalty, no column scaling, M = C^T
     ip.moptqr = 1;
     ip.variant = PLAM_VARIANT_PLAM;
@@ -818,6 +824,8 @@ plam_status_t plam_default_params(plam_params_t* prm) {
   prm->tensor_cores = -1;
   prm->refine_switch = 1e-3;
   prm->feas_max = 1e6;
+  prm->eta_min = 0.0;
+  prm->eta_max = 0.0;
   prm->orth_metrics = 1;
   return PLAM_OK;
 }
@@ -1581,6 +1589,8 @@ plam_status_t plam_batch_create(plam_batch_t* out, const plam_batch_problem_t* p
   b->prm.eta0_user = prm->eta0;
   b->prm.gamma = prm->eta_gamma;
   b->prm.tol = prm->tol;
+  b->prm.eta_min = prm->eta_min;
+  b->prm.eta_max = prm->eta_max;
   int dev = 0, sms = 1;
   if (cudaGetDevice(&dev) == cudaSuccess)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

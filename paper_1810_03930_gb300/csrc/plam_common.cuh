@@ -69,6 +69,7 @@ struct IterParams {
   double refine_switch;  // <= 0: the compensated phase never starts on its own (see DevState.refine)
   int moptqr;            // 1: MOptQR's update matrix, M = C^T (R = G - X G^T X), no penalty
   double feas_max;       // > 0: ||X^T X - I||_F above it stops the run as diverged
+  double eta_min, eta_max;   // > 0: bounds of eta^k; 0: 1e-10 eta0 and 1e10 eta0
 };
 
 // MOptQR's Barzilai-Borwein sums of S = X - X_prev and Y = R^k - R^{k-1}, per tile of the
@@ -309,7 +310,16 @@ struct BatchDesc {
 struct BatchParams {
   int variant, lambda2, eta_rule, maxit;
   double beta, eta0_user, gamma, tol;
+  double eta_min, eta_max;   // > 0: bounds of eta^k; 0: 1e-10 eta0 and 1e10 eta0
 };
+
+// The step-size interval: [eta_min, eta_max] where given, else [1e-10 eta0, 1e10 eta0].
+__host__ __device__ inline double eta_clamp(double eta, double eta0, double eta_min,
+                                            double eta_max) {
+  const double lo = eta_min > 0.0 ? eta_min : 1e-10 * eta0;
+  const double hi = eta_max > 0.0 ? eta_max : 1e10 * eta0;
+  return fmin(fmax(eta, lo), hi);
+}
 
 size_t batch_smem_bytes(int rb);
 cudaError_t launch_batched(int rb, const BatchDesc* desc, const int* order, int count, int* next,

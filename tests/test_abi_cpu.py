@@ -102,11 +102,17 @@ def test_create_rejects_bad_params_and_objectives(lib):
     obj.kind = _lib.PLAM_OBJ_HARTREE1D
     obj.alpha, obj.quad_scale = 1.0, 0.25
     for field, value in (("variant", 7), ("eta_rule", 9), ("precision", 5), ("beta", -1.0),
-                         ("maxit", -1), ("final_orth", 3)):
+                         ("maxit", -1), ("final_orth", 3), ("eta_min", -1.0), ("eta_max", -2.0),
+                         ("tensor_cores", 3), ("tensor_cores", 11)):
         prm = _lib.plam_default_params()
         setattr(prm, field, value)
         h = C.c_void_p()
         assert lib.plam_create(C.byref(h), 100, 5, C.byref(obj), C.byref(prm), None) == _lib.PLAM_ERR_INVALID
+    prm = _lib.plam_default_params()
+    prm.eta_min, prm.eta_max = 2.0, 1.0           # an empty step-size interval
+    h = C.c_void_p()
+    assert lib.plam_create(C.byref(h), 100, 5, C.byref(obj), C.byref(prm), None) == _lib.PLAM_ERR_INVALID
+    assert prm.eta_min > 0 and _lib.plam_default_params().eta_min == 0.0
     prm = _lib.plam_default_params()
     bad = _lib.plam_objective_t()
     bad.kind = _lib.PLAM_OBJ_STENCIL3D

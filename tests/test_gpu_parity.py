@@ -221,6 +221,44 @@ def test_first_twenty_step_sizes_match_oracle_every_rule(variant, rule):
     r.close()
 
 
+@pytest.mark.parametrize("variant", ["plam", "pcal"])
+def test_step_size_interval_matches_oracle(variant):
+    """eta^k clamped to [eta_min, eta_max] (the interval the convergence analysis assumes), with a
+    lower bound that binds on some steps: the FP64 graph engine's eta, KKT and f over 20
+    iterations as the oracle's, every eta inside the interval; the FP32 resident engine and the
+    batched engine clamp the same way (their first eta as the oracle's, all inside)."""
+    from paper_1810_03930_gb300 import BatchSolver
+    w = workload_dense_trace(500, 20)
+    obj = oo.TraceObjective(w.A)
+    free = op.solve(obj, w.X0, variant=variant, beta=1.0, tol=0.0, maxit=20)
+    lo = float(np.median([h.eta for h in free.history[:20]]))
+    hi = 4.0 * lo
+    ref = op.solve(obj, w.X0, variant=variant, beta=1.0, tol=0.0, maxit=20, eta_min=lo, eta_max=hi)
+    eta_ref = np.array([h.eta for h in ref.history[:20]])
+    assert np.sum(eta_ref == lo) >= 3
+    s = gpu_solver(w, "fp64", variant=variant, beta=1.0, tol=0.0, maxit=20, final_orth=0,
+                   eta_min=lo, eta_max=hi)
+    Xd = to_dev(w.X0, s)
+    s.solve(Xd)
+    hist = s.history()
+    np.testing.assert_allclose(hist[:20, 4], eta_ref, rtol=1e-9)
+    np.testing.assert_allclose(hist[:, 2], [h.kkt for h in ref.history], rtol=1e-8)
+    s.close()
+    r = gpu_solver(w, "fp32", variant=variant, beta=1.0, tol=0.0, maxit=6, final_orth=0,
+                   engine="resident", eta_min=lo, eta_max=hi)
+    assert r.engine() == "resident"
+    r.solve(to_dev(w.X0, r))
+    hr = r.history()[:6, 4]
+    np.testing.assert_allclose(hr, eta_ref[:6], rtol=1e-3)
+    assert np.all(hr >= lo * (1 - 1e-12)) and np.all(hr <= hi * (1 + 1e-12))
+    r.close()
+    bs = BatchSolver([w.A], [w.X0], variant=variant, beta=1.0, tol=0.0, maxit=6, eta_min=lo,
+                     eta_max=hi)
+    infos = bs.solve()
+    assert infos[0].iters == 6 and lo * (1 - 1e-12) <= infos[0].eta <= hi * (1 + 1e-12)
+    bs.close()
+
+
 # ---------------------------------------------------------------- single kernels, entry by entry
 
 

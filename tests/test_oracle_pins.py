@@ -872,3 +872,33 @@ def test_cholesky_qr_factor_recovers_a_planted_triangle():
     R0 = np.triu(np.random.default_rng(18).standard_normal((6, 6)))
     R0[np.diag_indices(6)] = np.abs(R0[np.diag_indices(6)]) + 0.5
     np.testing.assert_allclose(ok.cholesky_qr_factor(Q @ R0), R0, rtol=1e-12, atol=1e-13)
+
+
+def test_step_size_interval_of_width_zero_is_the_constant_rule():
+    """eta^k clamped to [eta_min, eta_max] with eta_min = eta_max = gamma takes eta = gamma at every
+    iteration, eta0 included, whatever the BB rule proposes: the run is the constant rule
+    eta_C = gamma of Section 5.1, iterate for iterate."""
+    w = workload_dense_trace(120, 6)
+    obj = oo.TraceObjective(w.A)
+    gamma = 30.0
+    for variant in ("plam", "pcal"):
+        a = op.solve(obj, w.X0, variant=variant, beta=1.0, eta_rule="abb", tol=0.0, maxit=25,
+                     eta_min=gamma, eta_max=gamma)
+        b = op.solve(obj, w.X0, variant=variant, beta=1.0, eta_rule="const", gamma=gamma, tol=0.0,
+                     maxit=25)
+        assert not a.diverged and len(a.history) == 26
+        assert np.array_equal(a.X, b.X)
+        assert all(h.eta == gamma for h in a.history[:-1])   # the last record takes no step
+
+
+def test_step_size_interval_bounds_every_step():
+    """A lower bound eta_min caps the step 1/eta^k: every recorded eta lies in the interval, and the
+    bound binds on some steps of this run (ABB proposes smaller eta there)."""
+    w = workload_dense_trace(120, 6)
+    obj = oo.TraceObjective(w.A)
+    free = op.solve(obj, w.X0, variant="pcal", beta=1.0, tol=0.0, maxit=40)
+    etas = np.array([h.eta for h in free.history[:40]])
+    lo = float(np.median(etas))
+    r = op.solve(obj, w.X0, variant="pcal", beta=1.0, tol=0.0, maxit=40, eta_min=lo)
+    got = np.array([h.eta for h in r.history[:40]])
+    assert np.all(got >= lo) and np.sum(got == lo) >= 5
