@@ -198,6 +198,10 @@ typedef struct {
   double kkt_orth;      /* relative KKT after the final orthonormalisation (likewise; NaN when
                            p x 16 storage-type values exceed 227 KB of shared memory) */
   double feas_orth;     /* ||Q^T Q - I||_F of the orthonormalised output (NaN with orth_metrics off) */
+  double ms_iterations; /* plam_solve: device time of the iterations in ms (CUDA events on the handle's
+                           stream; the kernel groups inside them: plam_time_kernels); NaN elsewhere */
+  double ms_orth;       /* plam_solve: device time of the final orthonormalisation and its metrics in
+                           ms (the paper's "Orth" category; 0 without one); NaN elsewhere */
 } plam_info_t;
 
 typedef struct plam_handle_s* plam_handle_t;
@@ -355,8 +359,8 @@ plam_status_t plam_batch_create(plam_batch_t* b, const plam_batch_problem_t* pro
                                 const plam_params_t* prm, void* stream);
 /* Solves every problem; infos (host, count entries, may be NULL) receives each
  * problem's result in the layout of plam_info_t (status PLAM_OK when it
- * converged; f_orth and kkt_orth are NaN).  Returns PLAM_OK unless a CUDA call
- * failed. */
+ * converged; f_orth, kkt_orth and the timings are NaN).  Returns PLAM_OK unless
+ * a CUDA call failed. */
 plam_status_t plam_batch_solve(plam_batch_t b, plam_info_t* infos);
 /* The autotuner: times `iters` iterations of every problem for each row-block
  * height of the kernel's tiles (64, 128, 256) from the current X (restored

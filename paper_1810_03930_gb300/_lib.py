@@ -80,7 +80,8 @@ class plam_info_t(C.Structure):
     _fields_ = [("iters", C.c_int), ("status", C.c_int), ("converged", C.c_int), ("pad_", C.c_int),
                 ("f", C.c_double), ("kkt_rel", C.c_double), ("feas", C.c_double),
                 ("eta", C.c_double), ("K0", C.c_double), ("eta0", C.c_double),
-                ("f_orth", C.c_double), ("kkt_orth", C.c_double), ("feas_orth", C.c_double)]
+                ("f_orth", C.c_double), ("kkt_orth", C.c_double), ("feas_orth", C.c_double),
+                ("ms_iterations", C.c_double), ("ms_orth", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}

@@ -148,6 +148,7 @@ struct plam_handle_s {
   void* qtmp = nullptr;     // n x p work of Problem 4's gradient (A X before the product with B)
   void* xprev = nullptr;    // MOptQR: the previous iterate (S = X - X_prev), leading dimension ldw
   void* vbuf = nullptr;     // MOptQR: the retraction's output before it is copied back to X
+  cudaEvent_t tev[3] = {nullptr, nullptr, nullptr};   // plam_solve's phase timing
 };
 
 namespace {
@@ -499,6 +500,7 @@ plam_status_t read_state(plam_handle_s* h, plam_info_t* info, int* stop) {
   const DevState& s = *h->st_host;
   if (stop) *stop = s.stop;
   if (info) {
+    info->ms_iterations = info->ms_orth = NAN;
     info->iters = s.k;
     info->converged = (s.stop == kConverged);
     info->f = s.f;
@@ -554,6 +556,8 @@ void free_handle(plam_handle_s* h) {
   if (h->info_host) cudaFreeHost(h->info_host);
   if (h->scal_host) cudaFreeHost(h->scal_host);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (cudaEvent_t e : h->tev)
+    if (e) cudaEventDestroy(e);
   delete h;
 }
 
@@ -1124,6 +1128,10 @@ static plam_status_t solve_impl(plam_handle_t h, void* X, int64_t ldx, double* X
   const int lambda2 = (variant == PLAM_VARIANT_PCAL && h->prm.lambda_rule == PLAM_LAMBDA2);
   plam_status_t st = reset_state(h);
   if (st != PLAM_OK) return st;
+  if (!h->tev[0]) {
+    for (int i = 0; i < 3; ++i) CK(cudaEventCreate(&h->tev[i]));
+  }
+  CK(cudaEventRecord(h->tev[0], h->stream));
   // a user gradient runs on the host between the kernels, and MOptQR's retraction checks its
   // Cholesky factorisation on the host: no graph capture
   const int gi = (h->obj.kind == PLAM_OBJ_CALLBACK || variant == PLAM_VARIANT_MOPTQR)
@@ -1221,9 +1229,16 @@ static plam_status_t solve_impl(plam_handle_t h, void* X, int64_t ldx, double* X
   nvtxRangePushA("plam_solve: final orthonormalisation");
   plam_info_t tmp;
   plam_info_t* inf = info ? info : &tmp;
+  CK(cudaEventRecord(h->tev[1], h->stream));
   st = read_state(h, inf, &stop);
   if (st != PLAM_OK) return st;
   inf->f_orth = inf->kkt_orth = inf->feas_orth = NAN;
+  {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->tev[0], h->tev[1]));
+    inf->ms_iterations = ms;
+    inf->ms_orth = 0.0;
+  }
   if (stop == kDiverged) return PLAM_ERR_DIVERGED;
   if (h->prm.final_orth > 0 && Xout) {
     double feas = NAN;
@@ -1246,6 +1261,11 @@ static plam_status_t solve_impl(plam_handle_t h, void* X, int64_t ldx, double* X
       st = post_orth_metrics<float>(h, Qf, h->ldw, &inf->f_orth, &inf->kkt_orth);
     }
     if (st != PLAM_OK) return st;
+    CK(cudaEventRecord(h->tev[2], h->stream));
+    CK(cudaEventSynchronize(h->tev[2]));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->tev[1], h->tev[2]));
+    inf->ms_orth = ms;
   }
   return stop == kConverged ? PLAM_OK : PLAM_ERR_NOT_CONVERGED;
 }
@@ -1675,7 +1695,10 @@ plam_status_t plam_batch_solve(plam_batch_t b, plam_info_t* infos) {
   }
   CK(cudaGraphLaunch(b->graph, b->stream));
   CK(cudaStreamSynchronize(b->stream));
-  if (infos) memcpy(infos, b->info_host, b->count * sizeof(plam_info_t));
+  if (infos) {
+    memcpy(infos, b->info_host, b->count * sizeof(plam_info_t));
+    for (int i = 0; i < b->count; ++i) infos[i].ms_iterations = infos[i].ms_orth = NAN;
+  }
   return PLAM_OK;
 }
 

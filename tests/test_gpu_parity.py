@@ -889,3 +889,23 @@ def test_feasibility_blow_up_stops_the_run_as_diverged():
     st, k10, h10 = out[10.0]
     assert k10 < out[0.0][1]
     assert h10[-1, 3] > 10.0 and np.all(h10[:-1, 3] <= 10.0)
+
+
+def test_solve_reports_phase_timings():
+    """plam_info_t carries the device time of the iterations and of the final orthonormalisation
+    (the paper's "Orth" category) measured with CUDA events; 0 for Orth without one, NaN after a
+    single step."""
+    w = workload_dense_trace(500, 20)
+    s = gpu_solver(w, "fp32", variant="pcal", beta=1.0, tol=1e-6, maxit=500, final_orth=1,
+                   engine="graph")
+    Qd = s.new_matrix(dtype=torch.float64)
+    st, info = s.solve(to_dev(w.X0, s), Qd)
+    assert st == 0 and info.ms_iterations > 0.0 and info.ms_orth > 0.0
+    s.close()
+    s = gpu_solver(w, "fp32", variant="pcal", beta=1.0, tol=1e-6, maxit=500, final_orth=0,
+                   engine="graph")
+    st, info = s.solve(to_dev(w.X0, s))
+    assert info.ms_iterations > 0.0 and info.ms_orth == 0.0
+    st, info = s.step(to_dev(w.X0, s))
+    assert math.isnan(info.ms_iterations) and math.isnan(info.ms_orth)
+    s.close()
