@@ -32,6 +32,7 @@
 // M is symmetric, so column i of M is row i.
 #include <type_traits>
 
+#include "exact_sum.cuh"
 #include "plam_device.cuh"
 
 namespace plam {
@@ -153,17 +154,9 @@ gram_partial_kernel(int64_t n, int p, const Tin* __restrict__ X, int64_t ldx, co
 }
 
 // The FP64 Gram X^T X of a float X (the final orthonormalisation's, and MOptQR's retraction's)
-// without FP64 multiplies: GB300 executes FP64 at 1/64 of the FP32 rate, so each product is
-// formed exactly in FP32 arithmetic, x y = h + r with h = fl(x y), r = fma(x, y, -h)
-// (TwoProduct), and summed as in Ogita, Rump and Oishi's Dot2: (s, q) = TwoSum(s, h) (exact),
-// with the TwoSum errors q and the product errors r in two separate float sums (added together
-// they lose r against the much larger q, and the product errors of squares are not centred: a
-// diagonal of X^T X then drifts low by a few u^2, u = 2^-24).  Every kExactFlush rows a thread
-// adds its three float sums into double totals, so a segment of 64 products carries an error of
-// order u^2 of its magnitude, and the segments are added in FP64.  Same tiles, stages and partial
-// layout as gram_partial_kernel (B only: G is not used).
-constexpr int kExactFlush = 64;   // rows per float segment of the exact Gram
-
+// without FP64 multiplies: each product is formed exactly in FP32 arithmetic and summed in the
+// three levels of exact_sum.cuh (a double addition every 1024 rows).  Same tiles, stages and
+// partial layout as gram_partial_kernel (B only: G is not used).
 // Tin = double (the feasibility report of a double Q): each entry is split into float parts
 // q = q_hi + q_lo (about 48 bits), q_hi q_hi' is formed exactly and the cross terms
 // q_hi q_lo' + q_lo q_hi' in FP32 (q_lo q_lo' is below 2^-48 of the product and dropped).
@@ -190,13 +183,12 @@ gram_partial_exact_kernel(int64_t n, int p, const Tin* __restrict__ X, int64_t l
   const int tx = t & 15, ty = t >> 4;
   const int kk = t & (kKStep - 1);
   const int cb = t / kKStep;
-  float hs[4][4], he[4][4], hr[4][4];
-  double tot[4][4];
+  ExactAcc acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) { hs[u][v] = 0.f; he[u][v] = 0.f; hr[u][v] = 0.f; tot[u][v] = 0.0; }
-  int since = 0;
+    for (int v = 0; v < 4; ++v) exact_zero(acc[u][v]);
+  int since = 0, segs = 0;
 
   for (int64_t k0 = r0; k0 < r1; k0 += kKStep) {
     const int64_t row = k0 + kk;
@@ -238,27 +230,22 @@ gram_partial_exact_kernel(int64_t n, int p, const Tin* __restrict__ X, int64_t l
           const float h = __fmul_rn(a[u], b[v]);
           float r = __fmaf_rn(a[u], b[v], -h);                // x y - h, exact
           if constexpr (kSplit) r = __fadd_rn(r, __fmaf_rn(al[u], b[v], __fmul_rn(a[u], bl[v])));
-          const float sn = __fadd_rn(hs[u][v], h);            // TwoSum(s, h)
-          const float bv = __fsub_rn(sn, hs[u][v]);
-          const float q2 = __fadd_rn(__fsub_rn(hs[u][v], __fsub_rn(sn, bv)), __fsub_rn(h, bv));
-          hs[u][v] = sn;
-          he[u][v] = __fadd_rn(he[u][v], q2);
-          hr[u][v] = __fadd_rn(hr[u][v], r);
+          exact_add(acc[u][v], h, r);
         }
     }
     __syncthreads();
     since += kKStep;
-    if (since >= kExactFlush) {
+    if (since >= kExactSeg) {
+      since = 0;
+      const bool block = ++segs == kExactSeg2;
+      if (block) segs = 0;
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          tot[u][v] += (double)hs[u][v] + ((double)he[u][v] + (double)hr[u][v]);
-          hs[u][v] = 0.f;
-          he[u][v] = 0.f;
-          hr[u][v] = 0.f;
+          exact_seg(acc[u][v]);
+          if (block) exact_block(acc[u][v]);
         }
-      since = 0;
     }
   }
   const size_t cstride = (size_t)2 * p * p;
@@ -269,8 +256,7 @@ gram_partial_exact_kernel(int64_t n, int p, const Tin* __restrict__ X, int64_t l
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const int j = j0 + ty + 16 * v;
-      if (i < p && j < p)
-        out[(size_t)j * p + i] = tot[u][v] + ((double)hs[u][v] + ((double)he[u][v] + (double)hr[u][v]));
+      if (i < p && j < p) out[(size_t)j * p + i] = exact_value(acc[u][v]);
     }
   }
 }

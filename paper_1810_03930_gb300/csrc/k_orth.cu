@@ -14,6 +14,7 @@
 // needs rows k <= c.
 #include <type_traits>
 
+#include "exact_sum.cuh"
 #include "plam_device.cuh"
 
 namespace plam {
@@ -383,20 +384,31 @@ apply_rinv_kernel(int64_t n, int p, const T* __restrict__ X, int64_t ldx, const 
   }
 }
 
+// Z = R^{-1} as two float planes z = z_hi + z_lo (z_lo = fl(z - z_hi): the pair carries z to
+// about 2^-48), written once into scratch for the FP64-free Q = X Z below.
+__global__ void split_z_kernel(int p, const double* __restrict__ Z, float* __restrict__ Zh,
+                               float* __restrict__ Zl) {
+  const size_t total = (size_t)p * p;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const double z = Z[e];
+    const float zh = (float)z;
+    Zh[e] = zh;
+    Zl[e] = (float)(z - (double)zh);
+  }
+}
+
 // Q = X Z for a float X without FP64 multiplies (GB300 executes FP64 at 1/64 of the FP32 rate):
-// each entry of Z is split into float parts z = z_hi + z_lo (z_lo = fl(z - z_hi), so the pair
-// carries z to about 2^-48), x z_hi is formed exactly (TwoProduct: h + r), x z_lo in FP32 (a
-// term 2^-24 smaller), and the sum runs as Dot2 (TwoSum of h into s; the TwoSum errors and the
-// product terms r + x z_lo in two separate float sums, see the exact Gram), added into double
-// totals every 64 terms.  Same tiles and triangular skipping as apply_rinv_kernel.
+// x z_hi is formed exactly (TwoProduct: h + r), x z_lo in FP32 (a term 2^-24 smaller), and the
+// terms are summed in the three levels of exact_sum.cuh.  Same tiles and triangular skipping as
+// apply_rinv_kernel; Z arrives split into float planes (split_z_kernel).
 template <typename To>
 __global__ void __launch_bounds__(kThreads, 1)
 apply_rinv_exact_kernel(int64_t n, int p, const float* __restrict__ X, int64_t ldx,
-                        const double* __restrict__ Z, To* __restrict__ Q, int64_t ldq,
-                        const DevState* __restrict__ st) {
+                        const float* __restrict__ Zhp, const float* __restrict__ Zlp,
+                        To* __restrict__ Q, int64_t ldq, const DevState* __restrict__ st) {
   if (st != nullptr && st->stop != kRunning) return;
   constexpr int KS = 16;
-  constexpr int kFlushK = 64;
   const int64_t r0 = (int64_t)blockIdx.x * kTile;
   const int c0 = blockIdx.y * kTile;
   __shared__ float Xs[KS][kTile];
@@ -404,14 +416,13 @@ apply_rinv_exact_kernel(int64_t n, int p, const float* __restrict__ X, int64_t l
   __shared__ float Zl[kTile][KS + 1];
   const int t = threadIdx.x;
   const int tx = t & 15, ty = t >> 4;
-  float hs[4][4], he[4][4], hr[4][4];
-  double tot[4][4];
+  ExactAcc acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) { hs[u][v] = 0.f; he[u][v] = 0.f; hr[u][v] = 0.f; tot[u][v] = 0.0; }
+    for (int v = 0; v < 4; ++v) exact_zero(acc[u][v]);
   const int kend = min(p, c0 + kTile);
-  int since = 0;
+  int since = 0, segs = 0;
   for (int k0 = 0; k0 < kend; k0 += KS) {
     {
       const int r = t & (kTile - 1);
@@ -430,10 +441,9 @@ apply_rinv_exact_kernel(int64_t n, int p, const float* __restrict__ X, int64_t l
       for (int s = 0; s < kTile * KS / kThreads; ++s) {
         const int c = t / KS + (kThreads / KS) * s;
         const int cc = c0 + c;
-        const double z = (kr < p && cc < p && kr <= cc) ? Z[kr + (size_t)cc * p] : 0.0;
-        const float zh = (float)z;
-        Zh[c][q] = zh;
-        Zl[c][q] = (float)(z - (double)zh);
+        const bool ok = kr < p && cc < p && kr <= cc;
+        Zh[c][q] = ok ? Zhp[kr + (size_t)cc * p] : 0.f;
+        Zl[c][q] = ok ? Zlp[kr + (size_t)cc * p] : 0.f;
       }
     }
     __syncthreads();
@@ -457,29 +467,23 @@ apply_rinv_exact_kernel(int64_t n, int p, const float* __restrict__ X, int64_t l
         for (int u = 0; u < 4; ++u) {
           const float h = __fmul_rn(a[u], bh[v]);
           const float r = __fmaf_rn(a[u], bh[v], -h);          // x z_hi - h, exact
-          const float m = __fmul_rn(a[u], bl[v]);
-          const float sn = __fadd_rn(hs[u][v], h);             // TwoSum(s, h)
-          const float bv = __fsub_rn(sn, hs[u][v]);
-          const float q2 = __fadd_rn(__fsub_rn(hs[u][v], __fsub_rn(sn, bv)), __fsub_rn(h, bv));
-          hs[u][v] = sn;
-          he[u][v] = __fadd_rn(he[u][v], q2);
-          hr[u][v] = __fadd_rn(hr[u][v], __fadd_rn(r, m));
+          exact_add(acc[u][v], h, __fmaf_rn(a[u], bl[v], r));  // + x z_lo
         }
       }
     }
     __syncthreads();
     since += KS;
-    if (since >= kFlushK) {
+    if (since >= kExactSeg) {
+      since = 0;
+      const bool block = ++segs == kExactSeg2;
+      if (block) segs = 0;
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          tot[u][v] += (double)hs[u][v] + ((double)he[u][v] + (double)hr[u][v]);
-          hs[u][v] = 0.f;
-          he[u][v] = 0.f;
-          hr[u][v] = 0.f;
+          exact_seg(acc[u][v]);
+          if (block) exact_block(acc[u][v]);
         }
-      since = 0;
     }
   }
 #pragma unroll
@@ -489,9 +493,7 @@ apply_rinv_exact_kernel(int64_t n, int p, const float* __restrict__ X, int64_t l
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int64_t r = r0 + tx + 16 * u;
-      if (r < n)
-        Q[r + (int64_t)c * ldq] =
-            (To)(tot[u][v] + ((double)hs[u][v] + ((double)he[u][v] + (double)hr[u][v])));
+      if (r < n) Q[r + (int64_t)c * ldq] = (To)exact_value(acc[u][v]);
     }
   }
 }
@@ -564,25 +566,45 @@ int cholesky_inverse_launches(int p) {
   return nbt + 2 * (nbt - 1) + 2 * levels + 1;
 }
 
+// scratch: p^2 doubles (the float planes of Z for a float X; unused for a double X).
+static cudaError_t launch_split_z(int p, const double* Z, double* scratch, cudaStream_t s) {
+  int blocks = (int)(((size_t)p * p + 255) / 256);
+  if (blocks > 2048) blocks = 2048;
+  float* zh = reinterpret_cast<float*>(scratch);
+  split_z_kernel<<<blocks, 256, 0, s>>>(p, Z, zh, zh + (size_t)p * p);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_apply_rinv(int64_t n, int p, const T* X, int64_t ldx, const double* Z, double* Q,
-                              int64_t ldq, cudaStream_t s) {
+                              int64_t ldq, double* scratch, cudaStream_t s) {
   dim3 grid((unsigned)((n + kTile - 1) / kTile), (p + kTile - 1) / kTile);
-  if constexpr (std::is_same<T, float>::value)
-    apply_rinv_exact_kernel<double><<<grid, kThreads, 0, s>>>(n, p, X, ldx, Z, Q, ldq, nullptr);
-  else
+  if constexpr (std::is_same<T, float>::value) {
+    cudaError_t e = launch_split_z(p, Z, scratch, s);
+    if (e != cudaSuccess) return e;
+    const float* zh = reinterpret_cast<const float*>(scratch);
+    apply_rinv_exact_kernel<double><<<grid, kThreads, 0, s>>>(n, p, X, ldx, zh, zh + (size_t)p * p,
+                                                              Q, ldq, nullptr);
+  } else {
     apply_rinv_kernel<T, double><<<grid, kThreads, 0, s>>>(n, p, X, ldx, Z, Q, ldq, nullptr);
+  }
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_apply_rinv_same(int64_t n, int p, const T* X, int64_t ldx, const double* Z, T* Q,
-                                   int64_t ldq, const DevState* st, cudaStream_t s) {
+                                   int64_t ldq, double* scratch, const DevState* st,
+                                   cudaStream_t s) {
   dim3 grid((unsigned)((n + kTile - 1) / kTile), (p + kTile - 1) / kTile);
-  if constexpr (std::is_same<T, float>::value)
-    apply_rinv_exact_kernel<float><<<grid, kThreads, 0, s>>>(n, p, X, ldx, Z, Q, ldq, st);
-  else
+  if constexpr (std::is_same<T, float>::value) {
+    cudaError_t e = launch_split_z(p, Z, scratch, s);
+    if (e != cudaSuccess) return e;
+    const float* zh = reinterpret_cast<const float*>(scratch);
+    apply_rinv_exact_kernel<float><<<grid, kThreads, 0, s>>>(n, p, X, ldx, zh, zh + (size_t)p * p,
+                                                             Q, ldq, st);
+  } else {
     apply_rinv_kernel<T, T><<<grid, kThreads, 0, s>>>(n, p, X, ldx, Z, Q, ldq, st);
+  }
   return cudaGetLastError();
 }
 
@@ -595,14 +617,14 @@ cudaError_t launch_feas(int p, const double* B, double* col, double* out, cudaSt
 }
 
 template cudaError_t launch_apply_rinv<float>(int64_t, int, const float*, int64_t, const double*,
-                                              double*, int64_t, cudaStream_t);
+                                              double*, int64_t, double*, cudaStream_t);
 template cudaError_t launch_apply_rinv<double>(int64_t, int, const double*, int64_t, const double*,
-                                               double*, int64_t, cudaStream_t);
+                                               double*, int64_t, double*, cudaStream_t);
 template cudaError_t launch_apply_rinv_same<float>(int64_t, int, const float*, int64_t,
-                                                   const double*, float*, int64_t, const DevState*,
-                                                   cudaStream_t);
+                                                   const double*, float*, int64_t, double*,
+                                                   const DevState*, cudaStream_t);
 template cudaError_t launch_apply_rinv_same<double>(int64_t, int, const double*, int64_t,
-                                                    const double*, double*, int64_t,
+                                                    const double*, double*, int64_t, double*,
                                                     const DevState*, cudaStream_t);
 
 }  // namespace plam

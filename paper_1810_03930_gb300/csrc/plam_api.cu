@@ -366,8 +366,8 @@ plam_status_t moptqr_retract(plam_handle_s* h, T* X, int64_t ldx, cudaStream_t s
                                       h->rows_per_chunk, h->nchunks, h->part64, h->st, s)));
   CK(launch_gram_reduce<double>(p, h->nchunks, 0, h->part64, h->B, nullptr, s));
   CK(launch_cholesky_inverse(p, h->B, h->W, h->Z, h->info, s));
-  CK(launch_apply_rinv_same<T>(h->n, p, (const T*)h->vbuf, h->ldw, h->Z, X, ldx, h->st, s));
-  *nk += 4 + cholesky_inverse_launches(p);
+  CK(launch_apply_rinv_same<T>(h->n, p, (const T*)h->vbuf, h->ldw, h->Z, X, ldx, h->W, h->st, s));
+  *nk += 4 + cholesky_inverse_launches(p) + (sizeof(T) == 4 ? 1 : 0);
   return PLAM_OK;
 }
 
@@ -593,15 +593,15 @@ plam_status_t orthonormalize_impl(plam_handle_s* h, const T* X, int64_t ldx, dou
     }
     if (pass == 0) {
       if (passes == 1) {
-        CK(launch_apply_rinv<T>(h->n, p, X, ldx, h->Z, Xout, ldo, s));
+        CK(launch_apply_rinv<T>(h->n, p, X, ldx, h->Z, Xout, ldo, h->W, s));
       } else {
-        CK(launch_apply_rinv<T>(h->n, p, X, ldx, h->Z, h->Qtmp, h->ldw, s));
+        CK(launch_apply_rinv<T>(h->n, p, X, ldx, h->Z, h->Qtmp, h->ldw, h->W, s));
         src64 = h->Qtmp;
       }
     } else {
-      CK(launch_apply_rinv<double>(h->n, p, src64, h->ldw, h->Z, Xout, ldo, s));
+      CK(launch_apply_rinv<double>(h->n, p, src64, h->ldw, h->Z, Xout, ldo, h->W, s));
     }
-    h->launches += 1;
+    h->launches += (pass == 0 && sizeof(T) == 4) ? 2 : 1;   // a float X: split Z, then apply
   }
   if (feas) {
     CK(launch_gram_report(h->n, p, Xout, ldo, h->rows_per_chunk, h->nchunks, h->part64, s));

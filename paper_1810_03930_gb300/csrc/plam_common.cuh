@@ -169,14 +169,17 @@ cudaError_t launch_stencil_grad(int nx, int ny, int nz, int p, const T* V, const
 cudaError_t launch_cholesky_inverse(int p, const double* B, double* W, double* Z, int* info,
                                     cudaStream_t s);
 int cholesky_inverse_launches(int p);   // kernels launch_cholesky_inverse launches
+// scratch: p^2 doubles of workspace (a float X: Z split into two float planes; the Cholesky
+// workspace W is free once Z is formed).
 template <typename T>
 cudaError_t launch_apply_rinv(int64_t n, int p, const T* X, int64_t ldx, const double* Z,
-                              double* Q, int64_t ldq, cudaStream_t s);
+                              double* Q, int64_t ldq, double* scratch, cudaStream_t s);
 // The same product written in the storage type (MOptQR's retraction X <- V R^{-1}); st (may
 // be null): skipped once the run has stopped.
 template <typename T>
 cudaError_t launch_apply_rinv_same(int64_t n, int p, const T* X, int64_t ldx, const double* Z, T* Q,
-                                   int64_t ldq, const DevState* st, cudaStream_t s);
+                                   int64_t ldq, double* scratch, const DevState* st,
+                                   cudaStream_t s);
 // out[0] = ||B - I||_F (p x p, FP64); col: p doubles of per-column sums.
 cudaError_t launch_feas(int p, const double* B, double* col, double* out, cudaStream_t s);
 
