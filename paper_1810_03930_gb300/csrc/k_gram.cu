@@ -17,9 +17,10 @@
 // gram_reduce_kernel: B and C (double) from the partials, summed over chunks
 // in chunk order (bitwise reproducible; FP32 partials with Kahan compensation).
 //
-// gram_chunk_reduce_kernel + gram_finalize_kernel: the same reduction
-// (coalesced, fixed order) followed by the p x p part of one iteration (one
-// CTA per row i of the symmetric matrices):
+// gram_chunk_reduce_kernel, gram_tile_finalize_kernel, gram_row_finalize_kernel:
+// the same reduction (coalesced, fixed order; at large p inside the tile kernel)
+// followed by the p x p part of one iteration, on 32 x 32 tile pairs of the
+// symmetric matrices, then per row i:
 //   Lambda0 = Psi(C)                                  eq. (Lambda1)
 //   d_i = diag(X^T grad_X L_beta(X, Lambda0))_i        eq. (lambda2)
 //       = C_ii - sum_k B_ik Lambda0_ik + beta (sum_k B_ik^2 - B_ii)
@@ -279,92 +280,297 @@ __global__ void gram_reduce_kernel(int p, int nchunks, int with_g, const T* __re
   }
 }
 
-// Cross-chunk reduction of the partial Grams, coalesced: each CTA owns 32
-// consecutive entries of the 2p x p partial layout (lane = entry), its 8 warps
-// sum the chunks c = w, w + 8, ... in increasing order, and the 8 warp sums
-// are added in warp order (bitwise reproducible).  Entries of the lower
-// triangle of B are never formed and are skipped.  red: 2p x p, double.
+// Cross-chunk reduction of the partial Grams, coalesced: each CTA owns 32 * kPer
+// entries of the 2p x p partial layout (lane + 32 q, q < kPer), its 8 warps sum the
+// chunks c = w, w + 8, ... in increasing order, and the 8 warp sums are added in
+// warp order (bitwise reproducible).  Entries of the lower triangle of B are never
+// formed and are skipped.  red: 2p x p, double.  kPer > 1 when the entries alone
+// give every SM several CTAs (a CTA per 32 entries is launch-bound at large p).
 constexpr int kRedWarps = 8;
 
-template <typename T>
+template <typename T, int kPer>
 __global__ void __launch_bounds__(32 * kRedWarps)
 gram_chunk_reduce_kernel(int p, int nchunks, const T* __restrict__ part, double* __restrict__ red,
                          const DevState* __restrict__ st) {
   if (st != nullptr && st->stop != kRunning) return;
-  __shared__ T ws[kRedWarps][32];
+  __shared__ T ws[kRedWarps][32 * kPer];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const size_t E = (size_t)2 * p * p;
-  const size_t e = (size_t)blockIdx.x * 32 + lane;
-  const bool live = e < E && !((int)(e / p) < p && (int)(e % p) > (int)(e / p));
-  T v = T(0);
-  if (live) {
-#pragma unroll 4
-    for (int c = w; c < nchunks; c += kRedWarps) v += part[(size_t)c * E + e];
+  const size_t e0 = (size_t)blockIdx.x * (32 * kPer) + lane;
+  // loads of dead entries read entry 0 of the chunk (always in bounds) and are not added:
+  // no branch around a load, so all of a thread's loads of one chunk are in flight together
+  unsigned live = 0;
+  T v[kPer];
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const size_t e = e0 + 32 * q;
+    if (e < E && !((int)(e / p) < p && (int)(e % p) > (int)(e / p))) live |= 1u << q;
+    v[q] = T(0);
   }
-  ws[w][lane] = v;
+#pragma unroll 2
+  for (int c = w; c < nchunks; c += kRedWarps) {
+    const T* src = part + (size_t)c * E;
+    T x[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) x[q] = src[(live >> q & 1u) ? e0 + 32 * q : 0];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) v[q] += (live >> q & 1u) ? x[q] : T(0);
+  }
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) ws[w][lane + 32 * q] = v[q];
   __syncthreads();
-  if (w == 0 && live) {
+  for (int t = threadIdx.x; t < 32 * kPer; t += blockDim.x) {
+    const size_t e = (size_t)blockIdx.x * (32 * kPer) + t;
+    if (e >= E || ((int)(e / p) < p && (int)(e % p) > (int)(e / p))) continue;
     T s = T(0);
 #pragma unroll
-    for (int i = 0; i < kRedWarps; ++i) s += ws[i][lane];
+    for (int i = 0; i < kRedWarps; ++i) s += ws[i][t];
     red[e] = (double)s;
   }
 }
 
-// p x p part of one iteration from the reduced Grams (one CTA per row i; B is
-// read through its upper triangle, B_ij = red[max(i,j) p + min(i,j)]).
-template <typename T>
-__global__ void __launch_bounds__(128)
-gram_finalize_kernel(int p, const double* __restrict__ red, double* __restrict__ Bout,
-                     double* __restrict__ L0out, T* __restrict__ Mt, T* __restrict__ L0t,
-                     double* __restrict__ feas_row, const DevState* __restrict__ st, IterParams prm) {
+// The p x p part of one iteration, on 32 x 32 tile pairs.  The CTA of tile pair (a, b),
+// a <= b, holds for rows i of tile a and columns j of tile b
+//   B_ij (B's upper triangle, as formed), C_ij and C_ji,
+// each summed over the chunks in chunk order (or read from the reduced Grams, nchunks = 1),
+// with every load coalesced along the partial layout's row index.  It writes
+//   Psi(C)_ij = (C_ij + C_ji) / 2 to L0t, and M_ij = Lambda_ij - beta (B_ij - delta_ij) to Mt
+//   (Lambda = Psi(C), or the dual ascent step; MOptQR: M_ij = C_ij, M = C^T in Mt's layout),
+// for row i and, mirrored, for row j (B, Psi(C), M and Lambda are symmetric), and the row
+// sums of B_ij Psi(C)_ij, B_ij^2 and (B_ij - delta_ij)^2 over its 32 columns, one slot per
+// (row, column tile): rowpart[(q nt + t) p + row].  A diagonal tile also records B_ii and C_ii
+// in dg = rowpart + 3 nt p.  gram_row_finalize_kernel then sums a row's slots in tile order:
+//   d_i = C_ii - sum_j B_ij Psi_ij + beta (sum_j B_ij^2 - B_ii)      eq. (lambda2)
+//   M_ii = (Psi_ii + d_i) - beta (B_ii - 1),  feas_row_i = sum_j (B_ij - delta_ij)^2.
+constexpr int kFinTile = 32;
+constexpr int kFinThreads = 256;
+
+// (a + b) / 2 = h + l exactly (TwoSum; halving is exact above the subnormal range).
+__device__ __forceinline__ float half_sum(float a, float b, float& l) {
+  float e;
+  const float s = two_sum(a, b, e);
+  l = 0.5f * e;
+  return 0.5f * s;
+}
+
+__device__ inline void decode_upper(int bx, int nt, int& a, int& b) {
+  int r = 0, rem = bx;
+  while (rem >= nt - r) { rem -= nt - r; ++r; }
+  a = r;
+  b = r + rem;
+}
+
+template <typename Tp, typename T>
+__global__ void __launch_bounds__(kFinThreads)
+gram_tile_finalize_kernel(int p, int nchunks, const Tp* __restrict__ part,
+                          double* __restrict__ rowpart, T* __restrict__ Mt, T* __restrict__ L0t,
+                          const DevState* __restrict__ st, IterParams prm) {
   if (st != nullptr && st->stop != kRunning) return;
-  extern __shared__ double sh[];
-  double* Brow = sh;          // B_ij
-  double* Lrow = sh + p;      // Psi(C)_ij
-  __shared__ double scratch[33];
-  __shared__ double cii;
-  const int i = blockIdx.x;
-  for (int j = threadIdx.x; j < p; j += blockDim.x) {
-    const double b = red[(size_t)max(i, j) * p + min(i, j)];
-    const double cij = red[(size_t)(p + j) * p + i];
-    const double cji = red[(size_t)(p + i) * p + j];
-    Brow[j] = b;
-    Lrow[j] = 0.5 * (cij + cji);
-    if (j == i) cii = cij;
+  __shared__ T sB[kFinTile][kFinTile + 1];    // B_ij   [i - i0][j - j0]
+  __shared__ T sC[kFinTile][kFinTile + 1];    // C_ij
+  __shared__ T sCt[kFinTile][kFinTile + 1];   // C_ji
+  const int nt = (p + kFinTile - 1) / kFinTile;
+  int a, b;
+  decode_upper(blockIdx.x, nt, a, b);
+  const bool diag = a == b;
+  const int i0 = a * kFinTile, j0 = b * kFinTile;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const size_t E = (size_t)2 * p * p;
+  constexpr int kQ = kFinTile / (kFinThreads / 32);
+  // thread (lane, w): B_ij and C_ij at i = i0 + lane, j = j0 + w + 8 q; C_ji at j = j0 + lane,
+  // i = i0 + w + 8 q (lane along the partial layout's row index in all three)
+  // entry q of a thread lies 8 q columns (8 q p elements) past its entry 0; a dead entry
+  // (ragged edge, or B's lower triangle in a diagonal tile) loads element 0 of the chunk and
+  // is not added: no branch around a load, so the 3 kQ loads of a chunk are in flight together
+  const size_t ob0 = (size_t)(j0 + w) * p + i0 + lane;        // B_ij,  j = j0 + w + 8 q
+  const size_t oc0 = (size_t)(p + j0 + w) * p + i0 + lane;    // C_ij
+  const size_t ot0 = (size_t)(p + i0 + w) * p + j0 + lane;    // C_ji,  i = i0 + w + 8 q
+  const size_t s8 = (size_t)8 * p;
+  unsigned mb = 0, mc = 0, mt = 0;
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) {
+    const int r = w + 8 * q;
+    if (i0 + lane < p && j0 + r < p && (!diag || lane <= r)) mb |= 1u << q;
+    if (i0 + lane < p && j0 + r < p) mc |= 1u << q;
+    if (!diag && i0 + r < p && j0 + lane < p) mt |= 1u << q;
+  }
+  Tp vb[kQ], vc[kQ], vt[kQ];
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) vb[q] = vc[q] = vt[q] = Tp(0);
+  for (int c = 0; c < nchunks; ++c) {
+    const Tp* src = part + (size_t)c * E;
+    Tp xb[kQ], xc[kQ], xt[kQ];
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      xb[q] = src[(mb >> q & 1u) ? ob0 + q * s8 : 0];
+      xc[q] = src[(mc >> q & 1u) ? oc0 + q * s8 : 0];
+      xt[q] = src[(mt >> q & 1u) ? ot0 + q * s8 : 0];
+    }
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      vb[q] += (mb >> q & 1u) ? xb[q] : Tp(0);
+      vc[q] += (mc >> q & 1u) ? xc[q] : Tp(0);
+      vt[q] += (mt >> q & 1u) ? xt[q] : Tp(0);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) {
+    const int r = w + 8 * q;
+    sB[lane][r] = (T)vb[q];
+    sC[lane][r] = (T)vc[q];
+    sCt[r][lane] = (T)vt[q];
   }
   __syncthreads();
-  double t1 = 0.0, t2 = 0.0, tf = 0.0;
-  for (int j = threadIdx.x; j < p; j += blockDim.x) {
-    const double bij = Brow[j];
-    t1 += bij * Lrow[j];
-    t2 += bij * bij;
-    const double e = bij - (j == i ? 1.0 : 0.0);
-    tf += e * e;
+  if (diag) {   // B's lower triangle and C_ji from the tile's own C
+    for (int t = threadIdx.x; t < kFinTile * kFinTile; t += kFinThreads) {
+      const int il = t / kFinTile, jl = t % kFinTile;
+      if (il > jl) sB[il][jl] = sB[jl][il];
+      sCt[il][jl] = sC[jl][il];
+    }
+    __syncthreads();
   }
-  const double s1 = block_sum(t1, scratch);
-  const double s2 = block_sum(t2, scratch);
-  const double sf = block_sum(tf, scratch);
   const double beta = prm.beta;
-  const double d = prm.lambda2 ? (cii - s1 + beta * (s2 - Brow[i])) : 0.0;
   const bool da = prm.lambda_da && prm.lam != nullptr;
   const bool da_first = da && (st == nullptr || st->k == 0);
-  for (int j = threadIdx.x; j < p; j += blockDim.x) {
-    const double delta = (j == i) ? 1.0 : 0.0;
-    double lam = Lrow[j] + delta * d;
-    if (da) {   // dual ascent (Algorithm 1's multiplier step) from Lambda^0 = Psi(C^0)
-      double* lp = prm.lam + j + (size_t)i * p;
-      lam = da_first ? Lrow[j] : *lp - beta * (Brow[j] - delta);
-      *lp = lam;
+  // FP32 storage: beta = bh + bl to 2^-48, and the entries of Mt and L0t in FP32 arithmetic
+  // (GB300 runs FP64 at 1/64 of the FP32 rate), each within about one rounding of its value
+  const float bh = (float)beta, bl = (float)(beta - (double)(float)beta);
+  // pass 0: row i = i0 + il, column j = j0 + jl; pass 1 (off-diagonal tiles): row j, column i
+  for (int pass = 0; pass < (diag ? 1 : 2); ++pass) {
+    for (int t = threadIdx.x; t < kFinTile * kFinTile; t += kFinThreads) {
+      const int il = pass == 0 ? t / kFinTile : t % kFinTile;
+      const int jl = pass == 0 ? t % kFinTile : t / kFinTile;
+      const int i = i0 + il, j = j0 + jl;
+      if (i >= p || j >= p) continue;
+      const int row = pass == 0 ? i : j, col = pass == 0 ? j : i;
+      const T bij = sB[il][jl];
+      const T crc = pass == 0 ? sC[il][jl] : sCt[il][jl];   // C_row,col
+      const T ccr = pass == 0 ? sCt[il][jl] : sC[il][jl];   // C_col,row
+      T m, psi_out;
+      if constexpr (std::is_same<T, float>::value) {
+        float pl;
+        const float ph = half_sum(crc, ccr, pl);   // Psi(C)_ij = ph + pl exactly
+        psi_out = ph;
+        const float e = __fsub_rn(bij, row == col ? 1.f : 0.f);   // exact
+        if (prm.moptqr) {   // MOptQR (Table "cost"): R = G - X (G^T X), the product with C^T
+          m = crc;
+        } else if (da) {    // dual ascent (Algorithm 1's multiplier step), FP64 multiplier
+          double* lp = prm.lam + col + (size_t)row * p;
+          const double lam = da_first ? (double)ph + (double)pl : *lp - beta * (double)e;
+          *lp = lam;
+          m = (float)(lam - beta * (double)e);
+        } else {            // Lambda - beta (B - I) = (ph + pl) - (th + tl)
+          const float th = __fmul_rn(bh, e);
+          const float tl = fmaf(bh, e, -th) + bl * e;
+          m = __fadd_rn(__fsub_rn(ph, th), __fsub_rn(pl, tl));
+        }
+      } else {
+        const double psi = 0.5 * (crc + ccr);
+        const double delta = row == col ? 1.0 : 0.0;
+        double lam = psi;
+        if (da) {   // dual ascent (Algorithm 1's multiplier step) from Lambda^0 = Psi(C^0)
+          double* lp = prm.lam + col + (size_t)row * p;
+          lam = da_first ? psi : *lp - beta * (bij - delta);
+          *lp = lam;
+        }
+        // MOptQR (Table "cost"): R = G - X (G^T X), i.e. the product with C^T = G^T X
+        m = prm.moptqr ? crc : lam - beta * (bij - delta);
+        psi_out = psi;
+      }
+      Mt[col + (size_t)row * p] = m;
+      L0t[col + (size_t)row * p] = psi_out;
     }
-    // MOptQR (Table "cost"): R = G - X (G^T X), i.e. the product with C^T = G^T X
-    const double m = prm.moptqr ? red[(size_t)(p + j) * p + i] : lam - beta * (Brow[j] - delta);
-    Mt[j + (size_t)i * p] = (T)m;
-    L0t[j + (size_t)i * p] = (T)Lrow[j];
-    if (Bout) Bout[j + (size_t)i * p] = Brow[j];
-    if (L0out) L0out[j + (size_t)i * p] = Lrow[j];
   }
-  if (threadIdx.x == 0) feas_row[i] = sf;
+  // row sums over the tile's 32 columns: threads 0..95 for rows i (three sums), 96..191 for
+  // rows j of an off-diagonal tile (its columns are the rows i of tile a).  FP32 storage: each
+  // product split exactly (TwoProduct) and summed as Dot2 (exact_add), so the sum is as
+  // accurate as an FP64 one with FP32 arithmetic only
+  const int t = threadIdx.x;
+  const int side = t / (3 * kFinTile), q = (t / kFinTile) % 3, r = t % kFinTile;
+  if (side < (diag ? 1 : 2)) {
+    const int row = (side == 0 ? i0 : j0) + r;
+    if (row < p) {
+      double acc = 0.0;
+      if constexpr (std::is_same<T, float>::value) {
+        ExactAcc ea;
+        exact_zero(ea);
+        for (int k = 0; k < kFinTile; ++k) {
+          const int il = side == 0 ? r : k, jl = side == 0 ? k : r;
+          const float bij = sB[il][jl];
+          float x = bij, y = bij, lo = 0.f;
+          if (q == 0) {          // B_ij Psi(C)_ij, symmetric in i, j
+            float pl;
+            y = half_sum(sC[il][jl], sCt[il][jl], pl);
+            lo = bij * pl;
+          } else if (q == 2) {   // (B_ij - delta_ij)^2
+            x = y = __fsub_rn(bij, (i0 + il) == (j0 + jl) ? 1.f : 0.f);
+          }
+          const float h = __fmul_rn(x, y);
+          exact_add(ea, h, fmaf(x, y, -h) + lo);
+        }
+        acc = exact_value(ea);
+      } else {
+        for (int k = 0; k < kFinTile; ++k) {
+          const int il = side == 0 ? r : k, jl = side == 0 ? k : r;
+          const double bij = sB[il][jl];
+          double v;
+          if (q == 0) {
+            v = bij * (0.5 * (sC[il][jl] + sCt[il][jl]));   // B_ij Psi(C)_ij
+          } else if (q == 1) {
+            v = bij * bij;
+          } else {
+            const double e = bij - ((i0 + il) == (j0 + jl) ? 1.0 : 0.0);
+            v = e * e;
+          }
+          acc += v;
+        }
+      }
+      rowpart[((size_t)q * nt + (side == 0 ? b : a)) * p + row] = acc;
+    }
+  }
+  if (diag && t < kFinTile && i0 + t < p) {
+    double* dg = rowpart + (size_t)3 * nt * p;
+    dg[i0 + t] = (double)sB[t][t];
+    dg[p + i0 + t] = (double)sC[t][t];
+  }
+}
+
+// One warp per row: lane l sums the row's slots t = l, l + 32, ... in order, then a fixed
+// butterfly adds the 32 lane sums (bitwise reproducible).
+constexpr int kRowWarps = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kRowWarps)
+gram_row_finalize_kernel(int p, const double* __restrict__ rowpart, T* __restrict__ Mt,
+                         double* __restrict__ feas_row, const DevState* __restrict__ st,
+                         IterParams prm) {
+  if (st != nullptr && st->stop != kRunning) return;
+  const int i = blockIdx.x * kRowWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= p) return;
+  const int nt = (p + kFinTile - 1) / kFinTile;
+  double s1 = 0.0, s2 = 0.0, sf = 0.0;
+  for (int t = lane; t < nt; t += 32) {
+    s1 += rowpart[(size_t)t * p + i];
+    s2 += rowpart[((size_t)nt + t) * p + i];
+    sf += rowpart[((size_t)2 * nt + t) * p + i];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    sf += __shfl_xor_sync(0xffffffffu, sf, o);
+  }
+  if (lane != 0) return;
+  feas_row[i] = sf;
+  const bool da = prm.lambda_da && prm.lam != nullptr;
+  if (prm.lambda2 && !da && !prm.moptqr) {
+    const double* dg = rowpart + (size_t)3 * nt * p;
+    const double bii = dg[i], cii = dg[p + i];   // Psi(C)_ii = C_ii
+    const double beta = prm.beta;
+    const double d = cii - s1 + beta * (s2 - bii);
+    Mt[i + (size_t)i * p] = (T)((cii + d) - beta * (bii - 1.0));
+  }
 }
 
 // ---------------------------------------------------------------- launchers
@@ -406,26 +612,61 @@ cudaError_t launch_gram_reduce(int p, int nchunks, int with_g, const T* part, do
   return cudaGetLastError();
 }
 
+size_t gram_rowpart_doubles(int p) {
+  const int nt = (p + kFinTile - 1) / kFinTile;
+  return ((size_t)3 * nt + 2) * (size_t)p;
+}
+
 template <typename T>
-cudaError_t launch_gram_finalize(int p, int nchunks, const T* part, double* red, double* B,
-                                 double* L0, T* Mt, T* L0t, double* feas_row, const DevState* st,
+static cudaError_t launch_chunk_reduce(int p, int nchunks, const T* part, double* red,
+                                       const DevState* st, cudaStream_t s) {
+  const size_t E = (size_t)2 * p * p;
+  const size_t want = (size_t)8 * device_sm_count();   // CTAs enough to fill the SMs
+  if ((E + 255) / 256 >= want) {
+    gram_chunk_reduce_kernel<T, 8><<<(unsigned)((E + 255) / 256), 32 * kRedWarps, 0, s>>>(
+        p, nchunks, part, red, st);
+  } else if ((E + 127) / 128 >= want) {
+    gram_chunk_reduce_kernel<T, 4><<<(unsigned)((E + 127) / 128), 32 * kRedWarps, 0, s>>>(
+        p, nchunks, part, red, st);
+  } else {
+    gram_chunk_reduce_kernel<T, 1><<<(unsigned)((E + 31) / 32), 32 * kRedWarps, 0, s>>>(
+        p, nchunks, part, red, st);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gram_finalize(int p, int nchunks, const T* part, double* red, double* rowpart,
+                                 T* Mt, T* L0t, double* feas_row, const DevState* st,
                                  IterParams prm, cudaStream_t s, int stage) {
   cudaError_t e = cudaSuccess;
-  if (stage != 2) {
-    const size_t E = (size_t)2 * p * p;
-    gram_chunk_reduce_kernel<T><<<(unsigned)((E + 31) / 32), 32 * kRedWarps, 0, s>>>(p, nchunks,
-                                                                                   part, red, st);
-    e = cudaGetLastError();
+  const int nt = (p + kFinTile - 1) / kFinTile;
+  const unsigned tiles = (unsigned)(nt * (nt + 1) / 2);
+  // enough tile pairs to give every SM two CTAs: sum the chunks inside the tile kernel;
+  // otherwise reduce over the chunks first (all entries in parallel)
+  const bool fused = stage == 0 && tiles >= 2u * (unsigned)device_sm_count();
+  if (stage == 1 || (stage == 0 && !fused)) {
+    e = launch_chunk_reduce<T>(p, nchunks, part, red, st, s);
     if (e != cudaSuccess || stage == 1) return e;
   }
-  const size_t smem = (size_t)2 * p * sizeof(double);
-  if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(gram_finalize_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  gram_finalize_kernel<T><<<p, 128, smem, s>>>(p, red, B, L0, Mt, L0t, feas_row, st, prm);
+  if (fused)
+    gram_tile_finalize_kernel<T, T><<<tiles, kFinThreads, 0, s>>>(p, nchunks, part, rowpart, Mt,
+                                                                  L0t, st, prm);
+  else
+    gram_tile_finalize_kernel<double, T><<<tiles, kFinThreads, 0, s>>>(p, 1, red, rowpart, Mt,
+                                                                       L0t, st, prm);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  gram_row_finalize_kernel<T><<<(unsigned)((p + kRowWarps - 1) / kRowWarps), 32 * kRowWarps, 0,
+                                 s>>>(p, rowpart, Mt, feas_row, st, prm);
   return cudaGetLastError();
+}
+
+int gram_finalize_launches(int p, int stage) {
+  const int nt = (p + kFinTile - 1) / kFinTile;
+  const bool fused = stage == 0 && nt * (nt + 1) / 2 >= 2 * device_sm_count();
+  if (stage == 1) return 1;
+  return (stage == 0 && !fused) ? 3 : 2;
 }
 
 cudaError_t preload_gram_kernels() {
@@ -438,10 +679,17 @@ cudaError_t preload_gram_kernels() {
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_partial_exact_kernel<double>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_reduce_kernel<float>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_reduce_kernel<double>);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_finalize_kernel<float>);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_finalize_kernel<double>);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_chunk_reduce_kernel<float>);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_chunk_reduce_kernel<double>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_tile_finalize_kernel<float, float>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_tile_finalize_kernel<double, float>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_tile_finalize_kernel<double, double>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_row_finalize_kernel<float>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_row_finalize_kernel<double>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_chunk_reduce_kernel<float, 1>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_chunk_reduce_kernel<float, 4>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_chunk_reduce_kernel<float, 8>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_chunk_reduce_kernel<double, 1>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_chunk_reduce_kernel<double, 4>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gram_chunk_reduce_kernel<double, 8>);
   return e;
 }
 
@@ -458,11 +706,11 @@ template cudaError_t launch_gram_reduce<float>(int, int, int, const float*, doub
                                                cudaStream_t);
 template cudaError_t launch_gram_reduce<double>(int, int, int, const double*, double*, double*,
                                                 cudaStream_t);
-template cudaError_t launch_gram_finalize<float>(int, int, const float*, double*, double*, double*,
-                                                 float*, float*, double*, const DevState*,
-                                                 IterParams, cudaStream_t, int);
+template cudaError_t launch_gram_finalize<float>(int, int, const float*, double*, double*, float*,
+                                                 float*, double*, const DevState*, IterParams,
+                                                 cudaStream_t, int);
 template cudaError_t launch_gram_finalize<double>(int, int, const double*, double*, double*,
-                                                  double*, double*, double*, double*,
-                                                  const DevState*, IterParams, cudaStream_t, int);
+                                                  double*, double*, double*, const DevState*,
+                                                  IterParams, cudaStream_t, int);
 
 }  // namespace plam

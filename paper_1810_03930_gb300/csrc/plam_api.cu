@@ -78,9 +78,9 @@ struct plam_handle_s {
   int nchunks = 1;
   int64_t rows_per_chunk = 0;
   double* B = nullptr;      // p x p
-  double* L0 = nullptr;     // p x p
   double* C = nullptr;      // p x p scratch for plam_grams
   double* red = nullptr;    // 2p x p reduced Grams [B | C] of the iteration
+  double* rowpart = nullptr;   // row sums of the p x p step (gram_rowpart_doubles(p))
   void* Mt = nullptr;
   void* L0t = nullptr;
   double* feas_row = nullptr;
@@ -407,17 +407,19 @@ plam_status_t launch_iteration(plam_handle_s* h, T* X, int64_t ldx, int variant,
                                    (T*)h->part, h->st, s)));
   }
   if (ev) CK(cudaEventRecord(ev[2], s));
+  // the fixed count below takes two launches for this stage
   if (h->sharded) {
-    CK(launch_gram_finalize<T>(p, nch, (const T*)h->part, h->red, h->B, h->L0, (T*)h->Mt,
+    CK(launch_gram_finalize<T>(p, nch, (const T*)h->part, h->red, h->rowpart, (T*)h->Mt,
                                (T*)h->L0t, h->feas_row, h->st, ip, s, 1));
     plam_status_t as = shard_allreduce(h, h->red, (int64_t)2 * p * p, s, &k, h->st);
     if (as != PLAM_OK) return as;
-    CK(launch_gram_finalize<T>(p, nch, (const T*)h->part, h->red, h->B, h->L0, (T*)h->Mt,
+    CK(launch_gram_finalize<T>(p, nch, (const T*)h->part, h->red, h->rowpart, (T*)h->Mt,
                                (T*)h->L0t, h->feas_row, h->st, ip, s, 2));
-    k += 1;
+    k += gram_finalize_launches(p, 1) + gram_finalize_launches(p, 2) - 2;
   } else {
-    CK(launch_gram_finalize<T>(p, nch, (const T*)h->part, h->red, h->B, h->L0, (T*)h->Mt,
+    CK(launch_gram_finalize<T>(p, nch, (const T*)h->part, h->red, h->rowpart, (T*)h->Mt,
                                (T*)h->L0t, h->feas_row, h->st, ip, s));
+    k += gram_finalize_launches(p, 0) - 2;
   }
   if (ev) CK(cudaEventRecord(ev[3], s));
   int nrt = h->nrt, nct = h->nct;
@@ -543,8 +545,8 @@ plam_status_t step_common(plam_handle_t h, void* X, int64_t ldx, plam_info_t* in
 void free_handle(plam_handle_s* h) {
   if (!h) return;
   if (h->graph) cudaGraphExecDestroy(h->graph);
-  void* dev[] = {h->G, h->R[0], h->R[1], h->part, h->part64, h->B, h->L0, h->C, h->red, h->Mt, h->L0t,
-                 h->feas_row, h->colpart, h->totpart, h->sums, h->dsum, h->ticket, h->st, h->nubuf,
+  void* dev[] = {h->G, h->R[0], h->R[1], h->part, h->part64, h->B, h->C, h->red, h->rowpart, h->Mt,
+                 h->L0t, h->feas_row, h->colpart, h->totpart, h->sums, h->dsum, h->ticket, h->st, h->nubuf,
                  h->coef, h->hist,
                  h->rho, h->blk, h->y, h->fpart, h->W, h->Z, h->info, h->feas_dev, h->Qtmp,
                  h->dotpart, h->r_halo, h->r_blk, h->r_part, h->r_red, h->r_dots, h->r_dred,
@@ -950,9 +952,10 @@ plam_status_t create_impl(plam_handle_t* out, int64_t n, int64_t p, const plam_o
             alloc((void**)&h->tc_err, sizeof(int)) &&
             (!h->use_tc || alloc((void**)&h->msplit, (size_t)4 * h->tcu.ldm * p * sizeof(float))) &&
             alloc((void**)&h->part64, (size_t)h->nchunks * 2 * pp * sizeof(double)) &&
-            alloc((void**)&h->B, pp * sizeof(double)) && alloc((void**)&h->L0, pp * sizeof(double)) &&
+            alloc((void**)&h->B, pp * sizeof(double)) &&
             alloc((void**)&h->C, pp * sizeof(double)) && alloc(&h->Mt, pp * esz) &&
             alloc((void**)&h->red, 2 * pp * sizeof(double)) &&
+            alloc((void**)&h->rowpart, gram_rowpart_doubles((int)p) * sizeof(double)) &&
             alloc(&h->L0t, pp * esz) && alloc((void**)&h->feas_row, p * sizeof(double)) &&
             alloc(&h->colpart, (size_t)h->nrt * kColDots * p * esz) &&
             alloc(&h->totpart, (size_t)h->nrt * h->nct * kTotDots * esz) &&

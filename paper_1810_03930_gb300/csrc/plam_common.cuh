@@ -96,13 +96,18 @@ cudaError_t launch_gram_partial(int64_t n, int p, const Tin* X, int64_t ldx, con
 template <typename T>
 cudaError_t launch_gram_reduce(int p, int nchunks, int with_g, const T* part, double* B,
                                double* C, cudaStream_t s);
-// red: 2p x p doubles of scratch for the reduced Grams [B | C].  stage 0: the chunk
-// reduction into red and the p x p step from it; 1: the reduction only; 2: the p x p step
-// only (a row-sharded solve sums red over the ranks in between).
+// red: 2p x p doubles of scratch for the reduced Grams [B | C]; rowpart:
+// gram_rowpart_doubles(p) doubles of scratch for the row sums.  stage 0: the chunk
+// reduction and the p x p step (through red at small p, inside the tile kernel at
+// large p); 1: the reduction into red only; 2: the p x p step from red only (a
+// row-sharded solve sums red over the ranks in between).  gram_finalize_launches:
+// the kernels one call launches.
 template <typename T>
-cudaError_t launch_gram_finalize(int p, int nchunks, const T* part, double* red, double* B,
-                                 double* L0, T* Mt, T* L0t, double* feas_row, const DevState* st,
+cudaError_t launch_gram_finalize(int p, int nchunks, const T* part, double* red, double* rowpart,
+                                 T* Mt, T* L0t, double* feas_row, const DevState* st,
                                  IterParams prm, cudaStream_t s, int stage = 0);
+size_t gram_rowpart_doubles(int p);
+int gram_finalize_launches(int p, int stage);
 
 // Row sharding: out[i] = sum over r = 0 .. size-1, in that order, of in[r * count + i]
 // (in: the all-gathered buffers of every rank).  st (may be null): skipped once stopped.
