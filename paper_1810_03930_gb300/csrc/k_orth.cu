@@ -36,49 +36,59 @@ constexpr int kCB = 32;
 __global__ void __launch_bounds__(1024)
 chol_diag_kernel(int p, int j0, double* __restrict__ W, double* __restrict__ Z,
                  int* __restrict__ info) {
-  __shared__ double A[kCB][kCB + 1];
-  __shared__ double Zi[kCB][kCB + 1];
-  __shared__ double rpiv[kCB];   // reciprocals of the pivots, formed once
+  __shared__ double A[kCB][kCB + 1];    // W_jj, updated in place (upper triangle)
+  __shared__ double Rs[kCB][kCB + 1];   // R_jj, row by row
+  __shared__ double Zi[kCB][kCB + 1];   // R_jj^{-1}
+  __shared__ double rpiv[kCB];          // reciprocals of the pivots
   __shared__ int fail;
   if (*(volatile int*)info != 0) return;
   const int t = threadIdx.x;
   const int r = t & 31, c = t >> 5;
   const int nb = min(kCB, p - j0);
   A[r][c] = (r < nb && c < nb) ? W[(j0 + r) + (size_t)(j0 + c) * p] : 0.0;
+  Rs[r][c] = 0.0;
   if (t == 0) fail = 0;
   __syncthreads();
+  // right-looking: pivot j, then row j of R and the trailing update from the unscaled row j
+  // (R_jk = A_jk / R_jj, A_rc -= R_jr R_jc), two block barriers per step
   for (int j = 0; j < nb; ++j) {
     if (t == 0) {
       const double d = A[j][j];
       if (!(d > 0.0) || !isfinite(d)) {
         fail = j0 + j + 1;
       } else {
-        A[j][j] = sqrt(d);
-        rpiv[j] = 1.0 / A[j][j];
+        const double q = rsqrt(d);
+        rpiv[j] = q;
+        Rs[j][j] = d * q;
       }
     }
     __syncthreads();
     if (fail) break;
-    if (r == j && c > j && c < nb) A[j][c] *= rpiv[j];
-    __syncthreads();
-    if (r > j && c >= r && c < nb) A[r][c] -= A[j][r] * A[j][c];
+    const double q = rpiv[j];
+    if (r == j && c > j && c < nb) Rs[j][c] = A[j][c] * q;
+    if (r > j && c >= r && c < nb) A[r][c] -= (A[j][r] * q) * (A[j][c] * q);
     __syncthreads();
   }
   if (fail) {
     if (t == 0) *info = fail;
     return;
   }
-  if (t < nb) {   // column t of R_jj^{-1} by back substitution
-    for (int i = nb - 1; i > t; --i) Zi[i][t] = 0.0;
-    for (int i = t; i >= 0; --i) {
-      double v = (i == t) ? 1.0 : 0.0;
-      for (int k = i + 1; k <= t; ++k) v -= A[i][k] * Zi[k][t];
-      Zi[i][t] = v * rpiv[i];
-    }
-  }
+  // Z = R_jj^{-1} (R Z = I), right-looking over k = nb-1 .. 0: row k of the running sums A'
+  // (the identity minus the rows below, kept in A, whose factorisation is no longer needed)
+  // is final at step k, Z_kc = A'_kc / R_kk, and rows r < k subtract R_rk Z_kc.  One block
+  // barrier per step; the 32 steps replace a 32-deep serial chain per column.
+  A[r][c] = (r == c) ? 1.0 : 0.0;
   __syncthreads();
+  for (int k = nb - 1; k >= 0; --k) {
+    if (c >= k && c < nb) {
+      const double zkc = A[k][c] * rpiv[k];
+      if (r < k) A[r][c] -= Rs[r][k] * zkc;
+      if (r == k) Zi[k][c] = zkc;
+    }
+    __syncthreads();
+  }
   if (r < nb && c < nb) {
-    W[(j0 + r) + (size_t)(j0 + c) * p] = (r <= c) ? A[r][c] : 0.0;
+    W[(j0 + r) + (size_t)(j0 + c) * p] = (r <= c) ? Rs[r][c] : 0.0;
     Z[(j0 + r) + (size_t)(j0 + c) * p] = (r <= c) ? Zi[r][c] : 0.0;
   }
 }
