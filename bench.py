@@ -596,6 +596,23 @@ def run_ours(args, rank, world, local):
                           "traffic": recorded_traffic(kernel_names[dom], wl["name"]),
                           "alg_flops_per_launch": kf[dom], "alg_bytes_per_launch": kb[dom],
                           "launch_ms": kms[dom]}
+    if moptqr and dom == "primal_update":
+        # MOptQR's retraction (the Cholesky-QR of V every iteration) fills this slot: FP64-accurate
+        # Gram V^T V and Q = V R^-1 from exact FP32 products, Cholesky and R^-1 in FP64.  Table
+        # "cost"'s flops of one retraction: 2 n p^2 (Gram, upper half, and the triangular solve)
+        # + 2 p^3 / 3 (Cholesky, R^-1), against the FP32 FMA peak (the products and their exact
+        # sums run on the FP32 pipe)
+        clk = clocks.get("sm_mhz") or 2070.0
+        peak_alu = sm_count(torch) * 128 * 2 * clk * 1e6 / 1e12
+        fl = 2.0 * n * p * p + 2.0 * p ** 3 / 3.0
+        achieved_r = fl / (kms[dom] * 1e-3) / 1e12
+        roofline_graph = {"bound": "alu", "kernel": "moptqr_retraction", "achieved": achieved_r,
+                          "peak": peak_alu, "unit": "TFLOP/s", "frac": achieved_r / peak_alu,
+                          "peak_source": f"derived: {sm_count(torch)} SMs x 128 FP32 FMA lanes x 2 "
+                                         f"flop x median SM clock {clk:.0f} MHz",
+                          "traffic": None, "alg_flops_per_launch": fl, "launch_ms": kms[dom],
+                          "note": "exact FP32 products cost about ten FP32 operations per "
+                                  "multiply-add of the algorithm"}
     if engine != "resident":
         roofline = roofline_graph
     # ---- end to end through the public API with host buffers
