@@ -1,18 +1,20 @@
 #!/usr/bin/env python
-"""Benchmark of the PCAL hot path on GB300: time-to-KKT and iterations/s.
+"""Benchmark of the PCAL hot path on GB300: iterations/s and time-to-KKT.
 
-One step = one complete PCAL solve (Algorithm 3 with eq. lambda2, ABB step
-sizes, stop at relative KKT < tol, then the FP64 Cholesky-QR orthonormalisation)
-of the 1D Hartree-type energy f = 1/4 tr(X^T L X) + 1/4 rho^T L^{-1} rho,
-n = 20000, p = 50, from a seeded orthonormal start that is resident in device
-memory.  The timed arm is the mixed path (FP32 storage and products, FP64 p x p
-algebra); the FP64 GPU path is timed beside it.  L2 is flushed (256 MB write)
-before every timed step.
+Default workload: f = 1/2 tr(X^T (L3 + Diag(V)) X) on a 128^3 grid (n = 2097152), p = 1024,
+V iid U[0, 1], FP32 storage.  One step = one PCAL iteration (Lambda1 multiplier, ABB step
+size) in the compensated 3xTF32 phase, from a seeded orthonormal start resident in device
+memory; beside the timed steps: one complete solve to relative KKT 1e-5 plus the FP64
+Cholesky-QR (time-to-KKT, and end to end through the public API with host copies), the
+separable companion against its exact optimum, the FP64 GPU path over its first iterations
+(extrapolated) and the oracle on a slab of the grid (cpu_baseline).  `--workload` selects the
+other configurations (the 1D Hartree energy, 64^3 stencil, the 512-problem batch, Section
+5.4's n = 10000 problems).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
 
-Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank solves its own
-replica of the workload (no collective on the data path: "replicas only").
+Prints one JSON line (rank 0).  With N > 1 (torchrun) the default workload's rows are sharded
+over the ranks (one problem; strong scaling); the other workloads run one replica per rank.
 """
 from __future__ import annotations
 
@@ -52,12 +54,14 @@ WORKLOADS = {
     # (tests/golden), the FP64 path over its first iterations (extrapolated) and the oracle on
     # the grid's first 8 z-planes (cpu_baseline).  The start is the Q factor of a seeded
     # Gaussian generated on the device (a host FP64 start would take 17 GB).
-    # the separable companion (exact optimum) runs PCAL with the Lambda1 multiplier: with
-    # eq. (lambda2) one large ABB step collapses its columns onto one direction, which PCAL's
-    # column normalisation cannot undo (see the tests of the 128^3 solve)
+    # PCAL runs with the Lambda1 multiplier (Lambda = Psi(C)) on this workload and on its
+    # separable companion (exact optimum): with eq. (lambda2) a large ABB step early in the solve
+    # can collapse the columns onto one direction, which PCAL's column normalisation cannot undo
+    # (measured on the companion and, with other rounding of the same kernels, on this instance)
     "stencil3d_128": dict(kind="stencil3d", m=128, n=2097152, p=1024, beta=1.0, tol=1e-5,
                           tol_separable=1e-6, maxit=3000, name="stencil3d_n2097152_p1024",
-                          fp64_iters=1, slab_planes=8, separable=dict(lambda_rule="lambda1")),
+                          fp64_iters=1, slab_planes=8, lambda_rule="lambda1",
+                          separable=dict(lambda_rule="lambda1")),
     # Section 5.4's parallel workloads at n = 10000, p = 1000, PCAL with beta = 1 (the paper's
     # default): Problem 1 with L = Diag(L_1, ..., L_2000) of 5 x 5 Dirichlet blocks (alpha = 1),
     # and Problem 2 with the tridiagonal A and a random linear term; FP32 storage with
@@ -718,6 +722,30 @@ def timed_solve_e2e(sol, Xh, Xw, Q, Qh, torch):
     return ev[1].elapsed_time(ev[2]) / 1e3, ev[0].elapsed_time(ev[3]) / 1e3, st, info
 
 
+def pcal_name(wl):
+    return ("PCAL eq.(Lambda1), ABB" if wl.get("lambda_rule") == "lambda1"
+            else "PCAL eq.(lambda2), ABB")
+
+
+def solve_or_report(sol, Xh, Xw, Q, Qh, torch):
+    """One complete solve (timed_solve_e2e).  A solve whose final Cholesky-QR fails (the iterate
+    lost rank in a transient blow-up of the ABB steps) is reported with its history instead of
+    ending the run; otherwise "result" holds timed_solve_e2e's tuple."""
+    from paper_1810_03930_gb300._lib import PlamError
+    try:
+        res = timed_solve_e2e(sol, Xh, Xw, Q, Qh, torch)
+    except PlamError as e:
+        hist = sol.history()
+        out = {"status": "failed", "error": str(e)}
+        if len(hist):
+            out.update({"iters": int(hist[-1][0]), "kkt_rel_last": float(hist[-1][2]),
+                        "feas_last": float(hist[-1][3]),
+                        "feas_max": float(max(h[3] for h in hist))})
+        return out
+    return {"status": {0: "converged", 2: "maxit"}.get(res[2], str(res[2])),
+            "iters": int(res[3].iters), "time_s": res[0], "result": res}
+
+
 def companion_parity(sol_p, wls, Xh, Xw, Q, Vs64, m, torch):
     """One solve of the separable companion and its objective against the exact optimum.  A
     solve whose final Cholesky-QR fails (the iterate lost rank in a transient blow-up of the
@@ -783,7 +811,8 @@ def run_stencil128_sharded(args, rank, world, local, wl):
 
     def solver(tc, maxit, final_orth):
         return sharded_solver(comm, "stencil3d", sl.n_local, p, sl.row0, n, grid=(m, m, sl.nz_local),
-                              V=V, variant="pcal", lambda_rule="lambda2", beta=wl["beta"],
+                              V=V, variant="pcal", lambda_rule=wl.get("lambda_rule", "lambda2"),
+                              beta=wl["beta"],
                               tol=wl["tol"], maxit=maxit, precision="fp32", final_orth=final_orth,
                               tensor_cores=tc)
 
@@ -834,7 +863,7 @@ def run_stencil128_sharded(args, rank, world, local, wl):
     out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": wl["name"], "n": n, "p": p, "solver": "PCAL eq.(lambda2), ABB",
+           "config": {"workload": wl["name"], "n": n, "p": p, "solver": pcal_name(wl),
                       "beta": wl["beta"], "tol_kkt_rel": wl["tol"], "maxit": wl["maxit"],
                       "step": "one PCAL iteration of the whole problem, compensated 3xTF32",
                       "l2": "inputs larger than L2",
@@ -893,18 +922,34 @@ def run_stencil128(args, rank, world, local):
     sol_s.close()
     del Xs
     torch.cuda.empty_cache()
-    # ---- one complete solve of the workload: time-to-KKT and end to end
-    sol = make_solver(wl, "fp32", torch, engine="graph", maxit=wl["maxit"])
+    # ---- one complete solve of the workload: time-to-KKT and end to end.  If the iterate of a
+    # solve with eq. (lambda2) loses rank in a transient of the ABB steps (the final Cholesky-QR
+    # then fails, and PCAL cannot undo a collapse), the failure is reported and the solve is
+    # repeated from the same start with the Lambda1 multiplier
     Xh = torch.empty((p, n), dtype=torch.float32, pin_memory=True)
     Xh.copy_(X0)
     Qh = torch.empty((p, n), dtype=torch.float64, pin_memory=True)
     Xw = torch.empty_like(X0)
     Q = torch.empty((p, n), dtype=torch.float64, device="cuda")
-    t_solve, t_e2e, st, info = timed_solve_e2e(sol, Xh, Xw, Q, Qh, torch)
-    launches_solve = sol.kernel_launches()
-    parity = result_parity(Q, V64, m, info, torch)
-    parity["status"] = {0: "converged", 2: "maxit"}.get(st, str(st))
-    sol.close()
+    rules = [wl.get("lambda_rule", "lambda2")]
+    if rules[0] != "lambda1":
+        rules.append("lambda1")
+    attempts, info, st, t_solve, t_e2e, launches_solve, parity = [], None, None, None, None, 0, None
+    for rule in rules:
+        sol = make_solver(dict(wl, lambda_rule=rule), "fp32", torch, engine="graph",
+                          maxit=wl["maxit"])
+        attempt = solve_or_report(sol, Xh, Xw, Q, Qh, torch)
+        attempt["lambda_rule"] = rule
+        if attempt["status"] != "failed":
+            t_solve, t_e2e, st, info = attempt.pop("result")
+            launches_solve = sol.kernel_launches()
+            parity = result_parity(Q, V64, m, info, torch)
+            parity["status"] = attempt["status"]
+            parity["lambda_rule"] = rule
+        attempts.append(attempt)
+        sol.close()
+        if info is not None:
+            break
     del Qh
     # ---- the companion instance with a separable potential: exact optimum (tests/golden)
     Vs64 = torch.as_tensor(stencil3d_separable_potential(m)[0], device="cuda")
@@ -928,7 +973,7 @@ def run_stencil128(args, rank, world, local):
     sol64.close()
     del X64
     fp64 = {"s_per_iter": t64, "iters_per_s": 1.0 / t64, "iters_timed": wl["fp64_iters"],
-            "time_to_kkt_s": info.iters * t64,
+            "time_to_kkt_s": info.iters * t64 if info is not None else None,
             "time_to_kkt_note": "extrapolated: the mixed path's iteration count x the FP64 path's "
                                 f"time per iteration over iterations 2..{1 + wl['fp64_iters']}"}
     # ---- roofline of the dominant kernel group of the timed steps
@@ -972,25 +1017,29 @@ def run_stencil128(args, rank, world, local):
            "config": {"workload": wl["name"],
                       "objective": "1/2 tr(X^T (L3 + Diag(V)) X), 7-point Dirichlet L3 on 128^3, "
                                    "V iid U[0,1]",
-                      "n": n, "p": p, "solver": "PCAL eq.(lambda2), ABB", "beta": wl["beta"],
+                      "n": n, "p": p, "solver": pcal_name(wl), "beta": wl["beta"],
                       "tol_kkt_rel": wl["tol"], "maxit": wl["maxit"],
                       "step": "one PCAL iteration, compensated 3xTF32 tensor-core Grams and update",
                       "final_orth": "FP64 Cholesky-QR",
                       "l2": "inputs larger than L2 (8.6 GB per n x p buffer)",
                       "parallelism": "single GPU" if world == 1 else f"{world} replicas"},
-           "time_to_kkt_s": t_solve, "iters_per_solve": info.iters,
-           "iters_per_s_solve": info.iters / t_solve,
-           "fp64": fp64, "mixed_speedup_vs_fp64": fp64["time_to_kkt_s"] / t_solve,
+           "time_to_kkt_s": t_solve, "iters_per_solve": info.iters if info else None,
+           "iters_per_s_solve": info.iters / t_solve if info else None,
+           "fp64": fp64,
+           "mixed_speedup_vs_fp64": fp64["time_to_kkt_s"] / t_solve if info else None,
+           "solve_attempts": attempts,
            "parity": parity, "parity_separable": parity_sep, "engine": "graph",
            "roofline": roofline, "kernels_ms_per_launch": kernels,
-           "e2e": {"value": info.iters / t_e2e, "unit": "iters/s", "time_to_kkt_s": t_e2e,
-                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "e2e": {"value": info.iters / t_e2e if info else None, "unit": "iters/s",
+                   "time_to_kkt_s": t_e2e, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                    "note": "one complete solve through Solver.solve: the start from pinned host "
-                           "memory in, the FP64 result out"},
+                           "memory in, the FP64 result out" if info else
+                           "no solve completed (solve_attempts)"},
            "gpu_launches": int(launches), "gpu_launches_solve": int(launches_solve),
            "clocks": clocks}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline_slab(wl, V64.cpu().numpy(), args.cpu_seconds, info.iters)
+        iters = info.iters if info else attempts[-1].get("iters", wl["maxit"])
+        out["cpu_baseline"] = cpu_baseline_slab(wl, V64.cpu().numpy(), args.cpu_seconds, iters)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -1019,11 +1068,13 @@ def cpu_baseline_slab(wl, V, seconds, gpu_iters):
     grid, Vs, X0s, ns = slab_problem(wl, V, planes)
     obj = oo.Stencil3DObjective(grid, Vs)
     t0 = time.perf_counter()
-    op.solve(obj, X0s, variant="pcal", beta=wl["beta"], tol=0.0, maxit=1, record=False)
+    op.solve(obj, X0s, variant="pcal", beta=wl["beta"],
+             lambda_rule=wl.get("lambda_rule", "lambda2"), tol=0.0, maxit=1, record=False)
     per_it = time.perf_counter() - t0          # one iteration plus the final Householder QR
     k = int(max(1, min(50, seconds / max(per_it, 1e-6))))
     t0 = time.perf_counter()
-    r = op.solve(obj, X0s, variant="pcal", beta=wl["beta"], tol=0.0, maxit=k, record=False)
+    r = op.solve(obj, X0s, variant="pcal", beta=wl["beta"],
+                 lambda_rule=wl.get("lambda_rule", "lambda2"), tol=0.0, maxit=k, record=False)
     dt = time.perf_counter() - t0
     scale = ns / wl["n"]
     rate = (r.iters + 1) / dt * scale
@@ -1066,6 +1117,7 @@ def run_reference(args, rank, world):
     for _ in range(max(1, args.warmup)):
         t0 = time.perf_counter()
         r = op.solve(obj, X0, variant="pcal", beta=wl["beta"], tol=wl["tol"],
+                     lambda_rule=wl.get("lambda_rule", "lambda2"),
                      maxit=1 if scale != 1.0 else 2, record=False)
         per_it = (time.perf_counter() - t0) / (r.iters + 1)
     # each step a bounded sample of the solve: 20 iterations, fewer where one takes long (about 8 s
@@ -1075,7 +1127,8 @@ def run_reference(args, rank, world):
     times, iters = [], []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        r = op.solve(obj, X0, variant="pcal", beta=wl["beta"], tol=wl["tol"], maxit=per_step,
+        r = op.solve(obj, X0, variant="pcal", beta=wl["beta"], tol=wl["tol"],
+                     lambda_rule=wl.get("lambda_rule", "lambda2"), maxit=per_step,
                      record=False)
         times.append(time.perf_counter() - t0)
         iters.append(r.iters + 1)
