@@ -109,3 +109,35 @@ def test_flop_accounting_matches_table_cost():
         kf = bench.kernel_flops(wl)
         assert kf["gram_partial"] == 3 * n * p * p and kf["update"] == 4 * n * p * p, name
         assert kf["gram_partial"] + kf["update"] == 7 * n * p * p, name
+
+
+def test_a_collapsed_solve_is_reported_not_raised(monkeypatch):
+    """A solve whose final Cholesky-QR fails (the iterate lost rank in an ABB transient) becomes
+    a "failed" record with the last iterate's KKT value and feasibility, so that the benchmark
+    still prints its line; a completed solve carries its status and iteration count."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1810_03930_gb300._lib import PlamError
+
+    class FakeSolver:
+        def history(self):
+            return [(0, 5.0, 1.0, 1e-14, 1.0), (1, 4.0, 0.5, 2.3, 0.5), (2, 3.0, 1e-6, 1023.0, 0.5)]
+
+    def collapse(*a):
+        raise PlamError(6, "plam_solve")
+
+    monkeypatch.setattr(bench, "timed_solve_e2e", collapse)
+    out = bench.solve_or_report(FakeSolver(), None, None, None, None, None)
+    assert out["status"] == "failed" and "plam_solve" in out["error"]
+    assert out["iters"] == 2 and out["kkt_rel_last"] == 1e-6
+    assert out["feas_last"] == 1023.0 and out["feas_max"] == 1023.0
+    json.dumps(out)
+
+    class Info:
+        iters = 953
+
+    monkeypatch.setattr(bench, "timed_solve_e2e", lambda *a: (55.6, 56.0, 0, Info()))
+    ok = bench.solve_or_report(FakeSolver(), None, None, None, None, None)
+    assert ok["status"] == "converged" and ok["iters"] == 953 and ok["time_s"] == 55.6
+    assert ok["result"][3].iters == 953
+    assert bench.pcal_name(bench.WORKLOADS["stencil3d_128"]) == "PCAL eq.(Lambda1), ABB"
